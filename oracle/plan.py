@@ -1,0 +1,267 @@
+"""The oracle's own choice of (b, N, lambda) from an FP64 error bound
+(test infrastructure only; written independently of the library's planner).
+
+Rule (a reading of the paper, which leaves b and lambda to the implementer;
+Section 2.3 Scenario #2 asks for 3b + lg N + beta_N <= 53, Section 5 picks b
+empirically, and the bounds below replace that by a proof-style budget):
+
+- digits are balanced (Section 5), |U_i| <= 2^(b-1); the high product's top
+  digit is unbalanced, 0 <= U_N <= 2^b;
+- transform lengths are even and smooth, L = 2^a m with odd part m in ODD_PARTS
+  (Section 5 restricts N to 2^e2 3^e3 5^e5 7^e7); the smallest such length that
+  satisfies the method's hypothesis is used: N >= n/b (Theorem 2.2),
+  (N+1) b >= n + lg N + 2 (Theorem 2.3), L >= 2 N_d - 1 with N_d b >= n + 1
+  (full product, Theorem 2.1 with any cyclic length that holds the product);
+- the convolution error is ||x||_2 ||y||_2 ((1+u)^3K (1+sqrt5 u)^(3K+1)
+  (1+tau)^3K - 1), the explicit FFT bound the paper points to in Section 2.1
+  (Brent-Zimmermann Theorem 3.6), with K radix-2-equivalent levels per
+  transform: lg L, plus 2 for every odd prime factor, plus 2 for the real-data
+  pre/post-processing;
+- the maps' coefficient bounds follow Lemmas 3.5 and 4.7 (with the proof of
+  Lemma 4.7 carried to |gamma_{k,r}| <= 2^-rb exp((r-1) H_r / N)), their norm
+  growth Lemmas 3.8/3.9 and 4.8/4.9 (with ||X H|| <= (1 + 2^-b)||H|| mod A
+  and <= (1 + 2^(1-b))||H|| mod C, as shown inside those proofs);
+- lambda is the smallest number of terms whose truncation tail is at most u/4
+  relative (Lemmas 3.10, 3.11, 4.10, 4.11);
+- b is the largest value in [4, 24] whose total bound, times 2^b for the
+  truncated products, is <= E_TARGET < 1/2 (Theorems 2.2 / 2.3 need < 1/2).
+"""
+import math
+
+U = 2.0 ** -53
+TAU = 2.0 * U
+E_TARGET = 0.45
+B_MIN, B_MAX = 4, 24
+ODD_PARTS = (1, 3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49, 63, 75, 81, 105, 125, 135, 147,
+             175, 189)
+SEARCH_SPAN = 1.25   # candidate lengths up to SEARCH_SPAN x the minimal one
+
+
+def ceil_log2(x: int) -> int:
+    return max(0, (int(x) - 1).bit_length())
+
+
+def odd_prime_factor_count(L: int) -> int:
+    c = 0
+    for p in (3, 5, 7):
+        while L % p == 0:
+            L //= p
+            c += 1
+    return c
+
+
+def is_valid_length(L: int) -> bool:
+    if L < 4 or L % 2:
+        return False
+    m = L
+    while m % 2 == 0:
+        m //= 2
+    return m in ODD_PARTS
+
+
+def smooth_at_least(x: int) -> int:
+    x = max(4, int(x))
+    best = None
+    for m in ODD_PARTS:
+        L = 2 * m
+        while L < x:
+            L *= 2
+        if best is None or L < best:
+            best = L
+    return best
+
+
+def levels(L: int) -> int:
+    return ceil_log2(L) + 2 * odd_prime_factor_count(L) + 2
+
+
+def eta_conv(L: int) -> float:
+    K = levels(L)
+    return math.expm1(3 * K * math.log1p(U) + (3 * K + 1) * math.log1p(math.sqrt(5) * U)
+                      + 3 * K * math.log1p(TAU))
+
+
+_H = [0.0]
+for _j in range(1, 400):
+    _H.append(_H[-1] + 1.0 / _j)
+
+
+def harmonic(r: int) -> float:
+    return _H[r]
+
+
+def gamma_coef_bound(r: int, b: int, N: int) -> float:
+    return 2.0 ** (-r * b) * math.exp((r - 1) * harmonic(r) / N) if r else 1.0
+
+
+def lam_alpha(b: int) -> int:
+    lam = 1
+    while (16.0 / 15.0) * 2.0 ** (-lam * b) > U / 4:
+        lam += 1
+    return lam
+
+
+def _lam_geometric(b: int, grow: float) -> int:
+    q = grow * 2.0 ** -b
+    lam = 1
+    while q ** lam / (1 - q) > U / 4:
+        lam += 1
+    return lam
+
+
+def lam_beta(b: int) -> int:
+    return _lam_geometric(b, 1 + 2.0 ** -b)
+
+
+def lam_delta(b: int) -> int:
+    return _lam_geometric(b, 1 + 2.0 ** (1 - b))
+
+
+def gamma_tail(lam: int, b: int, N: int) -> float:
+    return sum(gamma_coef_bound(r, b, N) for r in range(lam, lam + 64))
+
+
+def lam_gamma(b: int, N: int) -> int:
+    lam = 1
+    while gamma_tail(lam, b, N) > U / 4:
+        lam += 1
+    return lam
+
+
+def rho_float(N: int, b: int) -> float:
+    """Newton on B(z) = z^(N+1) - 2^b z^N + 2^b in the scaled form y = z/2^b:
+    y^N (y - 1) + 2^-Nb = 0 (proof of Lemma 4.2); float is enough for the bound."""
+    eps = 2.0 ** (-N * b)
+    y = 1.0
+    for _ in range(100):
+        f = y ** N * (y - 1.0) + eps
+        df = y ** (N - 1) * ((N + 1) * y - N)
+        y_new = y - f / df
+        if y_new == y:
+            break
+        y = y_new
+    return y * 2.0 ** b
+
+
+def min_len_lo(n: int, b: int) -> int:
+    """Theorem 2.2: N >= n/b, N >= 3."""
+    return max(3, -(-n // b))
+
+
+def hi_ok(n: int, b: int, N: int) -> bool:
+    """Theorem 2.3: (N + 1) b >= n + lg N + 2, N >= 3."""
+    return N >= 3 and (N + 1) * b >= n + ceil_log2(N) + 2
+
+
+def min_len_hi(n: int, b: int) -> int:
+    N = max(3, -(-(n + 2) // b) - 1)      # ignores lg N, so it is a lower bound
+    while not hi_ok(n, b, N):
+        N += 1
+    return N
+
+
+def full_digits(n: int, b: int) -> int:
+    """Balanced digits without a carry out of the top one need N_d b >= n + 1."""
+    return max(2, -(-(n + 1) // b))
+
+
+def bound_lo(n: int, b: int, N: int):
+    la, lb = lam_alpha(b), lam_beta(b)
+    eta = eta_conv(N)
+    g = 1.0 / (1.0 - 2.0 ** -b)
+    S = g * 2.0 ** (b - 1) * math.sqrt(N)
+    MW = S * S
+    d_in = ((la + 2) * U + (16.0 / 15.0) * 2.0 ** (-la * b)) * g * 2.0 ** (b - 1)
+    E_in = 2.0 * math.sqrt(N) * d_in * S * (1.0 + eta)
+    A = 1.0 / (1.0 - (1.0 + 2.0 ** -b) * 2.0 ** -b)
+    q = (1.0 + 2.0 ** -b) * 2.0 ** -b
+    tail = q ** lb / (1.0 - q)
+    E_W = eta * MW + E_in
+    E = 2.0 ** b * (A * E_W + (lb + 3) * U * A * MW + tail * MW)
+    return E, N, la, lb
+
+
+def bound_hi(n: int, b: int, N: int):
+    rho = rho_float(N, b)
+    lg, ld = lam_gamma(b, N), lam_delta(b)
+    eta = eta_conv(N)
+    g = sum(gamma_coef_bound(r, b, N) for r in range(0, 80))
+    kappa0 = 2.0 ** b / rho
+    K2 = kappa0 / math.sqrt(1.0 - rho ** -2)
+    S = g * (2.0 ** (b - 1) * math.sqrt(N) + 2.0 ** b * K2)
+    MW = S * S
+    m_F = 2.0 ** (b - 1) + 2.0 ** b * kappa0
+    d_in = ((lg + 4) * U + gamma_tail(lg, b, N)) * g * m_F
+    E_in = 2.0 * math.sqrt(N) * d_in * S * (1.0 + eta)
+    T = 2.0 ** b + 2.0 ** (b - 1) / (rho - 1.0)
+    J = -(-60 // b) + 1
+    E_theta = (2 * (J + 2) + 1) * U * T * T
+    q = (1.0 + 2.0 ** (1 - b)) * 2.0 ** -b
+    A = 1.01 * (1.0 + 2.0 ** -b) / (1.0 - q)
+    tail = q ** ld / (1.0 - q)
+    E_W = eta * MW + E_in
+    E = 2.0 ** b * (A * (E_W + E_theta) + (ld + 4) * U * A * (MW + T * T) + tail * MW)
+    return E, N, lg, ld
+
+
+def bound_full(n: int, b: int, L: int):
+    Nd = full_digits(n, b)
+    eta = eta_conv(L)
+    MW = 2.0 ** (2 * b - 2) * Nd
+    E = eta * MW + 2.0 * U * MW
+    return E, L, Nd
+
+
+def smooth_lengths_from(x: int, span: float = SEARCH_SPAN):
+    """Valid transform lengths in [x, span * x] (at least one), increasing."""
+    x = max(4, int(x))
+    first = smooth_at_least(x)
+    out = set()
+    top = max(first, int(span * x))
+    for m in ODD_PARTS:
+        L = 2 * m
+        while L < x:
+            L *= 2
+        while L <= top:
+            out.add(L)
+            L *= 2
+    return sorted(out)
+
+
+def choose(kind: str, n: int) -> dict:
+    """For each b in [B_MIN, B_MAX], the shortest valid length (searched up to
+    SEARCH_SPAN x the minimal one) whose bound is <= E_TARGET; then the b whose
+    length is shortest (ties: the larger b). Keys: kind, n, b, N (transform
+    length), n_digits, lam_fwd, lam_bwd, e_max."""
+    assert n >= 1
+    best = None
+    for b in range(B_MIN, B_MAX + 1):
+        if kind == "lo":
+            lmin = min_len_lo(n, b)
+        elif kind == "hi":
+            lmin = min_len_hi(n, b)
+        elif kind == "full":
+            lmin = 2 * full_digits(n, b) - 1
+        else:
+            raise ValueError(kind)
+        for N in smooth_lengths_from(lmin):
+            if kind == "hi" and not hi_ok(n, b, N):
+                continue
+            if kind == "lo":
+                E, _, lf, lb = bound_lo(n, b, N)
+                nd = N
+            elif kind == "hi":
+                E, _, lf, lb = bound_hi(n, b, N)
+                nd = N + 1
+            else:
+                E, _, nd = bound_full(n, b, N)
+                lf = lb = 0
+            if E <= E_TARGET:
+                cand = {"kind": kind, "n": n, "b": b, "N": N, "n_digits": nd,
+                        "lam_fwd": lf, "lam_bwd": lb, "e_max": E}
+                if best is None or N < best["N"] or (N == best["N"] and b > best["b"]):
+                    best = cand
+                break
+    if best is None:
+        raise ValueError(f"no FP64 plan for {kind} n={n}")
+    return best
