@@ -1,0 +1,168 @@
+/*
+ * truncmul.h - C ABI of a GB300 (sm_103a) library for full, low and high
+ * products of n-bit integers, after D. Harvey, "Faster truncated integer
+ * multiplication".
+ *
+ * Definitions (Section 1 of the paper). For integers 0 <= u, v < 2^n:
+ *   full product  uv, a 2n-bit integer;
+ *   low product   the unique 0 <= w < 2^n with w == uv (mod 2^n);
+ *   high product  any 0 <= w <= 2^n with |uv - 2^n w| < 2^n (at most two
+ *                 values qualify; w = 2^n is possible).
+ *
+ * Method. Full products follow Algorithm 1 (split into b-bit digits, one real
+ * cyclic convolution of length >= 2N - 1, round, overlap-add). Low products
+ * follow Algorithm 2 (Section 3): digits -> alpha* map -> real cyclic
+ * convolution of length N -> beta* map -> round(2^b W_i) -> overlap-add mod
+ * 2^n. High products follow Algorithm 3 (Section 4): digits of u 2^((N+1)b-n)
+ * -> gamma-dagger -> convolution plus the auxiliary scalar theta -> delta-dagger
+ * -> round -> round(t). Every step runs in CUDA kernels of this library; the
+ * convolution is an FP64 real FFT. The parameters (b, N, lambda) come from a
+ * worst-case FP64 error bound, so that every rounded coefficient is exact; each
+ * call measures the largest distance of a rounded value to its integer (the
+ * "margin") and fails with TM_EPRECISION if it exceeds the bound.
+ *
+ * Limb layout. Every integer is a little-endian array of uint64_t limbs (limb
+ * 0 holds bits 0..63). u and v have ceil(n/64) limbs each; bits at positions
+ * >= n of their top limb must be zero (they are ignored). Outputs:
+ *   full: 2*ceil(n/64) limbs;
+ *   low:  ceil(n/64) limbs, bits >= n cleared;
+ *   high: floor(n/64) + 1 limbs (room for w = 2^n).
+ *
+ * Memory and ownership. Unless a function says otherwise, u, v and out are
+ * DEVICE pointers owned by the caller; out must not overlap u or v (u == v is
+ * allowed). The library owns a plan cache (twiddle and map tables, kept
+ * resident per (kind, n) and device) and a workspace per (device, stream),
+ * both grown on demand and kept until tm_release() or process exit. Calls on
+ * the same stream are ordered; calls on different streams use different
+ * workspaces and may run concurrently. The library is thread-safe.
+ *
+ * Streams and status. `stream` is a cudaStream_t (NULL = the legacy default
+ * stream); the device is the current device of the calling thread. Work is
+ * enqueued on `stream`. If `rep` is NULL the call returns as soon as the work
+ * is enqueued and the device-side status (margin check) is collected later
+ * by tm_stream_status(). If `rep` is non-NULL the call waits for the stream,
+ * fills *rep and returns the device-side status as well.
+ */
+#ifndef TRUNCMUL_H
+#define TRUNCMUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (0 = success) ---- */
+#define TM_OK          0
+#define TM_EINVAL     -1   /* bad argument: n = 0, NULL pointer, unknown kind    */
+#define TM_ENOMEM     -2   /* device or host allocation failed                   */
+#define TM_EPRECISION -3   /* margin above the a-priori bound, or 2^b not
+                              dividing c_0: the output must not be trusted       */
+#define TM_ETIMEOUT   -4   /* a bounded device-side wait gave up                 */
+#define TM_ECUDA      -5   /* a CUDA runtime call failed                         */
+#define TM_ERANGE     -6   /* n too large for any FP64 plan of this library      */
+#define TM_EALIAS     -7   /* out overlaps u or v                                */
+
+/* ---- product kinds ---- */
+#define TM_FULL 0          /* Algorithm 1 */
+#define TM_LO   1          /* Algorithm 2 */
+#define TM_HI   2          /* Algorithm 3 */
+
+/* Largest supported operand size in bits. */
+#define TM_MAX_BITS (((uint64_t)1) << 31)
+
+/* Plan and outcome of one call. */
+typedef struct tm_report {
+  int32_t  kind;      /* TM_FULL, TM_LO or TM_HI                                  */
+  int32_t  status;    /* device-side status of the call (TM_OK or TM_EPRECISION)  */
+  uint32_t b;         /* digit size in bits                                       */
+  uint32_t N;         /* real transform length (N of Algorithms 2/3; the cyclic
+                         length >= 2 n_digits - 1 of Algorithm 1)                 */
+  uint32_t n_digits;  /* digits per operand: N (low), N + 1 (high), ceil((n+1)/b)
+                         (full)                                                   */
+  uint32_t lam_fwd;   /* terms of alpha* (low) or gamma* (high); 0 for full       */
+  uint32_t lam_bwd;   /* terms of beta* (low) or delta* (high); 0 for full        */
+  uint32_t fft_passes;/* HBM passes of each complex FFT of length N/2             */
+  double   margin;    /* largest |2^b Wbar_i - c_i| (low/high) or |W_i - w_i|
+                         (full) over the call; filled when rep != NULL           */
+  double   e_max;     /* a-priori bound on that distance (< 1/2)                  */
+  uint64_t workspace_bytes; /* device workspace the call needs                    */
+  uint64_t table_bytes;     /* resident plan tables on the device                 */
+} tm_report;
+
+/*
+ * tm_mul_full / tm_mul_lo / tm_mul_hi
+ *   out  device, see "Limb layout" for the length.
+ *   u, v device, ceil(n_bits/64) limbs each.
+ *   n_bits in [1, TM_MAX_BITS].
+ *   stream cudaStream_t or NULL.
+ *   rep  optional (NULL = asynchronous, see above).
+ * Returns TM_OK or a negative TM_E* code. On TM_EINVAL/TM_ERANGE/TM_EALIAS
+ * nothing is enqueued.
+ * Sources: full product - Algorithm 1 and Theorem 2.1; low product -
+ * Algorithm 2, Theorem 2.2, Proposition 3.1; high product - Algorithm 3,
+ * Theorem 2.3, Proposition 4.1 (the result is round(t) of line 7, rounding
+ * half up, which is one of the at most two admissible values).
+ */
+int tm_mul_full(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+                void* stream, tm_report* rep);
+int tm_mul_lo(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep);
+int tm_mul_hi(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep);
+
+/* The same three operations selected by `kind` (TM_FULL, TM_LO, TM_HI). */
+int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+           void* stream, tm_report* rep);
+
+/*
+ * tm_mul_host: one product with HOST buffers. Copies u and v to the device,
+ * runs tm_mul on `stream`, copies the result back and waits for the stream.
+ * Page-locked host buffers give the fastest copies; pageable ones work.
+ * Limb counts as above. Returns like tm_mul; *rep (optional) is filled.
+ */
+int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint64_t* v_host,
+                uint64_t n_bits, void* stream, tm_report* rep);
+
+/*
+ * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
+ * for checking the method stage by stage:
+ *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2 line 6,
+ *         Proposition 3.1);
+ *   high: c_i = round(2^b Wbar_i) = 2^b H_i, i <= N      (Algorithm 3 line 6,
+ *         Proposition 4.1);
+ *   full: c_i = round(Wbar_i) = w_i, i < N (the cyclic length) (Algorithm 1).
+ * c_out must hold rep->n_digits (high: N + 1) or N int64 values: use
+ * tm_plan_query first. Waits for the stream; *rep is required.
+ */
+int tm_coeffs(int kind, int64_t* c_out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep);
+
+/*
+ * tm_plan_query: the plan the library uses for (kind, n_bits), without any
+ * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, e_max and
+ * workspace_bytes of *rep. Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.
+ */
+int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep);
+
+/*
+ * tm_stream_status: waits for `stream`, then returns and clears the
+ * device-side status accumulated by asynchronous calls on it (TM_OK or
+ * TM_EPRECISION); if rep != NULL, rep->margin receives the largest margin
+ * seen since the last clear.
+ */
+int tm_stream_status(void* stream, tm_report* rep);
+
+/* tm_release: frees every plan table and workspace of the current device.
+ * No call may be in flight on that device. */
+int tm_release(void);
+
+/* Text for a status code (static storage). */
+const char* tm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRUNCMUL_H */

@@ -1,0 +1,193 @@
+"""Python binding of libtruncmul (include/truncmul.h): argument marshalling only.
+
+Every step of a product runs in the library's CUDA kernels. Operands and
+results are little-endian uint64 limb arrays; torch tensors (any 8-byte dtype,
+contiguous, on the current CUDA device) supply device memory and streams. The
+library must be built (``build()`` or ``__graft_entry__.build()``); importing
+fails loudly when it is missing, and there is no CPU fallback.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+KIND = {"full": 0, "lo": 1, "hi": 2}
+STATUS = {0: "TM_OK", -1: "TM_EINVAL", -2: "TM_ENOMEM", -3: "TM_EPRECISION", -4: "TM_ETIMEOUT",
+          -5: "TM_ECUDA", -6: "TM_ERANGE", -7: "TM_EALIAS"}
+TM_OK, TM_EINVAL, TM_ENOMEM, TM_EPRECISION, TM_ETIMEOUT, TM_ECUDA, TM_ERANGE, TM_EALIAS = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+
+
+class Report(ctypes.Structure):
+    """tm_report (include/truncmul.h)."""
+    _fields_ = [("kind", ctypes.c_int32), ("status", ctypes.c_int32), ("b", ctypes.c_uint32),
+                ("N", ctypes.c_uint32), ("n_digits", ctypes.c_uint32),
+                ("lam_fwd", ctypes.c_uint32), ("lam_bwd", ctypes.c_uint32),
+                ("fft_passes", ctypes.c_uint32), ("margin", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
+                ("table_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TruncMulError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})")
+        self.code = code
+
+
+EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_coeffs",
+           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def load(path: str = None):
+    """Loads libtruncmul.so (no build; raises OSError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: run paper_1703_00640_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    R = ctypes.POINTER(Report)
+    for name in ("tm_mul_full", "tm_mul_lo", "tm_mul_hi"):
+        getattr(lib, name).argtypes = [P, P, P, ctypes.c_uint64, P, R]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.tm_mul.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_host.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_coeffs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_plan_query.argtypes = [ctypes.c_int, ctypes.c_uint64, R]
+    lib.tm_stream_status.argtypes = [P, R]
+    lib.tm_release.argtypes = []
+    lib.tm_strerror.argtypes = [ctypes.c_int]
+    lib.tm_strerror.restype = ctypes.c_char_p
+    for name in ("tm_mul", "tm_mul_host", "tm_coeffs", "tm_plan_query", "tm_stream_status",
+                 "tm_release"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def strerror(code: int) -> str:
+    return load().tm_strerror(int(code)).decode()
+
+
+def _kind(kind) -> int:
+    return KIND[kind] if isinstance(kind, str) else int(kind)
+
+
+def out_limbs(kind, n_bits: int) -> int:
+    k = _kind(kind)
+    nl = (n_bits + 63) // 64
+    return 2 * nl if k == 0 else (nl if k == 1 else n_bits // 64 + 1)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_contiguous() and t.element_size() == 8, "limb tensors must be contiguous 8-byte"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def plan(kind, n_bits: int) -> dict:
+    """tm_plan_query: the library's plan for (kind, n) (host only, no GPU needed)."""
+    rep = Report()
+    rc = load().tm_plan_query(_kind(kind), int(n_bits), ctypes.byref(rep))
+    if rc:
+        raise TruncMulError(rc, "tm_plan_query")
+    return rep.as_dict()
+
+
+def mul(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True, check: bool = True):
+    """tm_mul on device tensors. Returns (out, report dict or None)."""
+    import torch
+    k = _kind(kind)
+    if out is None:
+        out = torch.empty(out_limbs(k, n_bits), dtype=torch.int64, device=u.device)
+    rep = Report() if report else None
+    rc = load().tm_mul(k, _ptr(out), _ptr(u), _ptr(v), int(n_bits), _stream_ptr(stream),
+                       ctypes.byref(rep) if rep is not None else None)
+    if check and rc:
+        raise TruncMulError(rc, "tm_mul")
+    return out, (rep.as_dict() if rep is not None else None)
+
+
+def mul_lo(u, v, n_bits, **kw):
+    return mul("lo", u, v, n_bits, **kw)
+
+
+def mul_hi(u, v, n_bits, **kw):
+    return mul("hi", u, v, n_bits, **kw)
+
+
+def mul_full(u, v, n_bits, **kw):
+    return mul("full", u, v, n_bits, **kw)
+
+
+def mul_host(kind, u, v, n_bits: int, out=None, stream=None):
+    """tm_mul_host on host (CPU) tensors or numpy arrays; returns (out, report)."""
+    import numpy as np
+    k = _kind(kind)
+    if out is None:
+        out = np.zeros(out_limbs(k, n_bits), dtype=np.uint64)
+
+    def p(a):
+        if hasattr(a, "data_ptr"):
+            assert a.is_contiguous() and a.element_size() == 8
+            return ctypes.c_void_p(a.data_ptr())
+        assert a.dtype.itemsize == 8 and a.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(a.ctypes.data)
+    rep = Report()
+    rc = load().tm_mul_host(k, p(out), p(u), p(v), int(n_bits), _stream_ptr(stream),
+                            ctypes.byref(rep))
+    if rc:
+        raise TruncMulError(rc, "tm_mul_host")
+    return out, rep.as_dict()
+
+
+def coeffs(kind, u, v, n_bits: int, stream=None):
+    """tm_coeffs: the rounded coefficients c_i (int64 device tensor) and the report."""
+    import torch
+    k = _kind(kind)
+    pl = plan(k, n_bits)
+    count = pl["N"] + 1 if k == 2 else pl["N"]
+    c = torch.empty(count, dtype=torch.int64, device=u.device)
+    rep = Report()
+    rc = load().tm_coeffs(k, _ptr(c), _ptr(u), _ptr(v), int(n_bits), _stream_ptr(stream),
+                          ctypes.byref(rep))
+    if rc and rc != TM_EPRECISION:
+        raise TruncMulError(rc, "tm_coeffs")
+    return c, rep.as_dict()
+
+
+def stream_status(stream=None) -> dict:
+    rep = Report()
+    rc = load().tm_stream_status(_stream_ptr(stream), ctypes.byref(rep))
+    d = rep.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def release():
+    rc = load().tm_release()
+    if rc:
+        raise TruncMulError(rc, "tm_release")

@@ -1,0 +1,522 @@
+// C ABI of the library (declared in include/truncmul.h): plan cache, per-stream
+// workspaces and the launch sequence of one product.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/truncmul.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace tmul {
+namespace {
+
+// Resident device tables of one (device, kind, n).
+struct PlanEntry {
+  PlanParams p;
+  FftPlan fft;
+  int64_t M = 0;
+  double2* tw = nullptr;       // all twiddle tables
+  size_t twN_off = 0;          // omega_N^k, k <= M/2 (real-FFT twist)
+  double* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1
+  double* bwd_tab = nullptr;   // beta rows (low) or delta' rows (high)
+  double* bwd_tab2 = nullptr;  // high: delta rows r = 1..lam_bwd-1
+  double* small = nullptr;     // high: kappa[nkappa] then rho^-j[ntheta]
+  int nkappa = 0, ntheta = 0;
+  size_t table_bytes = 0;
+};
+
+struct Workspace {
+  char* base = nullptr;
+  size_t size = 0;
+  DevStatus* status = nullptr;
+  char* io = nullptr;          // staging for tm_mul_host
+  size_t io_size = 0;
+};
+
+std::mutex g_mu;
+std::map<std::tuple<int, int, uint64_t>, std::shared_ptr<PlanEntry>> g_plans;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return TM_ENOMEM;
+  return e == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+#define TM_CHECK(x)                                   \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) {                          \
+      (void)cudaGetLastError();                       \
+      return cuda_fail(e_);                           \
+    }                                                 \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int64_t limbs_of(uint64_t n) { return int64_t((n + 63) / 64); }
+int64_t out_limbs(int kind, uint64_t n) {
+  if (kind == TM_FULL) return 2 * limbs_of(n);
+  if (kind == TM_LO) return limbs_of(n);
+  return int64_t(n / 64) + 1;
+}
+
+// Limbs of S the carry scan resolves, and where the output window starts.
+void carry_shape(const PlanParams& p, int64_t* nS, int64_t* shift, int64_t* round_bit) {
+  const int64_t nout = out_limbs(p.kind, p.n);
+  if (p.kind == TM_HI) {
+    const int64_t s = (p.N + 3) * int64_t(p.b) - int64_t(p.n);   // Algorithm 3 line 6
+    *shift = s;
+    *round_bit = s - 1;
+    *nS = (s + 64 * nout + 63) / 64 + 1;
+  } else {
+    *shift = 0;
+    *round_bit = -1;
+    *nS = nout;
+  }
+}
+
+size_t workspace_bytes(const PlanParams& p) {
+  const int64_t M = p.N / 2;
+  const size_t region = align_up(size_t(2) * M * sizeof(double2));
+  int64_t nS, sh, rb;
+  carry_shape(p, &nS, &sh, &rb);
+  const size_t carry = align_up(size_t(2) * nS * 8) + 2 * align_up(size_t(nS / 512 + 2));
+  const size_t coeff = align_up(size_t(p.N + 2) * 8);
+  return std::max(region, coeff) + std::max(region, carry) + 256;
+}
+
+int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
+  auto e = std::make_shared<PlanEntry>();
+  int rc = choose_params(kind, n, &e->p);
+  if (rc) return rc;
+  e->M = e->p.N / 2;
+  rc = make_fft_plan(e->M, &e->fft);
+  if (rc) return rc;
+  // twiddle tables: per pass omega_L (and omega_Mp), then omega_N for the twist
+  size_t cnt = 0;
+  for (int i = 0; i < e->fft.npass; ++i) {
+    FftPass& fp = e->fft.pass[i];
+    fp.tw_sub = cnt;
+    cnt += size_t(fp.L);
+    if (fp.Mp) { fp.tw_outer = cnt; cnt += size_t(fp.Mp); }
+  }
+  e->twN_off = cnt;
+  const size_t nN = size_t(e->M / 2 + 1);
+  cnt += nN;
+  TM_CHECK(cudaMalloc(&e->tw, cnt * sizeof(double2)));
+  e->table_bytes += cnt * sizeof(double2);
+  for (int i = 0; i < e->fft.npass; ++i) {
+    const FftPass& fp = e->fft.pass[i];
+    launch_init_twiddles(e->tw + fp.tw_sub, fp.L, fp.L, s);
+    if (fp.Mp) launch_init_twiddles(e->tw + fp.tw_outer, fp.Mp, fp.Mp, s);
+  }
+  launch_init_twiddles(e->tw + e->twN_off, e->p.N, int64_t(nN), s);
+  const int64_t N = e->p.N;
+  const int b = e->p.b;
+  if (kind == TM_LO || kind == TM_HI) {
+    const int rf = e->p.lam_fwd - 1;
+    const int rb = kind == TM_LO ? e->p.lam_bwd - 1 : e->p.lam_bwd;
+    if (rf > 0) {
+      TM_CHECK(cudaMalloc(&e->fwd_tab, size_t(rf) * N * 8));
+      launch_init_maptab(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, s);
+      e->table_bytes += size_t(rf) * N * 8;
+    }
+    if (rb > 0) {
+      TM_CHECK(cudaMalloc(&e->bwd_tab, size_t(rb) * N * 8));
+      launch_init_maptab(e->bwd_tab, kind == TM_LO ? kTabBeta : kTabDeltaPrime, N, b,
+                         kind == TM_LO ? rb : e->p.lam_bwd, s);
+      e->table_bytes += size_t(rb) * N * 8;
+    }
+    if (kind == TM_HI && e->p.lam_bwd > 1) {
+      const int r2 = e->p.lam_bwd - 1;
+      TM_CHECK(cudaMalloc(&e->bwd_tab2, size_t(r2) * N * 8));
+      launch_init_maptab(e->bwd_tab2, kTabDelta, N, b, r2, s);
+      e->table_bytes += size_t(r2) * N * 8;
+    }
+  }
+  if (kind == TM_HI) {
+    // kappa_i = 2^b / rho^(i+1) (eq. 4.4) while it can still reach the rounded
+    // coefficients: i <= 3 + (lg N + 64) / b; theta needs rho^-j, j <= 60/b + 3.
+    int lgN = 0;
+    while ((int64_t(1) << lgN) < N) ++lgN;
+    e->nkappa = int(std::min<int64_t>(N, 3 + (lgN + 64 + b - 1) / b));
+    e->ntheta = int(std::min<int64_t>(N + 1, (60 + b - 1) / b + 3));
+    std::vector<double> host(size_t(e->nkappa + e->ntheta));
+    const double rho = e->p.rho;
+    const double lr = std::log(rho);
+    for (int i = 0; i < e->nkappa; ++i) host[i] = std::exp(b * std::log(2.0) - (i + 1) * lr);
+    for (int j = 0; j < e->ntheta; ++j) host[e->nkappa + j] = std::exp(-j * lr);
+    TM_CHECK(cudaMalloc(&e->small, host.size() * 8));
+    TM_CHECK(cudaMemcpyAsync(e->small, host.data(), host.size() * 8, cudaMemcpyHostToDevice, s));
+    e->table_bytes += host.size() * 8;
+  }
+  TM_CHECK(cudaGetLastError());
+  TM_CHECK(cudaStreamSynchronize(s));
+  (void)dev;
+  *out = e;
+  return TM_OK;
+}
+
+int get_plan(int kind, uint64_t n, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
+  int dev = 0;
+  TM_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_tuple(dev, kind, n);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) { *out = it->second; return TM_OK; }
+  std::shared_ptr<PlanEntry> e;
+  const int rc = build_plan(dev, kind, n, s, &e);
+  if (rc) return rc;
+  g_plans[key] = e;
+  *out = e;
+  return TM_OK;
+}
+
+int get_workspace(cudaStream_t s, size_t bytes, Workspace** out) {
+  int dev = 0;
+  TM_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace& w = g_ws[std::make_pair(dev, s)];
+  if (!w.status) {
+    TM_CHECK(cudaMalloc(&w.status, sizeof(DevStatus)));
+    TM_CHECK(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  }
+  if (bytes && w.size < bytes) {
+    if (w.base) {
+      TM_CHECK(cudaStreamSynchronize(s));
+      TM_CHECK(cudaFree(w.base));
+      w.base = nullptr;
+      w.size = 0;
+    }
+    TM_CHECK(cudaMalloc(&w.base, bytes));
+    w.size = bytes;
+  }
+  *out = &w;
+  return TM_OK;
+}
+
+int get_io(cudaStream_t s, size_t bytes, char** out) {
+  Workspace* w = nullptr;
+  int rc = get_workspace(s, 0, &w);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (w->io_size < bytes) {
+    if (w->io) {
+      TM_CHECK(cudaStreamSynchronize(s));
+      TM_CHECK(cudaFree(w->io));
+      w->io = nullptr;
+      w->io_size = 0;
+    }
+    TM_CHECK(cudaMalloc(&w->io, bytes));
+    w->io_size = bytes;
+  }
+  *out = w->io;
+  return TM_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
+// Enqueues the whole product; `coeff_out` receives the rounded coefficients and
+// stops the pipeline before the carry scan when non-null.
+int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+            cudaStream_t s, const PlanEntry& pe, Workspace& ws, int64_t* coeff_out) {
+  const PlanParams& p = pe.p;
+  const int64_t N = p.N, M = pe.M;
+  const size_t region = std::max(align_up(size_t(2) * M * sizeof(double2)),
+                                 align_up(size_t(N + 2) * 8));
+  double2* R0 = reinterpret_cast<double2*>(ws.base);
+  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
+  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
+  // 1. digits + forward map (Algorithms 1-3, lines 2-3)
+  FwdArgs fa{};
+  fa.u = reinterpret_cast<const unsigned long long*>(u);
+  fa.v = reinterpret_cast<const unsigned long long*>(v);
+  fa.n = n;
+  fa.nlimbs = limbs_of(n);
+  fa.b = p.b;
+  fa.N = N;
+  fa.nd = p.n_digits;
+  fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
+  fa.tab = pe.fwd_tab;
+  fa.kappa = pe.small;
+  fa.nkappa = pe.nkappa;
+  fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
+  fa.ntheta = pe.ntheta;
+  fa.s0 = int64_t(N + 1) * p.b - int64_t(n);
+  fa.X = reinterpret_cast<double*>(R0);
+  fa.theta = theta;
+  launch_fwd(kind, fa, s);
+  // 2. forward FFTs of both operands (complex length M, batch 2)
+  double2* bufs[2] = {R0, R1};
+  int cur = 0;
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    const FftPass& fp = pe.fft.pass[i];
+    PassArgs a{};
+    a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
+    std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
+    a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
+    a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
+    a.batch_stride = M;
+    a.tw_sub = pe.tw + fp.tw_sub;
+    a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+    launch_fft_pass(-1, bufs[cur], bufs[cur ^ 1], a, 2, fp.threads, s);
+    cur ^= 1;
+  }
+  // 3. real-FFT twist, pointwise product, inverse pre-twist
+  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), s);
+  cur ^= 1;
+  // 4. inverse FFT (batch 1)
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    const FftPass& fp = pe.fft.pass[i];
+    PassArgs a{};
+    a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
+    std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
+    a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
+    a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
+    a.batch_stride = M;
+    a.tw_sub = pe.tw + fp.tw_sub;
+    a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+    launch_fft_pass(1, bufs[cur], bufs[cur ^ 1], a, 1, fp.threads, s);
+    cur ^= 1;
+  }
+  // 5. back map + round (Algorithm 1 line 4, Algorithm 2 lines 5-6, Algorithm 3 lines 5-6)
+  double2* wbuf = bufs[cur];
+  long long* cbuf = reinterpret_cast<long long*>(bufs[cur ^ 1]);
+  BackArgs ba{};
+  ba.w = reinterpret_cast<const double*>(wbuf);
+  ba.N = N;
+  ba.b = p.b;
+  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
+  ba.tab = pe.bwd_tab;
+  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  ba.kappa = pe.small;
+  ba.nkappa = pe.nkappa;
+  ba.theta = theta;
+  ba.rho = p.rho;
+  ba.c = cbuf;
+  ba.count = kind == TM_HI ? N + 1 : N;
+  ba.emax_fx = (unsigned long long)std::ldexp(p.e_max, 63);
+  ba.status = ws.status;
+  launch_back(kind, ba, s);
+  if (coeff_out) {
+    TM_CHECK(cudaMemcpyAsync(coeff_out, cbuf, size_t(ba.count) * 8, cudaMemcpyDeviceToDevice, s));
+    TM_CHECK(cudaGetLastError());
+    return TM_OK;
+  }
+  // 6. overlap-add and carries into the output limbs
+  int64_t nS, shift, rbit;
+  carry_shape(p, &nS, &shift, &rbit);
+  char* scratch = reinterpret_cast<char*>(wbuf);   // the inverse output is consumed
+  CarryArgs ca{};
+  ca.c = cbuf;
+  ca.K = kind == TM_HI ? N + 1 : N;
+  ca.b = p.b;
+  ca.kind = kind;
+  ca.nS = nS;
+  ca.round_bit = rbit;
+  ca.shift_bits = shift;
+  ca.nout = out_limbs(kind, n);
+  ca.top_mask = (kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+  ca.out = reinterpret_cast<unsigned long long*>(out);
+  ca.r = reinterpret_cast<unsigned long long*>(scratch);
+  ca.fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
+  ca.cin_block = ca.fblock + align_up(size_t(nS / 512 + 2));
+  launch_carry(ca, s);
+  TM_CHECK(cudaGetLastError());
+  return TM_OK;
+}
+
+int read_status(cudaStream_t s, Workspace& ws, tm_report* rep) {
+  TM_CHECK(cudaStreamSynchronize(s));
+  DevStatus st{};
+  TM_CHECK(cudaMemcpyAsync(&st, ws.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  TM_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  TM_CHECK(cudaStreamSynchronize(s));
+  const int code = st.flags ? TM_EPRECISION : TM_OK;
+  if (rep) {
+    rep->margin = std::ldexp(double(st.margin_fx), -63);
+    rep->status = code;
+  }
+  return code;
+}
+
+void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
+  rep->kind = p.kind;
+  rep->status = TM_OK;
+  rep->b = uint32_t(p.b);
+  rep->N = uint32_t(p.N);
+  rep->n_digits = uint32_t(p.n_digits);
+  rep->lam_fwd = uint32_t(p.lam_fwd);
+  rep->lam_bwd = uint32_t(p.lam_bwd);
+  rep->fft_passes = uint32_t(f.npass);
+  rep->margin = 0.0;
+  rep->e_max = p.e_max;
+  rep->workspace_bytes = workspace_bytes(p);
+  rep->table_bytes = 0;
+}
+
+int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n, void* stream,
+        tm_report* rep, int64_t* coeff_out) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n == 0 || !u || !v || (!out && !coeff_out)) return TM_EINVAL;
+  if (n > TM_MAX_BITS) return TM_ERANGE;
+  const size_t in_bytes = size_t(limbs_of(n)) * 8;
+  if (out) {
+    const size_t ob = size_t(out_limbs(kind, n)) * 8;
+    if (overlaps(out, ob, u, in_bytes) || overlaps(out, ob, v, in_bytes)) return TM_EALIAS;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::shared_ptr<PlanEntry> pe;
+  int rc = get_plan(kind, n, s, &pe);
+  if (rc) return rc;
+  Workspace* ws = nullptr;
+  rc = get_workspace(s, workspace_bytes(pe->p), &ws);
+  if (rc) return rc;
+  rc = enqueue(kind, out, u, v, n, s, *pe, *ws, coeff_out);
+  if (rc) return rc;
+  if (!rep) return TM_OK;
+  fill_plan_report(pe->p, pe->fft, rep);
+  rep->table_bytes = pe->table_bytes;
+  return read_status(s, *ws, rep);
+}
+
+}  // namespace
+}  // namespace tmul
+
+extern "C" {
+
+int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+           void* stream, tm_report* rep) {
+  return tmul::run(kind, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_mul_full(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+                void* stream, tm_report* rep) {
+  return tmul::run(TM_FULL, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_mul_lo(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep) {
+  return tmul::run(TM_LO, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_mul_hi(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep) {
+  return tmul::run(TM_HI, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_coeffs(int kind, int64_t* c_out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
+              void* stream, tm_report* rep) {
+  if (!rep || !c_out) return TM_EINVAL;
+  return tmul::run(kind, nullptr, u, v, n_bits, stream, rep, c_out);
+}
+
+int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint64_t* v_host,
+                uint64_t n_bits, void* stream, tm_report* rep) {
+  if (!out_host || !u_host || !v_host || n_bits == 0) return TM_EINVAL;
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t in_bytes = size_t(tmul::limbs_of(n_bits)) * 8;
+  const size_t out_bytes = size_t(tmul::out_limbs(kind, n_bits)) * 8;
+  char* io = nullptr;
+  int rc = tmul::get_io(s, tmul::align_up(in_bytes) * 2 + tmul::align_up(out_bytes), &io);
+  if (rc) return rc;
+  uint64_t* du = reinterpret_cast<uint64_t*>(io);
+  uint64_t* dv = reinterpret_cast<uint64_t*>(io + tmul::align_up(in_bytes));
+  uint64_t* dout = reinterpret_cast<uint64_t*>(io + 2 * tmul::align_up(in_bytes));
+  if (cudaMemcpyAsync(du, u_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return TM_ECUDA;
+  tm_report local{};
+  rc = tmul::run(kind, dout, du, dv, n_bits, stream, rep ? rep : &local, nullptr);
+  if (rc && rc != TM_EPRECISION) return rc;
+  if (cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return TM_ECUDA;
+  return rc;
+}
+
+int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep) {
+  if (!rep) return TM_EINVAL;
+  tmul::PlanParams p;
+  int rc = tmul::choose_params(kind, n_bits, &p);
+  if (rc) return rc;
+  tmul::FftPlan f;
+  rc = tmul::make_fft_plan(p.N / 2, &f);
+  if (rc) return rc;
+  tmul::fill_plan_report(p, f, rep);
+  return TM_OK;
+}
+
+int tm_stream_status(void* stream, tm_report* rep) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  tmul::Workspace* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    auto it = tmul::g_ws.find(std::make_pair(dev, static_cast<cudaStream_t>(stream)));
+    if (it == tmul::g_ws.end()) {
+      if (rep) { rep->margin = 0; rep->status = TM_OK; }
+      return TM_OK;
+    }
+    ws = &it->second;
+  }
+  return tmul::read_status(static_cast<cudaStream_t>(stream), *ws, rep);
+}
+
+int tm_release(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TM_ECUDA;
+  std::lock_guard<std::mutex> lk(tmul::g_mu);
+  for (auto it = tmul::g_plans.begin(); it != tmul::g_plans.end();) {
+    if (std::get<0>(it->first) == dev) {
+      tmul::PlanEntry& e = *it->second;
+      cudaFree(e.tw); cudaFree(e.fwd_tab); cudaFree(e.bwd_tab); cudaFree(e.bwd_tab2);
+      cudaFree(e.small);
+      it = tmul::g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = tmul::g_ws.begin(); it != tmul::g_ws.end();) {
+    if (it->first.first == dev) {
+      cudaFree(it->second.base);
+      cudaFree(it->second.status);
+      cudaFree(it->second.io);
+      it = tmul::g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return TM_OK;
+}
+
+const char* tm_strerror(int code) {
+  switch (code) {
+    case TM_OK: return "ok";
+    case TM_EINVAL: return "invalid argument";
+    case TM_ENOMEM: return "out of memory";
+    case TM_EPRECISION: return "rounding margin above the error bound: result not trusted";
+    case TM_ETIMEOUT: return "device-side wait timed out";
+    case TM_ECUDA: return "CUDA runtime error";
+    case TM_ERANGE: return "operand size outside the supported range";
+    case TM_EALIAS: return "output overlaps an input";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

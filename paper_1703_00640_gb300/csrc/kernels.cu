@@ -1,0 +1,957 @@
+// Device kernels of the truncated-product pipeline (sm_103a).
+//
+// On GB300 the FP64 pipe is the scarce resource (about 1/37 of the integer
+// rate), so every step that does not need FP64 arithmetic runs on the integer
+// pipe: digit extraction, int -> double conversion (built from the IEEE-754
+// fields), double -> int64 rounding with its distance to the integer, and the
+// carry scan. FP64 is spent on the maps and the FFT.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "../../include/truncmul.h"
+
+namespace tmul {
+
+// ------------------------------------------------------------ constants
+
+constexpr double kC5_1 = 0.30901699437494745;   // cos(2 pi/5)
+constexpr double kC5_2 = -0.8090169943749473;   // cos(4 pi/5)
+constexpr double kS5_1 = 0.9510565162951535;    // sin(2 pi/5)
+constexpr double kS5_2 = 0.5877852522924732;    // sin(4 pi/5)
+constexpr double kC7_1 = 0.6234898018587336;    // cos(2 pi k/7), k = 1, 2, 3
+constexpr double kC7_2 = -0.22252093395631434;
+constexpr double kC7_3 = -0.900968867902419;
+constexpr double kS7_1 = 0.7818314824680298;    // sin(2 pi k/7)
+constexpr double kS7_2 = 0.9749279121818236;
+constexpr double kS7_3 = 0.43388373911755823;
+constexpr double kSqrt3_2 = 0.8660254037844386;
+constexpr double kSqrt1_2 = 0.7071067811865476;
+
+// ------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 w) {  // a * conj(w)
+  return make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// a * (S i): S = -1 gives -i a = (a.y, -a.x); S = +1 gives i a = (-a.y, a.x)
+template <int S>
+__device__ __forceinline__ double2 mul_si(double2 a) {
+  return S < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
+}
+
+// ------------------------------------------- integer <-> double, exactly
+
+// |x| < 2^53: the double with value x, built from its sign, exponent and
+// mantissa fields on the integer pipe.
+__device__ __forceinline__ double i2d_exact(long long x) {
+  const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
+  const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int e = 63 - __clzll(a | 1ull);               // a in [2^e, 2^(e+1)); a = 0 -> e = 0
+  const unsigned long long m = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | m;
+  return a ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// x * 2^k for finite x (result stays normal): add k to the exponent field.
+__device__ __forceinline__ double scale2(double x, int k) {
+  const long long bits = __double_as_longlong(x);
+  return (bits & 0x7FF0000000000000ll) ? __longlong_as_double(bits + ((long long)k << 52)) : x;
+}
+
+// Rounds x (|x| < 2^62) to the nearest integer c (ties to even) and returns the
+// distance |x - c| in units of 2^-63 (<= 2^62). Integer pipe only.
+__device__ __forceinline__ long long round_dist(double x, unsigned long long* dist) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ef = int((bits >> 52) & 0x7FF);
+  const int e = ef - 1023;
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+  unsigned long long q, d;
+  if (e < -1) {                       // |x| < 1/2 (or zero / subnormal)
+    q = 0;
+    const int sh = e + 11;            // x = mant 2^(e-52) = mant 2^(sh-63)
+    d = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+  } else if (e >= 52) {               // already an integer
+    q = mant << (e - 52);
+    d = 0;
+  } else {
+    const int shift = 52 - e;         // 1 .. 53
+    q = mant >> shift;
+    const unsigned long long rem = mant & ((1ull << shift) - 1ull);
+    const unsigned long long half = 1ull << (shift - 1);
+    const bool up = rem > half || (rem == half && (q & 1ull));
+    q += up ? 1ull : 0ull;
+    d = (up ? (1ull << shift) - rem : rem) << (63 - shift);
+  }
+  *dist = d;
+  return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
+// -------------------------------------------------------- table kernels
+
+// tab[m] = exp(-2 pi i m / len), m < count. The angle is reduced to the first
+// half-quadrant with integer arithmetic, then sincospi of an argument in
+// [0, 1/4].
+__global__ void k_init_twiddles(double2* tab, long long len, long long count) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  const long long m4 = 4 * m;
+  const long long q = m4 / len;              // quadrant 0..3
+  long long r = m4 - q * len;                // angle = pi/2 (q + r/len)
+  bool swap = false;
+  if (2 * r > len) { r = len - r; swap = true; }   // use the complement angle
+  double s, c;
+  sincospi((double)r / (2.0 * (double)len), &s, &c);   // angle pi r / (2 len)
+  if (swap) { const double t = s; s = c; c = t; }
+  double cs, sn;                               // cos, sin of 2 pi m / len
+  switch (q) {
+    case 0: cs = c; sn = s; break;
+    case 1: cs = -s; sn = c; break;
+    case 2: cs = -c; sn = -s; break;
+    default: cs = s; sn = -c; break;
+  }
+  tab[m] = make_double2(cs, -sn);
+}
+
+// Coefficient rows of the ring maps (Sections 3.2 and 4.2), tab[(r-1) N + k]:
+//   alpha_{k,r} = k/(k+r) binom((k+r)/N, r) (-2^-b)^r
+//   beta_{k,r}  = binom(-k/N, r) (-2^-b)^r
+//   gamma_{k,r} = k/(k+r) binom(-(k+r)/N, r) (-2^-b)^r
+//   delta_{k,r} = binom(k/N, r) (-2^-b)^r
+// and for the high product's back map the combined rows
+//   delta'_{k,r} = delta_{k,r} - 2^-b delta_{k,r-1}, r = 1..rows (delta_{k,rows} := 0),
+// the coefficients of (1 - 2^-b X) delta*.
+__device__ double binom_scaled(double x, int r, int b) {
+  double acc = 1.0;
+  for (int j = 0; j < r; ++j) acc *= (x - j) / (j + 1);
+  return acc * ((r & 1) ? -1.0 : 1.0) * scale2(1.0, -r * b);
+}
+
+__global__ void k_init_maptab(double* tab, int which, long long N, int b, int rows) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const double dk = (double)k, dN = (double)N;
+  for (int r = 1; r <= rows; ++r) {
+    double v;
+    switch (which) {
+      case kTabAlpha: v = dk / (dk + r) * binom_scaled((dk + r) / dN, r, b); break;
+      case kTabBeta: v = binom_scaled(-dk / dN, r, b); break;
+      case kTabGamma: v = dk / (dk + r) * binom_scaled(-(dk + r) / dN, r, b); break;
+      case kTabDelta: v = binom_scaled(dk / dN, r, b); break;
+      default: {  // delta'
+        const double cur = r < rows ? binom_scaled(dk / dN, r, b) : 0.0;
+        const double prev = binom_scaled(dk / dN, r - 1, b);
+        v = cur - scale2(prev, -b);
+      }
+    }
+    tab[(long long)(r - 1) * N + k] = v;
+  }
+}
+
+// ------------------------------------------------------------ digits
+
+// bits [pos, pos + cnt) of the n-bit integer in `limbs` (cnt <= 32, pos may be
+// negative: bits below 0 read as zero; bits >= n read as zero).
+__device__ __forceinline__ unsigned get_bits(const unsigned long long* limbs, long long nlimbs,
+                                             unsigned long long n, long long pos, int cnt) {
+  if (pos + cnt <= 0) return 0u;
+  int lead = 0;                       // zero bits below position 0
+  if (pos < 0) { lead = int(-pos); cnt -= lead; pos = 0; }
+  if ((unsigned long long)pos >= n) return 0u;
+  const long long i = pos >> 6;
+  const int off = int(pos & 63);
+  unsigned long long lo = __ldg(limbs + i) >> off;
+  if (off + cnt > 64 && i + 1 < nlimbs) lo |= __ldg(limbs + i + 1) << (64 - off);
+  unsigned long long valid = n - (unsigned long long)pos;   // bits below n
+  int keep = cnt;
+  if (valid < (unsigned long long)keep) keep = int(valid);
+  lo &= (keep >= 64) ? ~0ull : ((1ull << keep) - 1ull);
+  return (unsigned)(lo << lead);
+}
+
+// Balanced digit p of x = limbs * 2^shift (Section 5 variant):
+// u_p = d_p - 2^b [d_p >= 2^(b-1)] + [d_(p-1) >= 2^(b-1)], d_p = bits [pb, pb+b) of x.
+// With top_unbalanced, digit p = top keeps d_p + carry (high product, u_N).
+__device__ __forceinline__ int balanced_digit(const unsigned long long* limbs, long long nlimbs,
+                                              unsigned long long n, long long shift, int b,
+                                              long long p, long long top, bool top_unbalanced) {
+  const long long pos = p * b - shift;
+  const unsigned d = get_bits(limbs, nlimbs, n, pos, b);
+  const unsigned half = 1u << (b - 1);
+  const int carry_in = p > 0 ? int(get_bits(limbs, nlimbs, n, pos - 1, 1)) : 0;
+  if (top_unbalanced && p == top) return int(d) + carry_in;
+  return int(d) - ((d >= half) ? (1 << b) : 0) + carry_in;
+}
+
+// ----------------------------------------------------- forward maps
+
+constexpr int kFwdTile = 1024;
+constexpr int kFwdThreads = 256;
+constexpr int kMaxLam = 24;
+
+// Low product: U~ = sum_{r<lam} alpha*_r U (Algorithm 2 line 3; Proposition 3.15),
+// U~_j = U_j + sum_{r=1}^{lam-1} alpha_{(j-r) mod N, r} U_{(j-r) mod N}.
+// Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1 line 2).
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind) {
+  __shared__ double du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  const long long j0 = (long long)blockIdx.x * kFwdTile;
+  const int halo = a.lam > 0 ? a.lam - 1 : 0;
+  const int span = kFwdTile + halo;
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    long long p = j0 - halo + t;                 // digit position, cyclic mod N
+    if (p < 0) p += a.N;
+    double xu = 0.0, xv = 0.0;
+    if (p < a.N && p < a.nd) {
+      xu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false));
+      xv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false));
+    }
+    du[t] = xu;
+    dv[t] = xv;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
+    const long long j = j0 + t;
+    if (j >= a.N) break;
+    double su = du[t + halo], sv = dv[t + halo];
+    for (int r = 1; r < a.lam; ++r) {
+      long long k = j - r;
+      if (k < 0) k += a.N;
+      const double al = __ldg(a.tab + (long long)(r - 1) * a.N + k);
+      su = fma(al, du[t + halo - r], su);
+      sv = fma(al, dv[t + halo - r], sv);
+    }
+    a.X[j] = su;
+    a.X[a.N + j] = sv;
+  }
+}
+
+// High product: gamma-dagger (Algorithm 3 line 3; Proposition 4.18).
+// F' = F mod C: F'_i = F_i + kappa_i F_N (eq. 4.5), then
+// U~_j = sum_{r<lam} gamma_{(j-r) mod N, r} F'_{(j-r) mod N}, and
+// theta = rho^-N F(rho) = sum_j rho^-j F_(N-j).
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a) {
+  __shared__ double du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  __shared__ double topu, topv;
+  const long long j0 = (long long)blockIdx.x * kFwdTile;
+  const int halo = a.lam - 1;
+  const int span = kFwdTile + halo;
+  const long long N = a.N;
+  if (threadIdx.x == 0) {
+    topu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, N, N, true));
+    topv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, N, N, true));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    long long p = j0 - halo + t;
+    if (p < 0) p += N;
+    double xu = 0.0, xv = 0.0;
+    if (p < N) {
+      xu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, p, N, true));
+      xv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true));
+      if (p < a.nkappa) {
+        const double kp = __ldg(a.kappa + p);
+        xu = fma(kp, topu, xu);
+        xv = fma(kp, topv, xv);
+      }
+    }
+    du[t] = xu;
+    dv[t] = xv;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
+    const long long j = j0 + t;
+    if (j >= N) break;
+    double su = du[t + halo], sv = dv[t + halo];
+    for (int r = 1; r < a.lam; ++r) {
+      long long k = j - r;
+      if (k < 0) k += N;
+      const double g = __ldg(a.tab + (long long)(r - 1) * N + k);
+      su = fma(g, du[t + halo - r], su);
+      sv = fma(g, dv[t + halo - r], sv);
+    }
+    a.X[j] = su;
+    a.X[N + j] = sv;
+  }
+  // theta: block 0, two threads (u and v), ntheta terms of rho^-j F_(N-j)
+  if (blockIdx.x == 0 && (threadIdx.x == 0 || threadIdx.x == 32)) {
+    const unsigned long long* src = threadIdx.x == 0 ? a.u : a.v;
+    double th = 0.0;
+    for (int j = a.ntheta - 1; j >= 0; --j) {
+      const long long p = N - j;
+      if (p < 0) continue;
+      const double f = i2d_exact(balanced_digit(src, a.nlimbs, a.n, a.s0, a.b, p, N, true));
+      th = fma(__ldg(a.rho_pow + j), f, th);
+    }
+    a.theta[threadIdx.x == 0 ? 0 : 1] = th;
+  }
+}
+
+void launch_fwd(int kind, const FwdArgs& a, cudaStream_t s) {
+  const unsigned blocks = unsigned((a.N + kFwdTile - 1) / kFwdTile);
+  if (kind == TM_HI)
+    k_fwd_hi<<<blocks, kFwdThreads, 0, s>>>(a);
+  else
+    k_fwd_lo_full<<<blocks, kFwdThreads, 0, s>>>(a, kind);
+}
+
+// ------------------------------------------------------------ FFT pass
+
+// Radix-R DFT of x[0..R) in place, sign S of the exponent (-1 forward).
+template <int R, int S>
+__device__ __forceinline__ void dft(double2* x);
+
+template <>
+__device__ __forceinline__ void dft<2, -1>(double2* x) { const double2 a = x[0]; x[0] = cadd(a, x[1]); x[1] = csub(a, x[1]); }
+template <>
+__device__ __forceinline__ void dft<2, 1>(double2* x) { const double2 a = x[0]; x[0] = cadd(a, x[1]); x[1] = csub(a, x[1]); }
+
+template <int S>
+__device__ __forceinline__ void dft4(double2& x0, double2& x1, double2& x2, double2& x3) {
+  const double2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
+  const double2 t2 = cadd(x1, x3), t3 = mul_si<S>(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+template <>
+__device__ __forceinline__ void dft<4, -1>(double2* x) { dft4<-1>(x[0], x[1], x[2], x[3]); }
+template <>
+__device__ __forceinline__ void dft<4, 1>(double2* x) { dft4<1>(x[0], x[1], x[2], x[3]); }
+
+template <int S>
+__device__ __forceinline__ void dft8(double2* x) {
+  double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<S>(e0, e1, e2, e3);
+  dft4<S>(o0, o1, o2, o3);
+  // omega^1 o1, omega^2 o2, omega^3 o3 with omega = exp(S 2 pi i / 8)
+  const double2 w1 = make_double2((o1.x - S * o1.y) * kSqrt1_2, (o1.y + S * o1.x) * kSqrt1_2);
+  const double2 w2 = mul_si<S>(o2);
+  const double2 w3 = make_double2((-o3.x - S * o3.y) * kSqrt1_2, (S * o3.x - o3.y) * kSqrt1_2);
+  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+  x[1] = cadd(e1, w1); x[5] = csub(e1, w1);
+  x[2] = cadd(e2, w2); x[6] = csub(e2, w2);
+  x[3] = cadd(e3, w3); x[7] = csub(e3, w3);
+}
+template <>
+__device__ __forceinline__ void dft<8, -1>(double2* x) { dft8<-1>(x); }
+template <>
+__device__ __forceinline__ void dft<8, 1>(double2* x) { dft8<1>(x); }
+
+template <int S>
+__device__ __forceinline__ void dft3(double2* x) {
+  const double2 t = cadd(x[1], x[2]);
+  const double2 m = make_double2(fma(t.x, -0.5, x[0].x), fma(t.y, -0.5, x[0].y));
+  const double2 d = csub(x[1], x[2]);
+  const double2 sd = mul_si<S>(make_double2(d.x * kSqrt3_2, d.y * kSqrt3_2));
+  x[0] = cadd(x[0], t);
+  x[1] = cadd(m, sd);
+  x[2] = csub(m, sd);
+}
+template <>
+__device__ __forceinline__ void dft<3, -1>(double2* x) { dft3<-1>(x); }
+template <>
+__device__ __forceinline__ void dft<3, 1>(double2* x) { dft3<1>(x); }
+
+template <int S>
+__device__ __forceinline__ void dft5(double2* x) {
+  const double2 t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+  const double2 d1 = csub(x[1], x[4]), d2 = csub(x[2], x[3]);
+  const double2 x0 = x[0];
+  const double2 a1 = make_double2(fma(kC5_1, t1.x, fma(kC5_2, t2.x, x0.x)), fma(kC5_1, t1.y, fma(kC5_2, t2.y, x0.y)));
+  const double2 a2 = make_double2(fma(kC5_2, t1.x, fma(kC5_1, t2.x, x0.x)), fma(kC5_2, t1.y, fma(kC5_1, t2.y, x0.y)));
+  const double2 b1 = mul_si<S>(make_double2(fma(kS5_1, d1.x, kS5_2 * d2.x), fma(kS5_1, d1.y, kS5_2 * d2.y)));
+  const double2 b2 = mul_si<S>(make_double2(fma(kS5_2, d1.x, -kS5_1 * d2.x), fma(kS5_2, d1.y, -kS5_1 * d2.y)));
+  x[0] = cadd(x0, cadd(t1, t2));
+  x[1] = cadd(a1, b1); x[4] = csub(a1, b1);
+  x[2] = cadd(a2, b2); x[3] = csub(a2, b2);
+}
+template <>
+__device__ __forceinline__ void dft<5, -1>(double2* x) { dft5<-1>(x); }
+template <>
+__device__ __forceinline__ void dft<5, 1>(double2* x) { dft5<1>(x); }
+
+template <int S>
+__device__ __forceinline__ void dft7(double2* x) {
+  const double2 t1 = cadd(x[1], x[6]), t2 = cadd(x[2], x[5]), t3 = cadd(x[3], x[4]);
+  const double2 d1 = csub(x[1], x[6]), d2 = csub(x[2], x[5]), d3 = csub(x[3], x[4]);
+  const double2 x0 = x[0];
+  // a_m = x0 + sum_k cos(2 pi m k / 7) t_k ;  b_m = S i sum_k sin(2 pi m k / 7) d_k
+  const double2 a1 = make_double2(fma(kC7_1, t1.x, fma(kC7_2, t2.x, fma(kC7_3, t3.x, x0.x))),
+                                  fma(kC7_1, t1.y, fma(kC7_2, t2.y, fma(kC7_3, t3.y, x0.y))));
+  const double2 a2 = make_double2(fma(kC7_2, t1.x, fma(kC7_3, t2.x, fma(kC7_1, t3.x, x0.x))),
+                                  fma(kC7_2, t1.y, fma(kC7_3, t2.y, fma(kC7_1, t3.y, x0.y))));
+  const double2 a3 = make_double2(fma(kC7_3, t1.x, fma(kC7_1, t2.x, fma(kC7_2, t3.x, x0.x))),
+                                  fma(kC7_3, t1.y, fma(kC7_1, t2.y, fma(kC7_2, t3.y, x0.y))));
+  // sin(2 pi m k/7): m=1: s1 s2 s3 ; m=2: s2 -s3 -s1 ; m=3: s3 -s1 s2
+  const double2 b1 = mul_si<S>(make_double2(fma(kS7_1, d1.x, fma(kS7_2, d2.x, kS7_3 * d3.x)),
+                                            fma(kS7_1, d1.y, fma(kS7_2, d2.y, kS7_3 * d3.y))));
+  const double2 b2 = mul_si<S>(make_double2(fma(kS7_2, d1.x, fma(-kS7_3, d2.x, -kS7_1 * d3.x)),
+                                            fma(kS7_2, d1.y, fma(-kS7_3, d2.y, -kS7_1 * d3.y))));
+  const double2 b3 = mul_si<S>(make_double2(fma(kS7_3, d1.x, fma(-kS7_1, d2.x, kS7_2 * d3.x)),
+                                            fma(kS7_3, d1.y, fma(-kS7_1, d2.y, kS7_2 * d3.y))));
+  x[0] = cadd(x0, cadd(t1, cadd(t2, t3)));
+  x[1] = cadd(a1, b1); x[6] = csub(a1, b1);
+  x[2] = cadd(a2, b2); x[5] = csub(a2, b2);
+  x[3] = cadd(a3, b3); x[4] = csub(a3, b3);
+}
+template <>
+__device__ __forceinline__ void dft<7, -1>(double2* x) { dft7<-1>(x); }
+template <>
+__device__ __forceinline__ void dft<7, 1>(double2* x) { dft7<1>(x); }
+
+// One Stockham stage of radix R over C sequences of length L held in shared
+// memory: butterfly j reads src[j + t L/R], applies omega_(Ns R)^(t (j mod Ns)),
+// and writes dst[(j/Ns) Ns R + (j mod Ns) + t Ns]; after all stages the result
+// is in natural order.
+template <int R, int S>
+__device__ __forceinline__ void stockham_stage(const double2* src, double2* dst, int L, int C,
+                                               int Ns, const double2* __restrict__ tw) {
+  const int nb = L / R;
+  const int total = C * nb;
+  const int twstep = L / (Ns * R);
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    const int c = g / nb, j = g - c * nb;
+    const double2* s = src + c * L;
+    double2 x[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) x[t] = s[j + t * nb];
+    const int k = j % Ns;
+    if (Ns > 1 && k != 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        const double2 w = __ldg(tw + (long long)k * t * twstep);
+        x[t] = S < 0 ? cmul(x[t], w) : cmulc(x[t], w);
+      }
+    }
+    dft<R, S>(x);
+    double2* d = dst + c * L + (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) d[t * Ns] = x[t];
+  }
+}
+
+template <int S>
+__global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p) {
+  extern __shared__ double2 smem[];
+  const int L = p.L, C = p.C;
+  double2* bufA = smem;
+  double2* bufB = smem + C * L;
+  const long long q0 = (long long)blockIdx.x * C;
+  const long long boff = (long long)blockIdx.y * p.batch_stride;
+  in += boff;
+  out += boff;
+  const int CL = C * L;
+  const bool rowload = p.IS == 1;
+  for (int e = threadIdx.x; e < CL; e += blockDim.x) {
+    int c, j;
+    if (rowload) { c = e / L; j = e - c * L; } else { j = e / C; c = e - j * C; }
+    const long long q = q0 + c;
+    double2 val = make_double2(0.0, 0.0);
+    if (q < p.Q) {
+      const long long qa = q / p.Qc, qc = q - qa * p.Qc;
+      val = in[qa * p.IA + qc * p.IC + (long long)j * p.IS];
+    }
+    bufA[c * L + j] = val;
+  }
+  __syncthreads();
+  int Ns = 1;
+  for (int st = 0; st < p.nstages; ++st) {
+    const int R = p.radix[st];
+    switch (R) {
+      case 2: stockham_stage<2, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      case 3: stockham_stage<3, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      case 4: stockham_stage<4, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      case 5: stockham_stage<5, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      case 7: stockham_stage<7, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      default: stockham_stage<8, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+    }
+    __syncthreads();
+    double2* t = bufA; bufA = bufB; bufB = t;
+    Ns *= R;
+  }
+  const bool rowstore = p.OS == 1;
+  for (int e = threadIdx.x; e < CL; e += blockDim.x) {
+    int c, k;
+    if (rowstore) { c = e / L; k = e - c * L; } else { k = e / C; c = e - k * C; }
+    const long long q = q0 + c;
+    if (q >= p.Q) continue;
+    const long long qa = q / p.Qc, qc = q - qa * p.Qc;
+    double2 val = bufA[c * L + k];
+    if (p.Mp) {
+      const double2 w = __ldg(p.tw_outer + qc * k);
+      val = S < 0 ? cmul(val, w) : cmulc(val, w);
+    }
+    out[qa * p.OA + qc * p.OC + (long long)k * p.OS] = val;
+  }
+}
+
+void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
+                     int threads, cudaStream_t s) {
+  static bool attr_set = false;   // shared memory above 48 KB needs the opt-in
+  if (!attr_set) {
+    const int bytes = 2 * kMaxCL * int(sizeof(double2));
+    cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr_set = true;
+  }
+  const unsigned blocks = unsigned((p.Q + p.C - 1) / p.C);
+  const size_t smem = size_t(2) * p.C * p.L * sizeof(double2);
+  dim3 grid(blocks, batch);
+  if (dir < 0)
+    k_fft_pass<-1><<<grid, threads, smem, s>>>(in, out, p);
+  else
+    k_fft_pass<1><<<grid, threads, smem, s>>>(in, out, p);
+}
+
+// ------------------------------------------------ twist + pointwise product
+
+// Z: FFT_M of z_u = u_even + i u_odd at Z[0..M) and of z_v at Z[M..2M).
+// For each pair (k, M-k): 2X_k = E + T, 2X_(M-k) = conj(E - T) with
+// E = Z_k + conj(Z_(M-k)), T = -i omega_N^k (Z_k - conj(Z_(M-k))) (real FFT of
+// length N from the half-length complex one); P = X^u X^v (the pointwise
+// product of the Convolution step); then the pre-twist of the inverse real
+// FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
+// S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
+__global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, long long M,
+                        const double2* __restrict__ twN, double scale) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k > M / 2) return;
+  const long long km = k == 0 ? 0 : M - k;
+  const double2 w = __ldg(twN + k);
+  double2 Xk[2], Xm[2];
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    const double2 A = Z[o * M + k];
+    const double2 B = cconj(Z[o * M + km]);
+    const double2 E = cadd(A, B);
+    const double2 T = mul_si<-1>(cmul(csub(A, B), w));
+    Xk[o] = cadd(E, T);
+    Xm[o] = cconj(csub(E, T));
+  }
+  const double2 Pk = cmul(Xk[0], Xk[1]);
+  const double2 Pm = cmul(Xm[0], Xm[1]);
+  const double2 Sm = cadd(Pk, cconj(Pm));
+  const double2 Dm = csub(Pk, cconj(Pm));
+  const double2 iwD = mul_si<1>(cmulc(Dm, w));          // i conj(w) D
+  const double2 qk = cadd(Sm, iwD), qm = cconj(csub(Sm, iwD));
+  Q[k] = make_double2(qk.x * scale, qk.y * scale);
+  if (k != 0 && km != k) Q[km] = make_double2(qm.x * scale, qm.y * scale);
+}
+
+void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
+                  cudaStream_t s) {
+  const long long n = M / 2 + 1;
+  k_twist<<<unsigned((n + 255) / 256), 256, 0, s>>>(Z, Q, M, twN, scale);
+}
+
+// ------------------------------------------------ back maps and rounding
+
+constexpr int kBackThreads = 256;
+
+__device__ __forceinline__ void note_distance(unsigned long long d, unsigned long long* bmax) {
+  // block-local max in shared memory, folded into the status at the end
+  atomicMax(bmax, d);
+}
+
+__device__ __forceinline__ void finish_block(unsigned long long* bmax, unsigned* bflags,
+                                             const BackArgs& a) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*bmax) atomicMax(&a.status->margin_fx, *bmax);
+    unsigned f = *bflags;
+    if (*bmax > a.emax_fx) f |= kFlagPrecision;
+    if (f) atomicOr(&a.status->flags, f);
+  }
+}
+
+__device__ __forceinline__ void emit(const BackArgs& a, long long i, double x, bool scaled,
+                                     unsigned long long* bmax) {
+  unsigned long long d;
+  const long long c = round_dist(scaled ? scale2(x, a.b) : x, &d);
+  a.c[i] = c;
+  note_distance(d, bmax);
+}
+
+// Full product (Algorithm 1 line 4): c_i = round(W_i).
+__global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a) {
+  __shared__ unsigned long long bmax;
+  __shared__ unsigned bflags;
+  if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.count;
+       i += (long long)gridDim.x * blockDim.x)
+    emit(a, i, a.w[i], false, &bmax);
+  finish_block(&bmax, &bflags, a);
+}
+
+// Low product (Algorithm 2 lines 5-6; Proposition 3.16): Wbar = sum_{r<lam} beta*_r W~
+// reduced mod A(X) = X^N + 2^-b X - 1, then c_i = round(2^b Wbar_i).
+// Interior positions i >= lam receive no wrapped terms. Head positions i < lam
+// add P_(N+i) and subtract 2^-b P_(N+i-1), where P_(N+m) =
+// sum_{r=m+1}^{lam-1} beta_{N+m-r, r} W~_(N+m-r) are the coefficients of X^(N+m)
+// before reduction (X^(N+m) = X^m - 2^-b X^(m+1) mod A). Requires N >= 2 lam + 2;
+// smaller N take k_back_small.
+__device__ __forceinline__ double beta_at(const BackArgs& a, long long k, int r) {
+  return r == 0 ? 1.0 : __ldg(a.tab + (long long)(r - 1) * a.N + k);
+}
+
+__device__ double lo_overflow(const BackArgs& a, int m) {   // P_(N+m)
+  double acc = 0.0;
+  for (int r = m + 1; r < a.lam; ++r) {
+    const long long k = a.N + m - r;
+    acc = fma(beta_at(a, k, r), a.w[k], acc);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a) {
+  __shared__ unsigned long long bmax;
+  __shared__ unsigned bflags;
+  if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
+  __syncthreads();
+  const long long N = a.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = a.w[i];
+    const int rmax = i < a.lam ? int(i) + 1 : a.lam;
+    for (int r = 1; r < rmax; ++r) acc = fma(beta_at(a, i - r, r), a.w[i - r], acc);
+    if (i < a.lam) {
+      if (i <= a.lam - 2) acc += lo_overflow(a, int(i));
+      if (i >= 1) acc = fma(-scale2(1.0, -a.b), lo_overflow(a, int(i) - 1), acc);
+    }
+    unsigned long long d;
+    const long long c = round_dist(scale2(acc, a.b), &d);
+    a.c[i] = c;
+    note_distance(d, &bmax);
+    if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(&bflags, kFlagC0);
+  }
+  finish_block(&bmax, &bflags, a);
+}
+
+// High product (Algorithm 3 lines 4-6; Proposition 4.19 with Remark 4.20 for
+// large N): H = sum_{r<lam} delta*_r W~ reduced mod C(X), whose X^N = sum_i
+// kappa_i X^i (eq. 4.4), and then by eq. (4.7)
+//   J_i = H_i - 2^-b H_(i-1) - psi kappa_i (i < N),  J_N = -2^-b H_(N-1) + psi,
+// with psi = theta_U theta_V: for N > 64 the other terms of eq. (4.6) lie far
+// below the last bit of psi. Interior i >= lam + nkappa: one stencil with the
+// combined rows delta' (tab). Head i < lam + nkappa and J_N: warp 0 of block 0.
+__device__ __forceinline__ double delta_at(const BackArgs& a, long long k, int r) {
+  return r == 0 ? 1.0 : __ldg(a.tab2 + (long long)(r - 1) * a.N + k);
+}
+
+__device__ double hi_H(const BackArgs& a, long long i, const double* P) {   // reduced H_i
+  double acc = 0.0;
+  const int rmax = i < a.lam ? int(i) + 1 : a.lam;
+  for (int r = 0; r < rmax; ++r) acc = fma(delta_at(a, i - r, r), a.w[i - r], acc);
+  // wrapped terms: P_(N+m) kappa_(i-m), m <= lam-2, 0 <= i-m < nkappa
+  for (int m = 0; m <= a.lam - 2; ++m) {
+    const long long t = i - m;
+    if (t >= 0 && t < a.nkappa) acc = fma(__ldg(a.kappa + t), P[m], acc);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a) {
+  __shared__ unsigned long long bmax;
+  __shared__ unsigned bflags;
+  __shared__ double P[kMaxLam];
+  __shared__ double Hh[kMaxLam + 64 + 1];
+  if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
+  __syncthreads();
+  const long long N = a.N;
+  const int head = a.lam + a.nkappa;     // J_i for i < head computed by the head warp
+  const double twmb = scale2(1.0, -a.b);
+  for (long long i = head + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = a.w[i];
+    for (int r = 1; r <= a.lam; ++r)
+      acc = fma(__ldg(a.tab + (long long)(r - 1) * N + (i - r)), a.w[i - r], acc);
+    unsigned long long d;
+    a.c[i] = round_dist(scale2(acc, a.b), &d);
+    note_distance(d, &bmax);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double psi = a.theta[0] * a.theta[1];
+    // overflow coefficients P_(N+m), m = 0..lam-2
+    for (int m = lane; m <= a.lam - 2; m += 32) {
+      double acc = 0.0;
+      for (int r = m + 1; r < a.lam; ++r) {
+        const long long k = N + m - r;
+        acc = fma(delta_at(a, k, r), a.w[k], acc);
+      }
+      P[m] = acc;
+    }
+    __syncwarp();
+    for (int i = lane; i < head; i += 32) Hh[i] = hi_H(a, i, P);
+    __syncwarp();
+    for (int i = lane; i < head; i += 32) {
+      double J = Hh[i];
+      if (i >= 1) J = fma(-twmb, Hh[i - 1], J);
+      if (i < a.nkappa) J = fma(-psi, __ldg(a.kappa + i), J);
+      unsigned long long d;
+      const long long c = round_dist(scale2(J, a.b), &d);
+      a.c[i] = c;
+      note_distance(d, &bmax);
+      if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(&bflags, kFlagC0);
+    }
+    if (lane == 0) {   // J_N = -2^-b H_(N-1) + psi (H_(N-1) is an interior value)
+      double H = 0.0;
+      for (int r = 0; r < a.lam; ++r) H = fma(delta_at(a, N - 1 - r, r), a.w[N - 1 - r], H);
+      const double J = fma(-twmb, H, psi);
+      unsigned long long d;
+      a.c[N] = round_dist(scale2(J, a.b), &d);
+      note_distance(d, &bmax);
+    }
+  }
+  finish_block(&bmax, &bflags, a);
+}
+
+// Small transforms (any N): one thread evaluates the back map from the
+// definitions, reducing the shifted terms modulo A or C from the top degree
+// down, and for the high product psi by eq. (4.6) in the scaled form
+// psi = (theta - rho^-2N H(rho)) / (1 - N 2^b rho^-(N+1)).
+constexpr int kSmallMax = 160;
+__global__ void k_back_small(BackArgs a, int kind) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double P[kSmallMax + kMaxLam];
+  const long long N = a.N;
+  const int tot = int(N) + a.lam - 1;
+  for (int i = 0; i < tot; ++i) P[i] = 0.0;
+  for (long long k = 0; k < N; ++k)
+    for (int r = 0; r < a.lam; ++r) {
+      const double co = kind == TM_LO ? beta_at(a, k, r) : delta_at(a, k, r);
+      P[k + r] = fma(co, a.w[k], P[k + r]);
+    }
+  const double twmb = scale2(1.0, -a.b);
+  for (int j = tot - 1; j >= N; --j) {       // reduce X^j, j >= N
+    const double pj = P[j];
+    P[j] = 0.0;
+    const int m = j - int(N);
+    if (kind == TM_LO) {                     // X^(N+m) = X^m - 2^-b X^(m+1)
+      P[m] += pj;
+      P[m + 1] = fma(-twmb, pj, P[m + 1]);
+    } else {                                 // X^(N+m) = X^m sum_i kappa_i X^i
+      for (int i = 0; i < a.nkappa && i < N; ++i) P[m + i] = fma(__ldg(a.kappa + i), pj, P[m + i]);
+    }
+  }
+  unsigned long long bm = 0, d;
+  unsigned flags = 0;
+  if (kind == TM_LO) {
+    for (long long i = 0; i < N; ++i) {
+      const long long c = round_dist(scale2(P[i], a.b), &d);
+      a.c[i] = c;
+      bm = d > bm ? d : bm;
+      if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) flags |= kFlagC0;
+    }
+  } else {
+    const double rho = a.rho;
+    // rho^-2N H(rho) = sum_i H_i rho^(i - 2N), by Horner on rho^-1 from the top
+    // h = sum_i H_i rho^(i-(N-1)) by Horner in 1/rho; rho^-2N H(rho) = h rho^-(N+1)
+    double h = 0.0;
+    const double ir = 1.0 / rho;
+    for (long long i = 0; i < N; ++i) h = fma(h, ir, P[i]);
+    const double rnp1 = pow(ir, double(N + 1));
+    const double psi = (a.theta[0] * a.theta[1] - h * rnp1) /
+                       (1.0 - double(N) * scale2(1.0, a.b) * rnp1);
+    for (long long i = 0; i <= N; ++i) {
+      double J = i < N ? P[i] : 0.0;
+      if (i >= 1) J = fma(-twmb, P[i - 1], J);
+      if (i < N) {
+        if (i < a.nkappa) J = fma(-psi, __ldg(a.kappa + i), J);
+      } else {
+        J += psi;
+      }
+      const long long c = round_dist(scale2(J, a.b), &d);
+      a.c[i] = c;
+      bm = d > bm ? d : bm;
+      if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) flags |= kFlagC0;
+    }
+  }
+  if (bm) atomicMax(&a.status->margin_fx, bm);
+  if (bm > a.emax_fx) flags |= kFlagPrecision;
+  if (flags) atomicOr(&a.status->flags, flags);
+}
+
+void launch_back(int kind, const BackArgs& a, cudaStream_t s) {
+  const long long n = a.count;
+  unsigned blocks = unsigned((n + kBackThreads - 1) / kBackThreads);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks == 0) blocks = 1;
+  if (kind == TM_FULL) {
+    k_back_full<<<blocks, kBackThreads, 0, s>>>(a);
+  } else if (a.N <= 64 || a.N < 2 * a.lam + a.nkappa + 2) {
+    k_back_small<<<1, 32, 0, s>>>(a, kind);
+  } else if (kind == TM_LO) {
+    k_back_lo<<<blocks, kBackThreads, 0, s>>>(a);
+  } else {
+    k_back_hi<<<blocks, kBackThreads, 0, s>>>(a);
+  }
+}
+
+// ------------------------------------------------------------ carry scan
+
+// S = sum_i t_i 2^(p_i) with signed 54-bit terms t_i: c_i at i b (full, high),
+// c_i at (i-1) b for i >= 1 and c_0 / 2^b at 0 (low, Algorithm 2 line 6), plus
+// 2^(s-1) for the high product's round(t) (Algorithm 3 line 7, half up).
+// A_L = sum over terms starting in limb L of t_i 2^(p_i - 64 L) (int128);
+// r_L = (A_L mod 2^64) + floor(A_(L-1) / 2^64) lies in (-2^60, 2^64 + 2^60), so
+// the carry into each limb is -1, 0 or +1 and each limb acts on it through a
+// 3-entry function f_L(cin) = floor((r_L + cin) / 2^64). The scan composes
+// these functions: per block, over blocks, then applied per limb.
+constexpr int kCarryThreads = 512;
+
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) {
+  return a >= 0 ? (a + b - 1) / b : -((-a) / b);
+}
+
+__device__ __int128 limb_sum(const CarryArgs& a, long long L) {
+  if (L < 0) return 0;
+  __int128 acc = 0;
+  const long long base = 64 * L;
+  const long long off = a.kind == TM_LO ? -a.b : 0;          // p_i = i b + off
+  long long ilo = ceil_div_ll(base - off, a.b), ihi = ceil_div_ll(base + 64 - off, a.b);
+  if (a.kind == TM_LO) {
+    if (ilo < 1) ilo = 1;
+    if (L == 0) acc += (__int128)(a.c[0] >> a.b);
+  }
+  if (ilo < 0) ilo = 0;
+  if (ihi > a.K) ihi = a.K;
+  for (long long i = ilo; i < ihi; ++i) {
+    const int sh = int(i * a.b + off - base);
+    acc += (__int128)((unsigned __int128)(__int128)a.c[i] << sh);
+  }
+  if (a.round_bit >= 0 && (a.round_bit >> 6) == L)
+    acc += (__int128)((unsigned __int128)1 << (a.round_bit & 63));
+  return acc;
+}
+
+// f encoded as 3 x 2 bits: bits [2t, 2t+2) hold f(t-1) + 1, t = 0, 1, 2.
+__device__ __forceinline__ unsigned carry_fn(__int128 r) {
+  unsigned f = 0;
+  for (int t = 0; t < 3; ++t) {
+    const __int128 x = r + (t - 1);
+    const long long co = (long long)(x >> 64);               // -1, 0 or 1
+    f |= unsigned(co + 1) << (2 * t);
+  }
+  return f;
+}
+__device__ __forceinline__ int apply_fn(unsigned f, int cin) { return int((f >> (2 * (cin + 1))) & 3u) - 1; }
+// (g o f)(c) = g(f(c))
+__device__ __forceinline__ unsigned compose(unsigned g, unsigned f) {
+  unsigned h = 0;
+  for (int t = 0; t < 3; ++t) h |= unsigned(apply_fn(g, apply_fn(f, t - 1)) + 1) << (2 * t);
+  return h;
+}
+constexpr unsigned kIdentityFn = 0u | (1u << 2) | (2u << 4);
+
+// inclusive scan of functions in shared memory: s[i] = f_i o ... o f_0
+__device__ void block_compose_scan(unsigned* s, int n) {
+  for (int d = 1; d < n; d <<= 1) {
+    unsigned v = 0;
+    const int i = threadIdx.x;
+    if (i < n && i >= d) v = compose(s[i], s[i - d]);
+    __syncthreads();
+    if (i < n && i >= d) s[i] = v;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a) {
+  __shared__ unsigned fs[kCarryThreads];
+  const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
+  unsigned f = kIdentityFn;
+  if (L < a.nS) {
+    const __int128 AL = limb_sum(a, L), Ap = limb_sum(a, L - 1);
+    const __int128 r = (__int128)(unsigned long long)AL + (Ap >> 64);
+    a.r[2 * L] = (unsigned long long)r;
+    a.r[2 * L + 1] = (unsigned long long)(r >> 64);
+    f = carry_fn(r);
+  }
+  fs[threadIdx.x] = f;
+  __syncthreads();
+  block_compose_scan(fs, kCarryThreads);
+  if (threadIdx.x == 0) a.fblock[blockIdx.x] = (unsigned char)fs[kCarryThreads - 1];
+}
+
+// carry into every block: cin_0 = 0, cin_(B+1) = F_B(cin_B)
+__global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a, long long nblocks) {
+  __shared__ unsigned fs[1024];
+  const long long per = (nblocks + 1023) / 1024;
+  const long long b0 = threadIdx.x * per;
+  unsigned f = kIdentityFn;
+  for (long long i = b0; i < b0 + per && i < nblocks; ++i) f = compose(a.fblock[i], f);
+  fs[threadIdx.x] = f;
+  __syncthreads();
+  block_compose_scan(fs, 1024);
+  const unsigned before = threadIdx.x ? fs[threadIdx.x - 1] : kIdentityFn;
+  int cin = apply_fn(before, 0);
+  for (long long i = b0; i < b0 + per && i < nblocks; ++i) {
+    a.cin_block[i] = (unsigned char)(cin + 1);
+    cin = apply_fn(a.fblock[i], cin);
+  }
+}
+
+__device__ __forceinline__ unsigned long long resolved(const CarryArgs& a, long long L, int cin) {
+  if (L >= a.nS) return 0ull;
+  const __int128 r = (__int128)(((unsigned __int128)a.r[2 * L + 1] << 64) | a.r[2 * L]);
+  return (unsigned long long)(r + cin);
+}
+
+__global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a) {
+  __shared__ unsigned fs[kCarryThreads];
+  const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
+  unsigned f = kIdentityFn;
+  __int128 r = 0;
+  if (L < a.nS) {
+    r = (__int128)(((unsigned __int128)a.r[2 * L + 1] << 64) | a.r[2 * L]);
+    f = carry_fn(r);
+  }
+  fs[threadIdx.x] = f;
+  __syncthreads();
+  block_compose_scan(fs, kCarryThreads);
+  const int cinB = int(a.cin_block[blockIdx.x]) - 1;
+  const unsigned before = threadIdx.x ? fs[threadIdx.x - 1] : kIdentityFn;
+  const int cin = apply_fn(before, cinB);
+  if (L >= a.nS) return;
+  const unsigned long long limb = (unsigned long long)(r + cin);
+  const long long sw = a.shift_bits >> 6;
+  const int sb = int(a.shift_bits & 63);
+  const long long j = L - sw;                // output limb whose low part comes from L
+  if (j < 0 || j >= a.nout) return;
+  unsigned long long o = limb >> sb;
+  if (sb) {
+    const int cnext = apply_fn(f, cin);
+    o |= resolved(a, L + 1, cnext) << (64 - sb);
+  }
+  if (j == a.nout - 1) o &= a.top_mask;
+  a.out[j] = o;
+}
+
+void launch_carry(const CarryArgs& a, cudaStream_t s) {
+  const long long nblocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
+  k_carry_local<<<unsigned(nblocks), kCarryThreads, 0, s>>>(a);
+  k_carry_blocks<<<1, 1024, 0, s>>>(a, nblocks);
+  k_carry_apply<<<unsigned(nblocks), kCarryThreads, 0, s>>>(a);
+}
+
+// ------------------------------------------------------------ tables
+
+void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_init_twiddles<<<unsigned((count + 255) / 256), 256, 0, s>>>(tab, len, count);
+}
+
+void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s) {
+  if (rows <= 0) return;
+  k_init_maptab<<<unsigned((N + 255) / 256), 256, 0, s>>>(tab, which, N, b, rows);
+}
+
+}  // namespace tmul

@@ -1,0 +1,99 @@
+// Kernel parameter blocks and launcher declarations shared by kernels.cu and api.cu.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace tmul {
+
+// Device-side outcome of asynchronous calls on one workspace.
+struct DevStatus {
+  unsigned long long margin_fx;  // largest rounding distance, units of 2^-63
+  unsigned int flags;            // kFlagPrecision | kFlagC0
+  unsigned int pad;
+};
+constexpr unsigned kFlagPrecision = 1u;  // a distance above the plan's bound
+constexpr unsigned kFlagC0 = 2u;         // 2^b does not divide c_0
+
+// Pass descriptor as seen by the FFT kernel (plan.h's FftPass plus pointers).
+struct PassArgs {
+  int L, nstages, C;
+  int radix[kMaxStages];
+  long long Q, Qc, IA, IC, IS, OA, OC, OS, Mp;
+  long long batch_stride;        // complex elements between batch entries
+  const double2* tw_sub;         // omega_L^k
+  const double2* tw_outer;       // omega_Mp^m (or nullptr)
+};
+
+// Digit unpack + forward map parameters.
+struct FwdArgs {
+  const unsigned long long* u;
+  const unsigned long long* v;
+  unsigned long long n;          // operand bits
+  long long nlimbs;
+  int b;
+  long long N;                   // transform length (real)
+  long long nd;                  // digits per operand
+  int lam;                       // map terms (0 for the full product)
+  const double* tab;             // (lam-1) x N coefficient rows, r = 1..lam-1
+  const double* kappa;           // high: kappa_i = 2^b / rho^(i+1), i < nkappa
+  int nkappa;
+  const double* rho_pow;         // high: rho^-j, j < ntheta
+  int ntheta;
+  long long s0;                  // high: (N+1) b - n
+  double* X;                     // out: u at X[0..N), v at X[N..2N)
+  double* theta;                 // high: theta_U, theta_V
+};
+
+struct BackArgs {
+  const double* w;               // N real values (inverse FFT output)
+  long long N;
+  int b;
+  int lam;
+  const double* tab;             // low: beta rows r=1..lam-1; high: delta' rows r=1..lam
+  const double* tab2;            // high: plain delta rows r=1..lam-1 (head positions)
+  const double* kappa;
+  int nkappa;
+  const double* theta;           // high: theta_U, theta_V
+  double rho;
+  long long* c;                  // out: rounded coefficients
+  long long count;               // number of c values (N, N+1 or L)
+  unsigned long long emax_fx;    // bound, units of 2^-63
+  DevStatus* status;
+};
+
+struct CarryArgs {
+  const long long* c;
+  long long K;                   // number of coefficients
+  int b;
+  int kind;
+  long long nS;                  // limbs of S that are resolved
+  long long round_bit;           // high: bit s-1 receives +1 (round half up); else -1
+  long long shift_bits;          // output starts at this bit of S
+  long long nout;                // output limbs
+  unsigned long long top_mask;   // mask of the last output limb
+  unsigned long long* out;
+  unsigned long long* r;         // scratch: 2 x nS words (r_L as 128-bit)
+  unsigned char* fblock;         // scratch: per-block carry functions
+  unsigned char* cin_block;      // scratch: per-block carry-in (+1 encoded)
+};
+
+// table initialisation
+// tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
+void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
+void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s);
+
+// pipeline stages
+void launch_fwd(int kind, const FwdArgs& a, cudaStream_t s);
+void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
+                     int threads, cudaStream_t s);
+void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
+                  cudaStream_t s);
+void launch_back(int kind, const BackArgs& a, cudaStream_t s);
+void launch_carry(const CarryArgs& a, cudaStream_t s);
+
+// map table selectors for launch_init_maptab
+constexpr int kTabAlpha = 0, kTabBeta = 1, kTabGamma = 2, kTabDelta = 3, kTabDeltaPrime = 4;
+
+}  // namespace tmul

@@ -1,0 +1,332 @@
+// Parameter selection for the three products and the FFT pass layout.
+//
+// Digits are balanced, |U_i| <= 2^(b-1) (the variant of Section 5); the high
+// product's top digit keeps the final carry, 0 <= U_N <= 2^b. A candidate
+// (b, N) must satisfy the hypotheses of Theorem 2.1 (cyclic length >= 2 N_d - 1
+// with N_d b >= n + 1, so no digit carries out of the top), Theorem 2.2
+// (N b >= n, N >= 3) or Theorem 2.3 ((N+1) b >= n + lg N + 2, N >= 3), and a
+// worst-case FP64 error bound: (bound on |W~_i - (exact)_i|) x 2^b <= kTarget
+// for the truncated products (Theorems 2.2 / 2.3 need < 1/2 after scaling by
+// 2^b), or the bound itself <= kTarget for the full product. The convolution
+// term is ||x||_2 ||y||_2 eta with eta = (1+u)^3K (1+sqrt5 u)^(3K+1) (1+tau)^3K - 1,
+// the explicit FFT bound the paper cites in Section 2.1 (Brent-Zimmermann,
+// Thm 3.6), K counting radix-2-equivalent levels of one transform. Map growth
+// and truncation follow Lemmas 3.5, 3.8-3.11 and 4.7-4.11. Lengths are
+// 2^a * m with m in kOddParts (Section 5 uses 2^e2 3^e3 5^e5 7^e7 with odd part
+// below 200); the shortest length meeting the bound wins, ties to the larger b.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/truncmul.h"
+
+namespace tmul {
+namespace {
+
+constexpr double kU = 1.0 / 9007199254740992.0;  // 2^-53
+constexpr double kTau = 2.0 * kU;                // twiddle table error
+constexpr double kTarget = 0.45;
+constexpr int kBMin = 4, kBMax = 24;
+constexpr double kSpan = 1.25;
+const int kOddParts[] = {1, 3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49, 63, 75, 81, 105, 125,
+                         135, 147, 175, 189};
+
+int ceil_lg(int64_t x) {  // ceil(log2 x), x >= 1
+  int k = 0;
+  while ((int64_t(1) << k) < x) ++k;
+  return k;
+}
+
+int odd_factor_count(int64_t L) {
+  int c = 0;
+  for (int p : {3, 5, 7})
+    while (L % p == 0) { L /= p; ++c; }
+  return c;
+}
+
+double eta_conv(int64_t L) {
+  const double K = ceil_lg(L) + 2.0 * odd_factor_count(L) + 2.0;
+  return std::expm1(3 * K * std::log1p(kU) + (3 * K + 1) * std::log1p(std::sqrt(5.0) * kU) +
+                    3 * K * std::log1p(kTau));
+}
+
+// |gamma_{k,r}| <= 2^-rb exp((r-1) H_r / N): the proof of Lemma 4.7 with
+// (k+r)/N + j <= (j+1)(1 + (r-1)/((j+1) N)) in place of the final estimate.
+double gamma_bound(int r, int b, int64_t N) {
+  if (r == 0) return 1.0;
+  double h = 0;
+  for (int j = 1; j <= r; ++j) h += 1.0 / j;
+  return std::ldexp(std::exp((r - 1) * h / double(N)), -r * b);
+}
+
+double gamma_tail(int lam, int b, int64_t N) {
+  double s = 0;
+  for (int r = lam; r < lam + 64; ++r) s += gamma_bound(r, b, N);
+  return s;
+}
+
+// Lemma 3.10 tail: (16/15) 2^(-lam b) <= u/4.
+int lambda_alpha(int b) {
+  int lam = 1;
+  while (16.0 / 15.0 * std::ldexp(1.0, -lam * b) > kU / 4) ++lam;
+  return lam;
+}
+
+// Tails of beta* / delta*: sum_{r>=lam} q^r with q = (1 + g) 2^-b, where
+// ||X H|| <= (1 + g) ||H|| is the growth of one multiplication by X modulo A
+// (g = 2^-b, inside the proof of Lemma 3.9) or C (g = 2^(1-b), Lemma 4.9).
+int lambda_geometric(int b, double g) {
+  const double q = (1.0 + g) * std::ldexp(1.0, -b);
+  int lam = 1;
+  while (std::pow(q, lam) / (1.0 - q) > kU / 4) ++lam;
+  return lam;
+}
+
+int lambda_gamma(int b, int64_t N) {
+  int lam = 1;
+  while (gamma_tail(lam, b, N) > kU / 4) ++lam;
+  return lam;
+}
+
+// rho of Lemma 4.2 by Newton's method from 2^b on y = rho / 2^b:
+// y^N (y - 1) + 2^(-N b) = 0.
+double rho_of(int64_t N, int b) {
+  const double eps = std::ldexp(1.0, -int(std::min<int64_t>(N * b, 2000)));
+  double y = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    const double yN1 = std::pow(y, double(N - 1));
+    const double f = yN1 * y * (y - 1.0) + eps;
+    const double df = yN1 * ((N + 1) * y - N);
+    const double yn = y - f / df;
+    if (yn == y) break;
+    y = yn;
+  }
+  return std::ldexp(y, b);
+}
+
+bool hi_hypothesis(uint64_t n, int b, int64_t N) {
+  return N >= 3 && uint64_t(N + 1) * b >= n + ceil_lg(N) + 2;
+}
+
+int64_t full_digit_count(uint64_t n, int b) {
+  return std::max<int64_t>(2, int64_t((n + 1 + b - 1) / b));
+}
+
+struct Bound { double E; int lf, lb; };
+
+Bound bound_lo(int b, int64_t N) {
+  const int la = lambda_alpha(b), lb = lambda_geometric(b, std::ldexp(1.0, -b));
+  const double eta = eta_conv(N);
+  const double g = 1.0 / (1.0 - std::ldexp(1.0, -b));           // alpha* growth
+  const double S = g * std::ldexp(1.0, b - 1) * std::sqrt(double(N));  // ||U~||_2
+  const double MW = S * S;                                       // |W~_i| bound
+  const double din = ((la + 2) * kU + 16.0 / 15.0 * std::ldexp(1.0, -la * b)) * g *
+                     std::ldexp(1.0, b - 1);                      // error of one U~_i
+  const double Ein = 2.0 * std::sqrt(double(N)) * din * S * (1.0 + eta);
+  const double q = (1.0 + std::ldexp(1.0, -b)) * std::ldexp(1.0, -b);
+  const double A = 1.0 / (1.0 - q);                              // beta* growth
+  const double tail = std::pow(q, lb) / (1.0 - q);
+  const double EW = eta * MW + Ein;
+  const double E = std::ldexp(A * EW + (lb + 3) * kU * A * MW + tail * MW, b);
+  return {E, la, lb};
+}
+
+Bound bound_hi(int b, int64_t N) {
+  const double rho = rho_of(N, b);
+  const int lg = lambda_gamma(b, N), ld = lambda_geometric(b, std::ldexp(1.0, 1 - b));
+  const double eta = eta_conv(N);
+  double g = 0;
+  for (int r = 0; r < 80; ++r) g += gamma_bound(r, b, N);       // gamma* growth
+  const double kappa0 = std::ldexp(1.0, b) / rho;
+  const double K2 = kappa0 / std::sqrt(1.0 - 1.0 / (rho * rho));  // ||kappa||_2
+  const double S = g * (std::ldexp(1.0, b - 1) * std::sqrt(double(N)) + std::ldexp(K2, b));
+  const double MW = S * S;
+  const double mF = std::ldexp(1.0, b - 1) + std::ldexp(kappa0, b);  // |(F mod C)_i|
+  const double din = ((lg + 4) * kU + gamma_tail(lg, b, N)) * g * mF;
+  const double Ein = 2.0 * std::sqrt(double(N)) * din * S * (1.0 + eta);
+  const double T = std::ldexp(1.0, b) + std::ldexp(1.0, b - 1) / (rho - 1.0);  // |theta|
+  const int J = (60 + b - 1) / b + 1;
+  const double Etheta = (2 * (J + 2) + 1) * kU * T * T;
+  const double q = (1.0 + std::ldexp(1.0, 1 - b)) * std::ldexp(1.0, -b);
+  const double A = 1.01 * (1.0 + std::ldexp(1.0, -b)) / (1.0 - q);  // delta-dagger growth
+  const double tail = std::pow(q, ld) / (1.0 - q);
+  const double EW = eta * MW + Ein;
+  const double E =
+      std::ldexp(A * (EW + Etheta) + (ld + 4) * kU * A * (MW + T * T) + tail * MW, b);
+  return {E, lg, ld};
+}
+
+double bound_full(uint64_t n, int b, int64_t L) {
+  const double MW = std::ldexp(double(full_digit_count(n, b)), 2 * b - 2);
+  return eta_conv(L) * MW + 2.0 * kU * MW;
+}
+
+std::vector<int64_t> candidate_lengths(int64_t x) {
+  x = std::max<int64_t>(4, x);
+  const int64_t first = smooth_at_least(x);
+  const int64_t top = std::max<int64_t>(first, int64_t(kSpan * double(x)));
+  std::vector<int64_t> out;
+  for (int m : kOddParts) {
+    int64_t L = 2 * int64_t(m);
+    while (L < x) L *= 2;
+    for (; L <= top; L *= 2) out.push_back(L);
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
+}
+
+}  // namespace
+
+bool is_valid_length(int64_t L) {
+  if (L < 4 || L % 2) return false;
+  while (L % 2 == 0) L /= 2;
+  for (int m : kOddParts)
+    if (L == m) return true;
+  return false;
+}
+
+int64_t smooth_at_least(int64_t x) {
+  x = std::max<int64_t>(4, x);
+  int64_t best = -1;
+  for (int m : kOddParts) {
+    int64_t L = 2 * int64_t(m);
+    while (L < x) L *= 2;
+    if (best < 0 || L < best) best = L;
+  }
+  return best;
+}
+
+int choose_params(int kind, uint64_t n, PlanParams* out) {
+  if (n == 0 || (kind != TM_FULL && kind != TM_LO && kind != TM_HI)) return TM_EINVAL;
+  if (n > TM_MAX_BITS) return TM_ERANGE;
+  bool found = false;
+  PlanParams best;
+  for (int b = kBMin; b <= kBMax; ++b) {
+    int64_t lmin;
+    if (kind == TM_LO) {
+      lmin = std::max<int64_t>(3, int64_t((n + b - 1) / b));
+    } else if (kind == TM_HI) {
+      lmin = std::max<int64_t>(3, int64_t((n + 2 + b - 1) / b) - 1);
+      while (!hi_hypothesis(n, b, lmin)) ++lmin;
+    } else {
+      lmin = 2 * full_digit_count(n, b) - 1;
+    }
+    for (int64_t N : candidate_lengths(lmin)) {
+      if (kind == TM_HI && !hi_hypothesis(n, b, N)) continue;
+      double E;
+      int lf = 0, lb = 0;
+      int64_t nd;
+      if (kind == TM_LO) {
+        Bound B = bound_lo(b, N);
+        E = B.E; lf = B.lf; lb = B.lb; nd = N;
+      } else if (kind == TM_HI) {
+        Bound B = bound_hi(b, N);
+        E = B.E; lf = B.lf; lb = B.lb; nd = N + 1;
+      } else {
+        E = bound_full(n, b, N);
+        nd = full_digit_count(n, b);
+      }
+      if (E <= kTarget) {
+        if (!found || N < best.N || (N == best.N && b > best.b)) {
+          best.kind = kind; best.n = n; best.b = b; best.N = N; best.n_digits = nd;
+          best.lam_fwd = lf; best.lam_bwd = lb; best.e_max = E;
+          best.rho = kind == TM_HI ? rho_of(N, b) : 0.0;
+          found = true;
+        }
+        break;
+      }
+    }
+  }
+  if (!found) return TM_ERANGE;
+  *out = best;
+  return TM_OK;
+}
+
+// ---------------------------------------------------------------- FFT plan
+
+namespace {
+
+void radices_of(int L, FftPass* p) {
+  p->nstages = 0;
+  int rest = L;
+  for (int r : {7, 5, 3})
+    while (rest % r == 0) { p->radix[p->nstages++] = r; rest /= r; }
+  int twos = 0;
+  while (rest % 2 == 0) { rest /= 2; ++twos; }
+  while (twos >= 3 && !(twos == 4)) { p->radix[p->nstages++] = 8; twos -= 3; }
+  if (twos == 4) { p->radix[p->nstages++] = 4; p->radix[p->nstages++] = 4; twos = 0; }
+  if (twos == 2) { p->radix[p->nstages++] = 4; twos = 0; }
+  if (twos == 1) { p->radix[p->nstages++] = 2; twos = 0; }
+}
+
+void shape(FftPass* p, int64_t ctas_wanted) {
+  // sequences per CTA: fill about 2048 points, but keep >= ctas_wanted CTAs.
+  int C = std::max(1, 2048 / p->L);
+  while (C > 1 && (p->Q + C - 1) / C < ctas_wanted) C /= 2;
+  C = std::min<int64_t>(C, p->Q);
+  while (int64_t(C) * p->L > kMaxCL) --C;
+  p->C = std::max(1, C);
+  int maxpts = p->C * p->L;
+  int minr = 8;
+  for (int s = 0; s < p->nstages; ++s) minr = std::min(minr, p->radix[s]);
+  int t = (maxpts / std::max(2, minr) + 31) / 32 * 32;   // one butterfly per thread
+  p->threads = std::max(32, std::min(512, t));
+}
+
+}  // namespace
+
+int make_fft_plan(int64_t M, FftPlan* out) {
+  FftPlan f;
+  f.M = M;
+  std::vector<int> primes;
+  int64_t rest = M;
+  for (int p : {7, 5, 3, 2})
+    while (rest % p == 0) { primes.push_back(p); rest /= p; }
+  if (rest != 1) return TM_EINVAL;
+  int np = M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3);
+  int64_t Ls[kMaxPasses] = {1, 1, 1};
+  for (int p : primes) {       // largest primes first, each to the smallest factor
+    int best = 0;
+    for (int i = 1; i < np; ++i)
+      if (Ls[i] < Ls[best]) best = i;
+    Ls[best] *= p;
+  }
+  for (int i = 0; i < np; ++i)
+    if (Ls[i] > kMaxSubLen) return TM_ERANGE;
+  f.npass = np;
+  const int64_t want = 2 * 152;
+  if (np == 1) {
+    FftPass& p = f.pass[0];
+    p.L = int(M); p.Q = 1; p.Qc = 1; p.IS = 1; p.OS = 1; p.Mp = 0;
+  } else if (np == 2) {
+    const int64_t L1 = Ls[0], L2 = Ls[1];
+    FftPass& a = f.pass[0];
+    a.L = int(L1); a.Q = L2; a.Qc = L2; a.IA = 0; a.IC = 1; a.IS = L2;
+    a.OA = 0; a.OC = 1; a.OS = L2; a.Mp = M;
+    FftPass& c = f.pass[1];
+    c.L = int(L2); c.Q = L1; c.Qc = L1; c.IA = 0; c.IC = L2; c.IS = 1;
+    c.OA = 0; c.OC = 1; c.OS = L1; c.Mp = 0;
+  } else {
+    const int64_t L1 = Ls[0], L2 = Ls[1], L3 = Ls[2], Mq = L2 * L3;
+    FftPass& a = f.pass[0];
+    a.L = int(L1); a.Q = Mq; a.Qc = Mq; a.IA = 0; a.IC = 1; a.IS = Mq;
+    a.OA = 0; a.OC = 1; a.OS = Mq; a.Mp = M;
+    FftPass& b = f.pass[1];
+    b.L = int(L2); b.Q = L3 * L1; b.Qc = L3; b.IA = Mq; b.IC = 1; b.IS = L3;
+    b.OA = Mq; b.OC = 1; b.OS = L3; b.Mp = Mq;
+    FftPass& c = f.pass[2];
+    c.L = int(L3); c.Q = L1 * L2; c.Qc = L1; c.IA = L3; c.IC = Mq; c.IS = 1;
+    c.OA = L1; c.OC = 1; c.OS = L1 * L2; c.Mp = 0;
+  }
+  for (int i = 0; i < np; ++i) {
+    radices_of(f.pass[i].L, &f.pass[i]);
+    shape(&f.pass[i], want);
+  }
+  *out = f;
+  return TM_OK;
+}
+
+}  // namespace tmul

@@ -1,0 +1,60 @@
+// Host-side plan of one product: digit size b, transform length, map lengths,
+// FP64 error bound, FFT pass decomposition and kernel launch shapes.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace tmul {
+
+constexpr int kMaxStages = 16;     // radix stages inside one sub-FFT
+constexpr int kMaxPasses = 3;      // HBM passes of one complex FFT
+constexpr int kMaxSubLen = 4096;   // longest sub-FFT held in shared memory
+constexpr int kMaxCL = 4096;       // sequences x length per CTA (2 buffers of 16 B each)
+
+// One HBM pass of a complex FFT: Q independent sub-FFTs of length L. Sequence q
+// has qc = q % Qc, qa = q / Qc; its element j is read at qa*IA + qc*IC + j*IS and
+// its output k is written at qa*OA + qc*OC + k*OS, multiplied by
+// omega_Mp^(qc*k) when Mp != 0 (the four-step twiddle).
+struct FftPass {
+  int L = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {};
+  int64_t Q = 0, Qc = 0;
+  int64_t IA = 0, IC = 0, IS = 0;
+  int64_t OA = 0, OC = 0, OS = 0;
+  int64_t Mp = 0;
+  int C = 1;         // sequences per CTA
+  int threads = 32;  // CTA size
+  size_t tw_sub = 0;     // offset (in double2) of omega_L^k, k < L, in the twiddle table
+  size_t tw_outer = 0;   // offset of omega_Mp^m, m < Mp
+};
+
+struct FftPlan {
+  int64_t M = 0;         // complex length
+  int npass = 0;
+  FftPass pass[kMaxPasses];
+};
+
+struct PlanParams {
+  int kind = 0;          // TM_FULL / TM_LO / TM_HI
+  uint64_t n = 0;        // operand bits
+  int b = 0;             // digit bits
+  int64_t N = 0;         // real transform length
+  int64_t n_digits = 0;  // digits per operand
+  int lam_fwd = 0, lam_bwd = 0;
+  double e_max = 0.0;    // bound on the rounding distance
+  double rho = 0.0;      // auxiliary real root (high product only)
+};
+
+// Chooses (b, N, lambda) for kind and n; returns 0 or a TM_E* code.
+int choose_params(int kind, uint64_t n, PlanParams* out);
+
+// Splits the complex length M into at most kMaxPasses sub-FFT passes and picks
+// their radices and launch shapes. Twiddle offsets are left for the caller.
+int make_fft_plan(int64_t M, FftPlan* out);
+
+// Exposed for tests of the planner.
+bool is_valid_length(int64_t L);
+int64_t smooth_at_least(int64_t x);
+
+}  // namespace tmul

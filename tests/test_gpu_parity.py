@@ -1,0 +1,156 @@
+"""Parity of the CUDA path with the oracle, through the C ABI (marked gpu).
+
+Low and full products must match the oracle bit for bit; high products must be
+the round-half-up value round(t) of Algorithm 3 line 7 that the exact trace
+gives (and therefore lie in the admissible set of Section 1); the rounded
+coefficients c_i (tm_coeffs) must equal the exact 2^b L_i, 2^b H_i and w_i of
+Propositions 3.1, 4.1 and Theorem 2.1; every call's margin must stay below its
+a-priori bound."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import dev, hi_ok, host
+from oracle import bigmul
+from oracle import plan as P
+from oracle import trace as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1703_00640_gb300 as p
+    p.build()
+    p.load()
+    return p
+
+
+def _check_all(pkg, n, u, v, exact_hi=True):
+    du, dv = dev(u), dev(v)
+    full_ref = bigmul.mul_full(u, v, par_depth=3)
+    nl = (n + 63) // 64
+    lo, rep = pkg.mul_lo(du, dv, n)
+    lo_ref = full_ref[:nl].copy()
+    if n % 64:
+        lo_ref[-1] &= np.uint64((1 << (n % 64)) - 1)
+    assert np.array_equal(host(lo), lo_ref), f"low n={n}"
+    assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
+    hi, rep = pkg.mul_hi(du, dv, n)
+    w = bigmul.to_int(host(hi))
+    assert hi_ok(w, u, v, n, full=full_ref), f"high n={n}"
+    if exact_hi:
+        pl = P.choose("hi", n)
+        ex = T.trace("hi", bigmul.to_int(u), bigmul.to_int(v), n, pl["b"], pl["N"])
+        assert w == ex["out"], f"high round(t) n={n}"
+    assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
+    full, rep = pkg.mul_full(du, dv, n)
+    assert np.array_equal(host(full), full_ref), f"full n={n}"
+    assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
+
+
+# sizes: tiny, ragged (n % 64 != 0), several radix stages, 1 / 2 pass boundaries
+SMALL_N = [1, 2, 3, 17, 63, 64, 65, 100, 127, 129, 255, 257, 500, 999, 1000, 1023, 1025,
+           2047, 3001, 4096, 4097, 8191, 10000, 12345, 20000, 40000, 65535, 65536, 65537,
+           100003, 131072, 250001]
+
+
+@pytest.mark.parametrize("n", SMALL_N)
+def test_random(pkg, n):
+    u, v = workloads.pattern_limbs("random", n, seed=n)
+    _check_all(pkg, n, u, v)
+
+
+@pytest.mark.parametrize("pattern", ["ones", "balanced_worst", "alternating", "zero", "one", "top"])
+@pytest.mark.parametrize("n", [64, 1000, 4097, 65536, 200000])
+def test_adversarial(pkg, n, pattern):
+    b = P.choose("lo", n)["b"]
+    u, v = workloads.pattern_limbs(pattern, n, seed=7, b=b)
+    _check_all(pkg, n, u, v)
+
+
+@pytest.mark.parametrize("n", [100, 5000, 65536, 300001])
+@pytest.mark.parametrize("kind", ["lo", "hi", "full"])
+def test_coefficients_exact(pkg, n, kind):
+    """tm_coeffs equals the exact trace coefficient by coefficient."""
+    u, v = workloads.pattern_limbs("random", n, seed=3)
+    pl = P.choose(kind, n)
+    c, rep = pkg.coeffs(kind, dev(u), dev(v), n)
+    c = c.cpu().numpy()
+    ex = T.trace(kind, bigmul.to_int(u), bigmul.to_int(v), n, pl["b"],
+                 pl["n_digits"] if kind == "full" else pl["N"])
+    want = np.zeros(c.size, dtype=np.int64)
+    want[: ex["c"].size] = ex["c"][: c.size]
+    assert np.array_equal(c, want)
+    assert rep["margin"] <= rep["e_max"]
+    if kind != "full":
+        assert c[0] % (1 << pl["b"]) == 0
+
+
+def test_square_and_alias_rules(pkg):
+    import torch
+    n = 3000
+    u, _ = workloads.pattern_limbs("random", n, seed=11)
+    du = dev(u)
+    lo, _ = pkg.mul_lo(du, du, n)                      # u == v is allowed
+    assert np.array_equal(host(lo), bigmul.mul_lo(u, u, n))
+    buf = torch.zeros(64, dtype=torch.int64, device="cuda")
+    with pytest.raises(pkg.TruncMulError) as e:       # out overlapping u
+        pkg.mul_lo(buf[:47], buf[:47], n, out=buf[10:57])
+    assert e.value.code == pkg.TM_EALIAS
+
+
+def test_async_then_status(pkg):
+    import torch
+    n = 20000
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        for seed in range(4):
+            u, v = workloads.pattern_limbs("random", n, seed=seed)
+            du, dv = dev(u), dev(v)
+            out, rep = pkg.mul("lo", du, dv, n, stream=s, report=False)
+            assert rep is None
+            outs.append((out, u, v))
+    st = pkg.stream_status(s)
+    assert st["rc"] == 0 and 0 < st["margin"] < 0.5
+    for out, u, v in outs:
+        assert np.array_equal(host(out), bigmul.mul_lo(u, v, n))
+
+
+def test_host_buffers(pkg):
+    n = 77777
+    u, v = workloads.pattern_limbs("random", n, seed=5)
+    for kind in ("lo", "hi", "full"):
+        out, rep = pkg.mul_host(kind, u, v, n)
+        d, _ = pkg.mul(kind, dev(u), dev(v), n)
+        assert np.array_equal(out, host(d))
+        assert rep["status"] == 0
+
+
+def test_deterministic(pkg):
+    n = 123457
+    u, v = workloads.pattern_limbs("random", n, seed=9)
+    a, _ = pkg.mul_hi(dev(u), dev(v), n)
+    b, _ = pkg.mul_hi(dev(u), dev(v), n)
+    assert np.array_equal(host(a), host(b))
+
+
+@pytest.mark.parametrize("n", [2**20, 2**24])
+@pytest.mark.parametrize("pattern", ["random", "ones", "balanced_worst"])
+def test_config_sizes(pkg, n, pattern):
+    """The single-product configurations at n = 2^20 and 2^24 (uniform random and
+    the adversarial all-ones / maximal-digit operands)."""
+    b = P.choose("lo", n)["b"]
+    u, v = workloads.pattern_limbs(pattern, n, seed=20, b=b)
+    _check_all(pkg, n, u, v, exact_hi=(n <= 2**20))
+
+
+def test_config_2_28(pkg):
+    """n = 2^28 (32 MiB operands): low / high / full against the oracle product."""
+    n = 2**28
+    u, v = workloads.pattern_limbs("random", n, seed=28)
+    _check_all(pkg, n, u, v, exact_hi=False)

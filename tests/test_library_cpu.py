@@ -1,0 +1,82 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+function include/truncmul.h declares, its tm_report layout matches the header,
+its host-only planner agrees with the oracle's independent planner, and bad
+arguments are rejected before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "truncmul.h")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1703_00640_gb300 as p
+    p.build()
+    p.load()
+    return p
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(tm_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(pkg):
+    names = _declared()
+    assert len(names) >= 10
+    out = subprocess.check_output(["nm", "-D", "--defined-only", pkg.library_path()], text=True)
+    exported = set(re.findall(r" T (tm_\w+)$", out, re.M))
+    assert set(names) <= exported, set(names) - exported
+    assert set(names) == set(pkg.EXPORTS)
+    lib = pkg.load()
+    for n in names:
+        getattr(lib, n)
+
+
+def test_report_layout_matches_header(tmp_path, pkg):
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "truncmul.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(tm_report),'
+                   ' offsetof(tm_report, margin), offsetof(tm_report, e_max),'
+                   ' offsetof(tm_report, table_bytes)); return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    size, om, oe, ot = map(int, subprocess.check_output([str(exe)], text=True).split())
+    R = pkg.Report
+    assert (size, om, oe, ot) == (ctypes.sizeof(R), R.margin.offset, R.e_max.offset,
+                                  R.table_bytes.offset)
+
+
+NS = [1, 2, 7, 63, 64, 65, 100, 999, 1000, 4096, 5000, 65536, 100003, 2**20, 10**6, 2**24,
+      21544346, 2**28]
+
+
+@pytest.mark.parametrize("n", NS)
+@pytest.mark.parametrize("kind", ["lo", "hi", "full"])
+def test_plan_matches_oracle_plan(pkg, n, kind):
+    from oracle import plan as P
+    mine = pkg.plan(kind, n)
+    ref = P.choose(kind, n)
+    assert (mine["b"], mine["N"], mine["n_digits"]) == (ref["b"], ref["N"], ref["n_digits"])
+    assert (mine["lam_fwd"], mine["lam_bwd"]) == (ref["lam_fwd"], ref["lam_bwd"])
+    assert mine["e_max"] == pytest.approx(ref["e_max"], rel=1e-9)
+    assert mine["e_max"] < 0.5
+
+
+def test_host_side_errors(pkg):
+    lib = pkg.load()
+    rep = pkg.Report()
+    assert lib.tm_plan_query(1, 0, ctypes.byref(rep)) == pkg.TM_EINVAL
+    assert lib.tm_plan_query(7, 100, ctypes.byref(rep)) == pkg.TM_EINVAL
+    assert lib.tm_plan_query(1, (1 << 31) + 1, ctypes.byref(rep)) == pkg.TM_ERANGE
+    assert lib.tm_plan_query(1, 100, None) == pkg.TM_EINVAL
+    # null operands are rejected before any CUDA call
+    assert lib.tm_mul(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_lo(None, None, None, 0, None, None) == pkg.TM_EINVAL
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, 99):
+        assert pkg.strerror(code)
