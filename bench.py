@@ -1,0 +1,334 @@
+"""Benchmark of the truncated-product library on GB300.
+
+One step = one low, one high and one full product of the same two n-bit
+operands (uniform random uint64 limbs from a seeded PCG64), n = 2^24 by
+default: the single-product configuration at n = 2^24 bits. The headline value
+is the truncated-product throughput, operand bits per second over the low and
+high products (2 n bits / (t_lo + t_hi)); the full product gives the
+t_trunc / t_full ratios. Each product is timed with CUDA events on its stream,
+with the L2 flushed (256 MB written) between products.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+Multi-GPU (torchrun, one rank per GPU): replicas, each rank multiplies its own
+operands; value = bits of all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50/p99 ms"
+UNIT = "Gbit/s"
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        """Samples taken inside [start, end]; when the region is shorter than the
+        sampling interval, the samples within 0.25 s of it."""
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = getattr(self, "start", 0.0), getattr(self, "end", 1e30)
+        inside = [l for t, l in self.lines if t0 <= t <= t1]
+        if not inside:
+            inside = [l for t, l in self.lines if t0 - 0.25 <= t <= t1 + 0.25]
+        for line in inside:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def oracle_products(n, seeds, par_depth):
+    """Times the oracle's low and high products (its C Karatsuba full product plus
+    truncation by definition) on the host; returns seconds per (lo, hi) pair."""
+    import workloads
+    from oracle import bigmul
+    times = []
+    for seed in seeds:
+        u, v = workloads.pattern_limbs("random", n, seed=seed)
+        t0 = time.perf_counter()
+        bigmul.mul_lo(u, v, n, par_depth=par_depth)
+        bigmul.mul_hi_floor(u, v, n, par_depth=par_depth)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def threads_for(par_depth):
+    return 3 ** par_depth if par_depth > 0 else 1
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    n = args.n
+    ncpu = os.cpu_count() or 1
+    depth = 0
+    while threads_for(depth + 1) <= ncpu and depth < 3:
+        depth += 1
+    oracle_products(n, range(1000, 1000 + args.warmup), depth)
+    t = oracle_products(n, range(2000, 2000 + args.steps), depth)
+    total = sum(t)
+    value = 2 * n * args.steps / total / 1e9
+    cores = min(threads_for(depth), ncpu)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"single low + high product, n = {n} bits, uniform random "
+                               "uint64 limbs (seeded PCG64)", "n_bits": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of one low + one high product at n={n} "
+                                   "(C Karatsuba full product + truncation), "
+                                   f"{threads_for(depth)} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ CUDA arm
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+    import paper_1703_00640_gb300 as pkg
+    import workloads
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    pkg.build()
+    pkg.load()
+    n = args.n
+    nl = (n + 63) // 64
+    u_np, v_np = workloads.pattern_limbs("random", n, seed=100 + rank)
+    u = torch.from_numpy(u_np.view(np.int64)).cuda()
+    v = torch.from_numpy(v_np.view(np.int64)).cuda()
+    stream = torch.cuda.current_stream()
+    kinds = ["lo", "hi", "full"]
+    outs = {k: torch.empty(pkg.out_limbs(k, n), dtype=torch.int64, device="cuda") for k in kinds}
+    plans = {k: pkg.plan(k, n) for k in kinds}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # correctness gate on the bench workload (sampled against the oracle's low product)
+    _, rep = pkg.mul("lo", u, v, n, out=outs["lo"])
+    margin = {"lo": rep["margin"]}
+    for k in ("hi", "full"):
+        _, rep = pkg.mul(k, u, v, n, out=outs[k])
+        margin[k] = rep["margin"]
+
+    def one_step(record):
+        ev = {}
+        for k in kinds:
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(pkg.NPHASES + 1)]
+            for x in e:          # torch creates the CUDA event on its first record
+                x.record(stream)
+            pkg.mul_events(k, u, v, n, e, out=outs[k], stream=stream)
+            ev[k] = e
+        if record is not None:
+            record.append(ev)
+
+    for _ in range(args.warmup):
+        one_step(None)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    recs = []
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)                 # let the sampler start
+        clk.mark("start")
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(recs)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk.mark("end")
+        time.sleep(0.3)
+    st = pkg.stream_status(stream)
+    # per-product and per-phase device times
+    per = {k: [] for k in kinds}
+    phase = {k: [[] for _ in range(pkg.NPHASES)] for k in kinds}
+    for ev in recs:
+        for k in kinds:
+            e = ev[k]
+            per[k].append(e[0].elapsed_time(e[-1]))
+            for i in range(pkg.NPHASES):
+                phase[k][i].append(e[i].elapsed_time(e[i + 1]))
+    t_lo, t_hi, t_full = (sum(per[k]) for k in kinds)
+    dev_total = t_lo + t_hi + t_full
+    if dist:
+        tt = torch.tensor([t_lo, t_hi, t_full, dev_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_lo, t_hi, t_full, dev_total = tt.tolist()
+    value = 2 * n * args.steps * world / ((t_lo + t_hi) * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the FFT passes): 3 complex FFTs of length
+    # M = N/2 per product at the conventional 5 M log2 M flops each
+    fft_flops, fft_ms, fft_launches = 0.0, 0.0, 0
+    for k in kinds:
+        M = plans[k]["N"] // 2
+        fft_flops += args.steps * 3 * 5.0 * M * np.log2(M)
+        fft_ms += sum(phase[k][1]) + sum(phase[k][3])
+        fft_launches += args.steps * 2 * plans[k]["fft_passes"]
+    achieved = fft_flops / (fft_ms * 1e-3) / 1e12
+    launches = args.steps * sum(2 * plans[k]["fft_passes"] + 6 for k in kinds)
+
+    # end to end through tm_mul_host with page-locked host buffers
+    hu = torch.from_numpy(u_np.view(np.int64)).pin_memory()
+    hv = torch.from_numpy(v_np.view(np.int64)).pin_memory()
+    hout = {k: torch.empty(pkg.out_limbs(k, n), dtype=torch.int64).pin_memory() for k in kinds}
+    e2e_t = []
+    for it in range(args.warmup + args.steps):
+        t1 = time.perf_counter()
+        for k in ("lo", "hi"):
+            pkg.mul_host(k, hu, hv, n, out=hout[k], stream=stream)
+        if it >= args.warmup:
+            e2e_t.append(time.perf_counter() - t1)
+    e2e_val = 2 * n * len(e2e_t) * world / sum(e2e_t) / 1e9
+    assert np.array_equal(hout["lo"].numpy(), outs["lo"].cpu().numpy())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        ts = oracle_products(n, range(3000, 3001), 0)
+        cpu = {"value": 2 * n / sum(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one low + one high product at n={n} bits (C Karatsuba full "
+                         "product + truncation by definition), 1 thread"}
+    phases = {k: {pkg.PHASES[i]: round(statistics.median(phase[k][i]), 4)
+                  for i in range(pkg.NPHASES)} for k in kinds}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"single low + high (+ full for the ratio) product, n = {n} bits, "
+                               "uniform random uint64 limbs (seeded PCG64)",
+                   "n_bits": n, "l2": "flushed (256 MB write) before every product",
+                   "parallelism": f"replicas x{world}"},
+        "lo_gbit_s": n * args.steps / (t_lo * 1e-3) / 1e9,
+        "hi_gbit_s": n * args.steps / (t_hi * 1e-3) / 1e9,
+        "full_gbit_s": n * args.steps / (t_full * 1e-3) / 1e9,
+        "t_lo_over_full": t_lo / t_full, "t_hi_over_full": t_hi / t_full,
+        "ms": {k: {"p50": statistics.median(per[k]),
+                   "p99": float(np.percentile(per[k], 99))} for k in kinds},
+        "phases_ms_median": phases,
+        "plans": {k: {x: plans[k][x] for x in ("b", "N", "lam_fwd", "lam_bwd", "fft_passes",
+                                                 "e_max")} for k in kinds},
+        "margin": margin, "status_after_timed_region": st["rc"],
+        "roofline": {"bound": "alu", "kernel": "k_fft_pass", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "note": "FP64; 5 M log2 M flops per complex FFT of length M = N/2, 3 per "
+                             "product; peak = nominal FP64 (recipe), not measured"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * 2 * nl * 8,
+                "d2h_bytes_per_step": (pkg.out_limbs("lo", n) + pkg.out_limbs("hi", n)) * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -102,7 +102,7 @@ typedef struct tm_report {
  * nothing is enqueued.
  * Sources: full product - Algorithm 1 and Theorem 2.1; low product -
  * Algorithm 2, Theorem 2.2, Proposition 3.1; high product - Algorithm 3,
- * Theorem 2.3, Proposition 4.1 (the result is round(t) of line 7, rounding
+ * Theorem 2.3, Proposition 4.1 (the result is the returned round(t), rounding
  * half up, which is one of the at most two admissible values).
  */
 int tm_mul_full(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
@@ -126,11 +126,26 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
                 uint64_t n_bits, void* stream, tm_report* rep);
 
 /*
+ * tm_mul_events: tm_mul that also records caller-created CUDA events
+ * (cudaEvent_t, timing enabled) on `stream` around its phases, for measuring
+ * where the device time goes. events[0] is recorded before the first kernel
+ * and events[i+1] after phase i, i < TM_NPHASES:
+ *   0 digits + forward map (split and convert steps), 1 forward FFTs,
+ *   2 real-FFT twist + pointwise product, 3 inverse FFT,
+ *   4 back map + rounding (convert back), 5 overlap-add / carry scan.
+ * events must hold TM_NPHASES + 1 entries. Same arguments and return values as
+ * tm_mul otherwise.
+ */
+#define TM_NPHASES 6
+int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, void* stream, void* const* events, tm_report* rep);
+
+/*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
  * for checking the method stage by stage:
- *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2 line 6,
+ *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2,
  *         Proposition 3.1);
- *   high: c_i = round(2^b Wbar_i) = 2^b H_i, i <= N      (Algorithm 3 line 6,
+ *   high: c_i = round(2^b Wbar_i) = 2^b H_i, i <= N      (Algorithm 3,
  *         Proposition 4.1);
  *   full: c_i = round(Wbar_i) = w_i, i < N (the cyclic length) (Algorithm 1).
  * c_out must hold rep->n_digits (high: N + 1) or N int64 values: use

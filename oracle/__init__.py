@@ -11,9 +11,9 @@ Contents (each function cites the passage of the paper it follows):
 - ``bigmul``   exact full product of uint64 limb arrays (C: schoolbook + Karatsuba)
                and the low / high products by their definitions (Section 1).
 - ``trace``    exact integer trace of the method: digit splits (Algorithms 1-3,
-               line 2), the integer product coefficients w_i, the rounded
+               split step), the integer product coefficients w_i, the rounded
                coefficients 2^b L_i (Proposition 3.1) and 2^b H_i (Proposition 4.1),
-               the overlap-add of Algorithm 2 line 6 and Algorithm 3 lines 6-7.
+               the overlap-add steps of Algorithms 2 and 3.
 - ``series``   exact rational coefficients alpha_{k,r}, beta_{k,r} (Section 3.2),
                gamma_{k,r}, delta_{k,r} (Section 4.2), the auxiliary root rho
                (Lemma 4.2) and the maps alpha*, beta*, gamma-dagger, delta-dagger

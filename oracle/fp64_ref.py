@@ -8,7 +8,7 @@ box of Section 2.1; every other step is written from its definition:
 - delta-dagger:      eqs. (4.6)-(4.7), with psi in the scaled form
                      psi = (theta - rho^-2N H(rho)) / (1 - N 2^b rho^-(N+1)),
                      which is (4.6) divided through by rho^N
-- rounding:          round(2^b Wbar_i) (Algorithm 2 line 6, Algorithm 3 line 6)
+- rounding:          round(2^b Wbar_i) (overlap-add step of Algorithms 2 and 3)
 
 Results: the rounded coefficients, the final integer and the largest distance
 to the nearest integer ("margin").
@@ -126,11 +126,11 @@ def mul_lo(u: int, v: int, n: int, b: int, N: int, lam_a: int, lam_b: int) -> di
     """Algorithm 2."""
     U = np.array(trace.split("lo", u, n, b, N), dtype=np.float64)
     V = np.array(trace.split("lo", v, n, b, N), dtype=np.float64)
-    Ut = alpha_star(U, N, b, lam_a)                       # line 3
+    Ut = alpha_star(U, N, b, lam_a)                       # convert to cyclic convolution
     Vt = alpha_star(V, N, b, lam_a)
-    Wt = convolution(Ut, Vt)                              # line 4
-    Wbar = beta_star(Wt, N, b, lam_b)                     # line 5
-    c, margin = _round(Wbar, 2.0 ** b)                    # line 6
+    Wt = convolution(Ut, Vt)                              # perform convolution
+    Wbar = beta_star(Wt, N, b, lam_b)                     # convert back
+    c, margin = _round(Wbar, 2.0 ** b)                    # overlap-add (rounding)
     return {"Ut": Ut, "Vt": Vt, "Wt": Wt, "Wbar": Wbar, "c": c, "margin": margin,
             "out": trace.low_output(c, n, b)}
 
@@ -181,11 +181,11 @@ def mul_hi(u: int, v: int, n: int, b: int, N: int, lam_g: int, lam_d: int) -> di
     rho = rho_float(N, b)
     U = np.array(trace.split("hi", u, n, b, N), dtype=np.float64)
     V = np.array(trace.split("hi", v, n, b, N), dtype=np.float64)
-    Ut, thU = gamma_dagger(U, N, b, lam_g, rho)          # line 3
+    Ut, thU = gamma_dagger(U, N, b, lam_g, rho)          # convert to cyclic convolution
     Vt, thV = gamma_dagger(V, N, b, lam_g, rho)
-    Wt = convolution(Ut, Vt)                              # line 4
+    Wt = convolution(Ut, Vt)                              # perform convolution
     thW = thU * thV
-    Wbar = delta_dagger(Wt, thW, N, b, lam_d, rho)        # line 5
-    c, margin = _round(Wbar, 2.0 ** b)                    # line 6
+    Wbar = delta_dagger(Wt, thW, N, b, lam_d, rho)        # convert back
+    c, margin = _round(Wbar, 2.0 ** b)                    # overlap-add (rounding)
     return {"Ut": Ut, "Vt": Vt, "thU": thU, "thV": thV, "Wt": Wt, "Wbar": Wbar, "c": c,
             "margin": margin, "out": trace.high_output(c, n, N, b)}

@@ -3,16 +3,16 @@
 Everything here is exact integer arithmetic (Python ints and int64 numpy arrays
 whose ranges are checked). Given the split parameters (b, N), the trace gives:
 
-- the digits of Algorithms 1-3, line 2 ("Split inputs"), in the balanced form the
+- the digits of the "Split inputs" step of Algorithms 1-3, in the balanced form the
   paper's implementation uses (Section 5: |U_i| <= 2^(b-1)); the reading for
   the high product keeps its top digit U_N unbalanced, 0 <= U_N <= 2^b;
 - w_i, the coefficients of W = U V (proofs of Theorems 2.1-2.3), by Kronecker
   substitution X = 2^64 through the exact big-integer product;
 - c_i = 2^b L_i (Proposition 3.1) for the low product and c_i = 2^b H_i
-  (Proposition 4.1) for the high product: the integers that line 6 of
-  Algorithm 2 and line 6 of Algorithm 3 obtain as round(2^b * Wbar_i);
-- the overlap-add outputs: Algorithm 2 line 6, Algorithm 3 lines 6-7 (with the
-  round-half-up reading of round(t)), Algorithm 1 line 4.
+  (Proposition 4.1) for the high product: the integers that the overlap-add
+  steps of Algorithms 2 and 3 obtain as round(2^b * Wbar_i);
+- the overlap-add outputs of Algorithms 1, 2 and 3 (with the round-half-up
+  reading of Algorithm 3's final round(t)).
 """
 import numpy as np
 
@@ -48,7 +48,7 @@ def balanced_digits(x: int, count: int, b: int, balance_top: bool) -> list:
 
 
 def split(kind: str, u: int, n: int, b: int, N: int) -> list:
-    """Line 2 of Algorithms 1-3 with balanced digits.
+    """The "Split inputs" step of Algorithms 1-3 with balanced digits.
 
     full: N digits, requires N*b >= n+1 so that the top digit never carries out;
     lo:   N digits with U(2^b) == u (mod 2^(Nb)) (Algorithm 2 only needs that);
@@ -161,7 +161,7 @@ def eval_at_2b(c, b: int) -> int:
 
 
 def low_output(c: np.ndarray, n: int, b: int) -> int:
-    """Algorithm 2 line 6: sum 2^-b c_i 2^(ib) mod 2^n. c_0 is divisible by 2^b
+    """Algorithm 2, overlap-add: sum 2^-b c_i 2^(ib) mod 2^n. c_0 is divisible by 2^b
     (c_0 = 2^b (w_0 + w_N)), so the sum is an integer."""
     c0 = int(c[0])
     assert c0 % (1 << b) == 0
@@ -169,12 +169,12 @@ def low_output(c: np.ndarray, n: int, b: int) -> int:
 
 
 def high_t_numerator(c: np.ndarray, n: int, N: int, b: int):
-    """Algorithm 3 line 6: t = S / 2^s with S = sum c_i 2^(ib), s = (N+3)b - n."""
+    """Algorithm 3, overlap-add: t = S / 2^s with S = sum c_i 2^(ib), s = (N+3)b - n."""
     return eval_at_2b(c, b), (N + 3) * b - n
 
 
 def high_output(c: np.ndarray, n: int, N: int, b: int) -> int:
-    """Algorithm 3 line 7, round(t) read as round half up: floor(t + 1/2)."""
+    """Algorithm 3, returned value round(t), read as round half up: floor(t + 1/2)."""
     S, s = high_t_numerator(c, n, N, b)
     return (S + (1 << (s - 1))) >> s
 

@@ -37,7 +37,10 @@ class TruncMulError(RuntimeError):
         self.code = code
 
 
-EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_coeffs",
+NPHASES = 6
+PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "carry"]
+EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
+           "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -64,12 +67,14 @@ def load(path: str = None):
     lib.tm_mul.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_mul_host.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_coeffs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_events.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P,
+                                  ctypes.POINTER(ctypes.c_void_p), R]
     lib.tm_plan_query.argtypes = [ctypes.c_int, ctypes.c_uint64, R]
     lib.tm_stream_status.argtypes = [P, R]
     lib.tm_release.argtypes = []
     lib.tm_strerror.argtypes = [ctypes.c_int]
     lib.tm_strerror.restype = ctypes.c_char_p
-    for name in ("tm_mul", "tm_mul_host", "tm_coeffs", "tm_plan_query", "tm_stream_status",
+    for name in ("tm_mul", "tm_mul_host", "tm_mul_events", "tm_coeffs", "tm_plan_query", "tm_stream_status",
                  "tm_release"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -129,6 +134,22 @@ def mul(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True, che
     if check and rc:
         raise TruncMulError(rc, "tm_mul")
     return out, (rep.as_dict() if rep is not None else None)
+
+
+def mul_events(kind, u, v, n_bits: int, events, out=None, stream=None):
+    """tm_mul_events: enqueue one product recording torch.cuda.Event objects
+    (NPHASES + 1 of them, enable_timing=True) between its phases. Asynchronous."""
+    import torch
+    k = _kind(kind)
+    assert len(events) == NPHASES + 1
+    if out is None:
+        out = torch.empty(out_limbs(k, n_bits), dtype=torch.int64, device=u.device)
+    arr = (ctypes.c_void_p * (NPHASES + 1))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    rc = load().tm_mul_events(k, _ptr(out), _ptr(u), _ptr(v), int(n_bits), _stream_ptr(stream),
+                              arr, None)
+    if rc:
+        raise TruncMulError(rc, "tm_mul_events")
+    return out
 
 
 def mul_lo(u, v, n_bits, **kw):

@@ -72,7 +72,7 @@ int64_t out_limbs(int kind, uint64_t n) {
 void carry_shape(const PlanParams& p, int64_t* nS, int64_t* shift, int64_t* round_bit) {
   const int64_t nout = out_limbs(p.kind, p.n);
   if (p.kind == TM_HI) {
-    const int64_t s = (p.N + 3) * int64_t(p.b) - int64_t(p.n);   // Algorithm 3 line 6
+    const int64_t s = (p.N + 3) * int64_t(p.b) - int64_t(p.n);   // Algorithm 3, overlap-add
     *shift = s;
     *round_bit = s - 1;
     *nS = (s + 64 * nout + 63) / 64 + 1;
@@ -231,7 +231,12 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 // Enqueues the whole product; `coeff_out` receives the rounded coefficients and
 // stops the pipeline before the carry scan when non-null.
 int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
-            cudaStream_t s, const PlanEntry& pe, Workspace& ws, int64_t* coeff_out) {
+            cudaStream_t s, const PlanEntry& pe, Workspace& ws, int64_t* coeff_out,
+            void* const* events) {
+  auto mark = [&](int i) {
+    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
+  };
+  mark(0);
   const PlanParams& p = pe.p;
   const int64_t N = p.N, M = pe.M;
   const size_t region = std::max(align_up(size_t(2) * M * sizeof(double2)),
@@ -239,7 +244,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   double2* R0 = reinterpret_cast<double2*>(ws.base);
   double2* R1 = reinterpret_cast<double2*>(ws.base + region);
   double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
-  // 1. digits + forward map (Algorithms 1-3, lines 2-3)
+  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
   FwdArgs fa{};
   fa.u = reinterpret_cast<const unsigned long long*>(u);
   fa.v = reinterpret_cast<const unsigned long long*>(v);
@@ -258,6 +263,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   fa.X = reinterpret_cast<double*>(R0);
   fa.theta = theta;
   launch_fwd(kind, fa, s);
+  mark(1);
   // 2. forward FFTs of both operands (complex length M, batch 2)
   double2* bufs[2] = {R0, R1};
   int cur = 0;
@@ -274,9 +280,11 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
     launch_fft_pass(-1, bufs[cur], bufs[cur ^ 1], a, 2, fp.threads, s);
     cur ^= 1;
   }
+  mark(2);
   // 3. real-FFT twist, pointwise product, inverse pre-twist
   launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), s);
   cur ^= 1;
+  mark(3);
   // 4. inverse FFT (batch 1)
   for (int i = 0; i < pe.fft.npass; ++i) {
     const FftPass& fp = pe.fft.pass[i];
@@ -291,7 +299,8 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
     launch_fft_pass(1, bufs[cur], bufs[cur ^ 1], a, 1, fp.threads, s);
     cur ^= 1;
   }
-  // 5. back map + round (Algorithm 1 line 4, Algorithm 2 lines 5-6, Algorithm 3 lines 5-6)
+  mark(4);
+  // 5. back map + round (convert-back and rounding of Algorithms 1-3)
   double2* wbuf = bufs[cur];
   long long* cbuf = reinterpret_cast<long long*>(bufs[cur ^ 1]);
   BackArgs ba{};
@@ -310,6 +319,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   ba.emax_fx = (unsigned long long)std::ldexp(p.e_max, 63);
   ba.status = ws.status;
   launch_back(kind, ba, s);
+  mark(5);
   if (coeff_out) {
     TM_CHECK(cudaMemcpyAsync(coeff_out, cbuf, size_t(ba.count) * 8, cudaMemcpyDeviceToDevice, s));
     TM_CHECK(cudaGetLastError());
@@ -334,6 +344,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   ca.fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
   ca.cin_block = ca.fblock + align_up(size_t(nS / 512 + 2));
   launch_carry(ca, s);
+  mark(6);
   TM_CHECK(cudaGetLastError());
   return TM_OK;
 }
@@ -368,7 +379,7 @@ void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
 }
 
 int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n, void* stream,
-        tm_report* rep, int64_t* coeff_out) {
+        tm_report* rep, int64_t* coeff_out, void* const* events = nullptr) {
   if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
   if (n == 0 || !u || !v || (!out && !coeff_out)) return TM_EINVAL;
   if (n > TM_MAX_BITS) return TM_ERANGE;
@@ -384,7 +395,7 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
   Workspace* ws = nullptr;
   rc = get_workspace(s, workspace_bytes(pe->p), &ws);
   if (rc) return rc;
-  rc = enqueue(kind, out, u, v, n, s, *pe, *ws, coeff_out);
+  rc = enqueue(kind, out, u, v, n, s, *pe, *ws, coeff_out, events);
   if (rc) return rc;
   if (!rep) return TM_OK;
   fill_plan_report(pe->p, pe->fft, rep);
@@ -400,6 +411,14 @@ extern "C" {
 int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
            void* stream, tm_report* rep) {
   return tmul::run(kind, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, void* stream, void* const* events, tm_report* rep) {
+  if (!events) return TM_EINVAL;
+  for (int i = 0; i <= TM_NPHASES; ++i)
+    if (!events[i]) return TM_EINVAL;
+  return tmul::run(kind, out, u, v, n_bits, stream, rep, nullptr, events);
 }
 
 int tm_mul_full(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,

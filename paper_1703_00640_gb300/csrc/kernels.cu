@@ -194,9 +194,9 @@ constexpr int kFwdTile = 1024;
 constexpr int kFwdThreads = 256;
 constexpr int kMaxLam = 24;
 
-// Low product: U~ = sum_{r<lam} alpha*_r U (Algorithm 2 line 3; Proposition 3.15),
+// Low product: U~ = sum_{r<lam} alpha*_r U (Algorithm 2, convert step; Proposition 3.15),
 // U~_j = U_j + sum_{r=1}^{lam-1} alpha_{(j-r) mod N, r} U_{(j-r) mod N}.
-// Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1 line 2).
+// Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1, split step).
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind) {
   __shared__ double du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   const long long j0 = (long long)blockIdx.x * kFwdTile;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind
   }
 }
 
-// High product: gamma-dagger (Algorithm 3 line 3; Proposition 4.18).
+// High product: gamma-dagger (Algorithm 3, convert step; Proposition 4.18).
 // F' = F mod C: F'_i = F_i + kappa_i F_N (eq. 4.5), then
 // U~_j = sum_{r<lam} gamma_{(j-r) mod N, r} F'_{(j-r) mod N}, and
 // theta = rho^-N F(rho) = sum_j rho^-j F_(N-j).
@@ -579,7 +579,7 @@ __device__ __forceinline__ void emit(const BackArgs& a, long long i, double x, b
   note_distance(d, bmax);
 }
 
-// Full product (Algorithm 1 line 4): c_i = round(W_i).
+// Full product (Algorithm 1, overlap-add): c_i = round(W_i).
 __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a) {
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a) {
   finish_block(&bmax, &bflags, a);
 }
 
-// Low product (Algorithm 2 lines 5-6; Proposition 3.16): Wbar = sum_{r<lam} beta*_r W~
+// Low product (Algorithm 2, convert back and rounding; Proposition 3.16): Wbar = sum_{r<lam} beta*_r W~
 // reduced mod A(X) = X^N + 2^-b X - 1, then c_i = round(2^b Wbar_i).
 // Interior positions i >= lam receive no wrapped terms. Head positions i < lam
 // add P_(N+i) and subtract 2^-b P_(N+i-1), where P_(N+m) =
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a) {
   finish_block(&bmax, &bflags, a);
 }
 
-// High product (Algorithm 3 lines 4-6; Proposition 4.19 with Remark 4.20 for
+// High product (Algorithm 3, convert back and rounding; Proposition 4.19 with Remark 4.20 for
 // large N): H = sum_{r<lam} delta*_r W~ reduced mod C(X), whose X^N = sum_i
 // kappa_i X^i (eq. 4.4), and then by eq. (4.7)
 //   J_i = H_i - 2^-b H_(i-1) - psi kappa_i (i < N),  J_N = -2^-b H_(N-1) + psi,
@@ -799,8 +799,8 @@ void launch_back(int kind, const BackArgs& a, cudaStream_t s) {
 // ------------------------------------------------------------ carry scan
 
 // S = sum_i t_i 2^(p_i) with signed 54-bit terms t_i: c_i at i b (full, high),
-// c_i at (i-1) b for i >= 1 and c_0 / 2^b at 0 (low, Algorithm 2 line 6), plus
-// 2^(s-1) for the high product's round(t) (Algorithm 3 line 7, half up).
+// c_i at (i-1) b for i >= 1 and c_0 / 2^b at 0 (low, Algorithm 2 overlap-add), plus
+// 2^(s-1) for the high product's returned round(t) (Algorithm 3, half up).
 // A_L = sum over terms starting in limb L of t_i 2^(p_i - 64 L) (int128);
 // r_L = (A_L mod 2^64) + floor(A_(L-1) / 2^64) lies in (-2^60, 2^64 + 2^60), so
 // the carry into each limb is -1, 0 or +1 and each limb acts on it through a

@@ -1,7 +1,7 @@
 """Parity of the CUDA path with the oracle, through the C ABI (marked gpu).
 
 Low and full products must match the oracle bit for bit; high products must be
-the round-half-up value round(t) of Algorithm 3 line 7 that the exact trace
+the round-half-up value round(t) that Algorithm 3 returns, as the exact trace
 gives (and therefore lie in the admissible set of Section 1); the rounded
 coefficients c_i (tm_coeffs) must equal the exact 2^b L_i, 2^b H_i and w_i of
 Propositions 3.1, 4.1 and Theorem 2.1; every call's margin must stay below its
