@@ -141,6 +141,31 @@ int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
                   uint64_t n_bits, void* stream, void* const* events, tm_report* rep);
 
 /*
+ * tm_mul_static: tm_mul for callers that cannot allocate device memory, for
+ * example code that runs where the memory allocator belongs to someone else, or
+ * that must not block on an allocation. The paper has no counterpart; this is
+ * a library facility. Everything the call needs on the device (twiddle and map
+ * tables, FFT buffers, carry scratch, status word) lives in one file-scope
+ * device array of TM_STATIC_SCRATCH_BYTES that every GPU which loads the library
+ * holds until the process exits. The call makes no CUDA allocation and no heap
+ * allocation; the caller passes u, v and out (device pointers) as for tm_mul.
+ *   n_bits must be <= TM_STATIC_MAX_BITS; larger sizes (or a plan that would not
+ *   fit the array) return TM_ERANGE and enqueue nothing.
+ *   The first call on a device looks the array's device address up
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call on a device shares the same array and leaves its contents for
+ *   the next call (each call rebuilds its tables and clears its status word), so
+ *   calls that overlap on the GPU - on different streams, threads or in flight
+ *   at once - race and must be serialised by the caller.
+ *   rep as for tm_mul (NULL = asynchronous; a non-NULL rep waits and reports).
+ */
+#define TM_STATIC_MAX_BITS 65536
+#define TM_STATIC_SCRATCH_BYTES (((size_t)4) << 20)
+int tm_mul_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, void* stream, tm_report* rep);
+
+/*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
  * for checking the method stage by stage:
  *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2,

@@ -39,8 +39,9 @@ class TruncMulError(RuntimeError):
 
 NPHASES = 6
 PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "carry"]
+STATIC_MAX_BITS = 65536
 EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
-           "tm_coeffs",
+           "tm_mul_static", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -66,6 +67,7 @@ def load(path: str = None):
         getattr(lib, name).restype = ctypes.c_int
     lib.tm_mul.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_mul_host.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_static.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_coeffs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_mul_events.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P,
                                   ctypes.POINTER(ctypes.c_void_p), R]
@@ -74,7 +76,7 @@ def load(path: str = None):
     lib.tm_release.argtypes = []
     lib.tm_strerror.argtypes = [ctypes.c_int]
     lib.tm_strerror.restype = ctypes.c_char_p
-    for name in ("tm_mul", "tm_mul_host", "tm_mul_events", "tm_coeffs", "tm_plan_query", "tm_stream_status",
+    for name in ("tm_mul", "tm_mul_host", "tm_mul_events", "tm_mul_static", "tm_coeffs", "tm_plan_query", "tm_stream_status",
                  "tm_release"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -150,6 +152,15 @@ def mul_events(kind, u, v, n_bits: int, events, out=None, stream=None):
     if rc:
         raise TruncMulError(rc, "tm_mul_events")
     return out
+
+
+def mul_static(kind, u, v, n_bits: int, out, stream=None, report: bool = True):
+    """tm_mul_static: the product with no device allocation (n_bits <= STATIC_MAX_BITS).
+    `out` must be supplied by the caller. Returns (status code, report dict or None)."""
+    rep = Report() if report else None
+    rc = load().tm_mul_static(_kind(kind), _ptr(out), _ptr(u), _ptr(v), int(n_bits),
+                              _stream_ptr(stream), ctypes.byref(rep) if rep is not None else None)
+    return rc, (rep.as_dict() if rep is not None else None)
 
 
 def mul_lo(u, v, n_bits, **kw):

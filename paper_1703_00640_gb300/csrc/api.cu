@@ -403,10 +403,152 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
   return read_status(s, *ws, rep);
 }
 
+// ------------------------------------------- products without allocation
+
+// The scratch of tm_mul_static: one device array per GPU, kept for the life of
+// the process. Host code cannot use its name as a device address; the address is
+// looked up once per device with cudaGetSymbolAddress.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace tmul
+
+static __device__ __align__(256) unsigned char g_static_scratch[TM_STATIC_SCRATCH_BYTES];
+
+namespace tmul {
+namespace {
+
+// Device address of g_static_scratch on the current device (set-up on first use).
+int static_scratch(char** out) {
+  int dev = 0;
+  TM_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return TM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return TM_ECUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = static_cast<char*>(g_static_addr[dev]);
+  return TM_OK;
+}
+
+// Lays out the plan tables, the status word and the workspace inside `base`
+// (TM_STATIC_SCRATCH_BYTES) and enqueues the table initialisation. Returns
+// TM_ERANGE when they do not fit.
+int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* ws) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off += align_up(bytes); return at; };
+  const size_t status_off = take(sizeof(DevStatus));
+  size_t cnt = 0;
+  for (int i = 0; i < e->fft.npass; ++i) {
+    FftPass& fp = e->fft.pass[i];
+    fp.tw_sub = cnt;
+    cnt += size_t(fp.L);
+    if (fp.Mp) { fp.tw_outer = cnt; cnt += size_t(fp.Mp); }
+  }
+  e->twN_off = cnt;
+  const size_t nN = size_t(e->M / 2 + 1);
+  cnt += nN;
+  const size_t tw_off = take(cnt * sizeof(double2));
+  const int64_t N = e->p.N;
+  const int b = e->p.b;
+  const int rf = kind == TM_FULL ? 0 : e->p.lam_fwd - 1;
+  const int rb = kind == TM_FULL ? 0 : (kind == TM_LO ? e->p.lam_bwd - 1 : e->p.lam_bwd);
+  const int r2 = kind == TM_HI ? e->p.lam_bwd - 1 : 0;
+  const size_t fwd_off = take(size_t(std::max(rf, 0)) * N * 8);
+  const size_t bwd_off = take(size_t(std::max(rb, 0)) * N * 8);
+  const size_t bwd2_off = take(size_t(std::max(r2, 0)) * N * 8);
+  int lgN = 0;
+  while ((int64_t(1) << lgN) < N) ++lgN;
+  const int nkappa = kind == TM_HI ? int(std::min<int64_t>(N, 3 + (lgN + 64 + b - 1) / b)) : 0;
+  const int ntheta = kind == TM_HI ? int(std::min<int64_t>(N + 1, (60 + b - 1) / b + 3)) : 0;
+  double host_small[96];
+  if (nkappa + ntheta > 96) return TM_ERANGE;
+  const size_t small_off = take(size_t(nkappa + ntheta) * 8);
+  const size_t ws_bytes = workspace_bytes(e->p);
+  const size_t ws_off = take(ws_bytes);
+  if (off > TM_STATIC_SCRATCH_BYTES) return TM_ERANGE;
+  e->tw = reinterpret_cast<double2*>(base + tw_off);
+  e->fwd_tab = rf > 0 ? reinterpret_cast<double*>(base + fwd_off) : nullptr;
+  e->bwd_tab = rb > 0 ? reinterpret_cast<double*>(base + bwd_off) : nullptr;
+  e->bwd_tab2 = r2 > 0 ? reinterpret_cast<double*>(base + bwd2_off) : nullptr;
+  e->small = kind == TM_HI ? reinterpret_cast<double*>(base + small_off) : nullptr;
+  e->nkappa = nkappa;
+  e->ntheta = ntheta;
+  ws->base = base + ws_off;
+  ws->size = ws_bytes;
+  ws->status = reinterpret_cast<DevStatus*>(base + status_off);
+  // the previous call's contents stay in the array: clear the status word and
+  // rebuild every table this call reads
+  TM_CHECK(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
+  for (int i = 0; i < e->fft.npass; ++i) {
+    const FftPass& fp = e->fft.pass[i];
+    launch_init_twiddles(e->tw + fp.tw_sub, fp.L, fp.L, s);
+    if (fp.Mp) launch_init_twiddles(e->tw + fp.tw_outer, fp.Mp, fp.Mp, s);
+  }
+  launch_init_twiddles(e->tw + e->twN_off, N, int64_t(nN), s);
+  if (rf > 0) launch_init_maptab(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, s);
+  if (rb > 0)
+    launch_init_maptab(e->bwd_tab, kind == TM_LO ? kTabBeta : kTabDeltaPrime, N, b,
+                       kind == TM_LO ? rb : e->p.lam_bwd, s);
+  if (r2 > 0) launch_init_maptab(e->bwd_tab2, kTabDelta, N, b, r2, s);
+  if (kind == TM_HI) {
+    const double lr = std::log(e->p.rho);
+    for (int i = 0; i < nkappa; ++i) host_small[i] = std::exp(b * std::log(2.0) - (i + 1) * lr);
+    for (int j = 0; j < ntheta; ++j) host_small[nkappa + j] = std::exp(-j * lr);
+    // pageable source: the copy has consumed host_small when the call returns
+    TM_CHECK(cudaMemcpyAsync(e->small, host_small, size_t(nkappa + ntheta) * 8,
+                             cudaMemcpyHostToDevice, s));
+  }
+  return TM_OK;
+}
+
+int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+               void* stream, tm_report* rep) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n == 0 || !u || !v || !out) return TM_EINVAL;
+  if (n > TM_STATIC_MAX_BITS) return TM_ERANGE;
+  const size_t in_bytes = size_t(limbs_of(n)) * 8;
+  const size_t ob = size_t(out_limbs(kind, n)) * 8;
+  if (overlaps(out, ob, u, in_bytes) || overlaps(out, ob, v, in_bytes)) return TM_EALIAS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PlanEntry pe;
+  int rc = choose_params_noalloc(kind, n, &pe.p);
+  if (rc) return rc;
+  pe.M = pe.p.N / 2;
+  rc = make_fft_plan_noalloc(pe.M, &pe.fft);
+  if (rc) return rc;
+  char* base = nullptr;
+  rc = static_scratch(&base);
+  if (rc) return rc;
+  Workspace ws;
+  rc = static_plan(kind, base, s, &pe, &ws);
+  if (rc) return rc;
+  rc = enqueue(kind, out, u, v, n, s, pe, ws, nullptr, nullptr);
+  if (rc) return rc;
+  if (!rep) return TM_OK;
+  fill_plan_report(pe.p, pe.fft, rep);
+  rep->table_bytes = 0;
+  return read_status(s, ws, rep);
+}
+
 }  // namespace
 }  // namespace tmul
 
 extern "C" {
+
+int tm_mul_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, void* stream, tm_report* rep) {
+  return tmul::run_static(kind, out, u, v, n_bits, stream, rep);
+}
+
 
 int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
            void* stream, tm_report* rep) {

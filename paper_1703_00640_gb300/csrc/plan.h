@@ -53,6 +53,12 @@ int choose_params(int kind, uint64_t n, PlanParams* out);
 // their radices and launch shapes. Twiddle offsets are left for the caller.
 int make_fft_plan(int64_t M, FftPlan* out);
 
+// The same two plans computed without any heap allocation (for the entry point
+// whose callers cannot allocate): identical choice of (b, N, lambda); the FFT
+// layout may differ only in how the prime factors are grouped.
+int choose_params_noalloc(int kind, uint64_t n, PlanParams* out);
+int make_fft_plan_noalloc(int64_t M, FftPlan* out);
+
 // Exposed for tests of the planner.
 bool is_valid_length(int64_t L);
 int64_t smooth_at_least(int64_t x);
