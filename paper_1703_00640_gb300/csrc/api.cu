@@ -93,6 +93,54 @@ size_t workspace_bytes(const PlanParams& p) {
   return std::max(region, coeff) + std::max(region, carry) + 256;
 }
 
+// Offsets of every twiddle table of a plan inside one double2 allocation:
+// per pass omega_L (when a stage needs it), omega_Mp, the radix-4 tangent
+// tables; then omega_N^k, k <= M/2, for the real-FFT twist. Returns the count.
+size_t layout_twiddles(PlanEntry* e) {
+  size_t cnt = 0;
+  for (int i = 0; i < e->fft.npass; ++i) {
+    FftPass& fp = e->fft.pass[i];
+    int Ns = 1, len4 = 0;
+    fp.need_wL = false;
+    for (int st = 0; st < fp.nstages; ++st) {
+      const int R = fp.radix[st];
+      if (R == 4 && Ns > 1) {
+        fp.tw4_off[st] = len4;
+        len4 += Ns;
+      } else {
+        fp.tw4_off[st] = -1;
+        if (Ns > 1) fp.need_wL = true;
+      }
+      Ns *= R;
+    }
+    fp.tw_sub = cnt;
+    cnt += size_t(fp.L);
+    if (fp.Mp) { fp.tw_outer = cnt; cnt += size_t(fp.Mp); }
+    cnt = (cnt + 1) & ~size_t(1);
+    fp.tw4 = cnt;
+    fp.tw4_len = len4;
+    cnt += 2 * size_t(len4);
+  }
+  e->twN_off = cnt;
+  cnt += size_t(e->M / 2 + 1);
+  return cnt;
+}
+
+void init_twiddles(const PlanEntry& e, cudaStream_t s) {
+  for (int i = 0; i < e.fft.npass; ++i) {
+    const FftPass& fp = e.fft.pass[i];
+    launch_init_twiddles(e.tw + fp.tw_sub, fp.L, fp.L, s);
+    if (fp.Mp) launch_init_twiddles(e.tw + fp.tw_outer, fp.Mp, fp.Mp, s);
+    int Ns = 1;
+    for (int st = 0; st < fp.nstages; ++st) {
+      if (fp.tw4_off[st] >= 0)
+        launch_init_tw4(reinterpret_cast<Tan4*>(e.tw + fp.tw4) + fp.tw4_off[st], Ns, s);
+      Ns *= fp.radix[st];
+    }
+  }
+  launch_init_twiddles(e.tw + e.twN_off, e.p.N, e.M / 2 + 1, s);
+}
+
 int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
   auto e = std::make_shared<PlanEntry>();
   int rc = choose_params(kind, n, &e->p);
@@ -100,25 +148,10 @@ int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<Pl
   e->M = e->p.N / 2;
   rc = make_fft_plan(e->M, &e->fft);
   if (rc) return rc;
-  // twiddle tables: per pass omega_L (and omega_Mp), then omega_N for the twist
-  size_t cnt = 0;
-  for (int i = 0; i < e->fft.npass; ++i) {
-    FftPass& fp = e->fft.pass[i];
-    fp.tw_sub = cnt;
-    cnt += size_t(fp.L);
-    if (fp.Mp) { fp.tw_outer = cnt; cnt += size_t(fp.Mp); }
-  }
-  e->twN_off = cnt;
-  const size_t nN = size_t(e->M / 2 + 1);
-  cnt += nN;
+  const size_t cnt = layout_twiddles(e.get());
   TM_CHECK(cudaMalloc(&e->tw, cnt * sizeof(double2)));
   e->table_bytes += cnt * sizeof(double2);
-  for (int i = 0; i < e->fft.npass; ++i) {
-    const FftPass& fp = e->fft.pass[i];
-    launch_init_twiddles(e->tw + fp.tw_sub, fp.L, fp.L, s);
-    if (fp.Mp) launch_init_twiddles(e->tw + fp.tw_outer, fp.Mp, fp.Mp, s);
-  }
-  launch_init_twiddles(e->tw + e->twN_off, e->p.N, int64_t(nN), s);
+  init_twiddles(*e, s);
   const int64_t N = e->p.N;
   const int b = e->p.b;
   if (kind == TM_LO || kind == TM_HI) {
@@ -277,6 +310,10 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
     a.batch_stride = M;
     a.tw_sub = pe.tw + fp.tw_sub;
     a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+    a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
+    a.tw4_len = fp.tw4_len;
+    std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
+    a.need_wL = fp.need_wL ? 1 : 0;
     launch_fft_pass(-1, bufs[cur], bufs[cur ^ 1], a, 2, fp.threads, s);
     cur ^= 1;
   }
@@ -296,6 +333,10 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
     a.batch_stride = M;
     a.tw_sub = pe.tw + fp.tw_sub;
     a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+    a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
+    a.tw4_len = fp.tw4_len;
+    std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
+    a.need_wL = fp.need_wL ? 1 : 0;
     launch_fft_pass(1, bufs[cur], bufs[cur ^ 1], a, 1, fp.threads, s);
     cur ^= 1;
   }
@@ -446,16 +487,7 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t at = off; off += align_up(bytes); return at; };
   const size_t status_off = take(sizeof(DevStatus));
-  size_t cnt = 0;
-  for (int i = 0; i < e->fft.npass; ++i) {
-    FftPass& fp = e->fft.pass[i];
-    fp.tw_sub = cnt;
-    cnt += size_t(fp.L);
-    if (fp.Mp) { fp.tw_outer = cnt; cnt += size_t(fp.Mp); }
-  }
-  e->twN_off = cnt;
-  const size_t nN = size_t(e->M / 2 + 1);
-  cnt += nN;
+  const size_t cnt = layout_twiddles(e);
   const size_t tw_off = take(cnt * sizeof(double2));
   const int64_t N = e->p.N;
   const int b = e->p.b;
@@ -488,12 +520,7 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   // the previous call's contents stay in the array: clear the status word and
   // rebuild every table this call reads
   TM_CHECK(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
-  for (int i = 0; i < e->fft.npass; ++i) {
-    const FftPass& fp = e->fft.pass[i];
-    launch_init_twiddles(e->tw + fp.tw_sub, fp.L, fp.L, s);
-    if (fp.Mp) launch_init_twiddles(e->tw + fp.tw_outer, fp.Mp, fp.Mp, s);
-  }
-  launch_init_twiddles(e->tw + e->twN_off, N, int64_t(nN), s);
+  init_twiddles(*e, s);
   if (rf > 0) launch_init_maptab(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, s);
   if (rb > 0)
     launch_init_maptab(e->bwd_tab, kind == TM_LO ? kTabBeta : kTabDeltaPrime, N, b,

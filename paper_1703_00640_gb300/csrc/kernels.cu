@@ -118,6 +118,25 @@ __global__ void k_init_twiddles(double2* tab, long long len, long long count) {
   tab[m] = make_double2(cs, -sn);
 }
 
+// Tangent-form twiddles of a radix-4 stage (see launch_init_tw4).
+__global__ void k_init_tw4(Tan4* tab, int Ns) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Ns) return;
+  double s1, c1, s2, c2;
+  sincospi((double)k / (2.0 * Ns), &s1, &c1);          // theta = 2 pi k / (4 Ns) < pi/2
+  double c2s;
+  if (2 * k < Ns) {
+    sincospi((double)k / (double)Ns, &s2, &c2);        // 2 theta < pi/2
+    c2s = c2;
+  } else {
+    sincospi((double)(2 * k - Ns) / (2.0 * Ns), &s2, &c2);   // 2 theta - pi/2
+    c2s = -c2;
+  }
+  Tan4 e;
+  e.t1 = s1 / c1; e.c1 = c1; e.t2 = s2 / c2; e.c2s = c2s;
+  tab[k] = e;
+}
+
 // Coefficient rows of the ring maps (Sections 3.2 and 4.2), tab[(r-1) N + k]:
 //   alpha_{k,r} = k/(k+r) binom((k+r)/N, r) (-2^-b)^r
 //   beta_{k,r}  = binom(-k/N, r) (-2^-b)^r
@@ -407,33 +426,117 @@ template <>
 __device__ __forceinline__ void dft<7, 1>(double2* x) { dft7<1>(x); }
 
 // One Stockham stage of radix R over C sequences of length L held in shared
-// memory: butterfly j reads src[j + t L/R], applies omega_(Ns R)^(t (j mod Ns)),
-// and writes dst[(j/Ns) Ns R + (j mod Ns) + t Ns]; after all stages the result
-// is in natural order.
+// memory, in place: butterfly j reads buf[j + t L/R], applies
+// omega_(Ns R)^(t (j mod Ns)) and writes buf[(j/Ns) Ns R + (j mod Ns) + t Ns];
+// after all stages the result is in natural order. Each thread owns up to
+// ceil(4/R) butterflies (the CTA has C L / 4 threads): it reads all of their
+// inputs, the CTA synchronises, then it writes all of their outputs.
 template <int R, int S>
-__device__ __forceinline__ void stockham_stage(const double2* src, double2* dst, int L, int C,
-                                               int Ns, const double2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(double2* buf, int L, int C, int Ns,
+                                               const double2* tw, double2 (&xs)[8],
+                                               int (&base)[4], int (&kk)[4]) {
+  constexpr int MB = (4 + R - 1) / R;
   const int nb = L / R;
   const int total = C * nb;
   const int twstep = L / (Ns * R);
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
-    const int c = g / nb, j = g - c * nb;
-    const double2* s = src + c * L;
-    double2 x[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) x[t] = s[j + t * nb];
-    const int k = j % Ns;
-    if (Ns > 1 && k != 0) {
+  for (int i = 0; i < MB; ++i) {
+    const int g = threadIdx.x + i * blockDim.x;
+    base[i] = -1;
+    if (g < total) {
+      const int c = g / nb, j = g - c * nb;
+      const double2* s = buf + c * L + j;
+#pragma unroll
+      for (int t = 0; t < R; ++t) xs[i * R + t] = s[t * nb];
+      kk[i] = j % Ns;
+      base[i] = c * L + (j / Ns) * Ns * R + kk[i];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MB; ++i) {
+    if (base[i] < 0) continue;
+    double2* x = xs + i * R;
+    if (Ns > 1) {
 #pragma unroll
       for (int t = 1; t < R; ++t) {
-        const double2 w = __ldg(tw + (long long)k * t * twstep);
+        const double2 w = tw[kk[i] * t * twstep];
         x[t] = S < 0 ? cmul(x[t], w) : cmulc(x[t], w);
       }
     }
     dft<R, S>(x);
-    double2* d = dst + c * L + (j / Ns) * Ns * R + k;
+    double2* d = buf + base[i];
 #pragma unroll
     for (int t = 0; t < R; ++t) d[t * Ns] = x[t];
+  }
+}
+
+// Radix-4 Stockham stage with tangent-form twiddles, 24 FMAs per butterfly in
+// place of 12 for the three twiddle products and 16 additions. With
+// w_t = omega^(t k) (t = 1, 2, 3), w3 = w1 w2, so for the DFT of
+// (x0, w1 x1, w2 x2, w3 x3):  A, B = x0 +- w2 x2,  E, F = x1 +- w2 x3,
+// y0, y2 = A +- w1 E,  y1, y3 = B +- S i w1 F.  Each w z is c (z -+ i t z):
+// one FMA per component for the bracket, and the factor c folds into the FMA
+// that adds it. When the angle of w2 reaches pi/2, w2 = -+i c (1 -+ i t): the
+// real and imaginary parts trade places, selected on the integer pipe.
+template <int S>
+__device__ __forceinline__ double2 tan_bracket(double2 z, double t) {
+  // z (1 - i t) for the forward direction, z (1 + i t) for the inverse
+  return S < 0 ? make_double2(fma(t, z.y, z.x), fma(-t, z.x, z.y))
+               : make_double2(fma(-t, z.y, z.x), fma(t, z.x, z.y));
+}
+
+template <int S>
+__device__ __forceinline__ void radix4_tan(double2* x, Tan4 w) {
+  const double t1 = w.t1, c1 = w.c1, t2 = w.t2;
+  const long long cb = __double_as_longlong(w.c2s);
+  const bool rot = cb < 0;
+  const long long mag = cb & 0x7FFFFFFFFFFFFFFFll;
+  const long long neg = mag | (long long)0x8000000000000000ull;
+  // coefficient of the real part and of the imaginary part of w2 z
+  const double ca = __longlong_as_double(rot && S > 0 ? neg : mag);
+  const double cq = __longlong_as_double(rot && S < 0 ? neg : mag);
+  const double2 x2 = tan_bracket<S>(x[2], t2), x3 = tan_bracket<S>(x[3], t2);
+  const double p2 = rot ? x2.y : x2.x, q2 = rot ? x2.x : x2.y;
+  const double p3 = rot ? x3.y : x3.x, q3 = rot ? x3.x : x3.y;
+  const double2 x0 = x[0], x1 = x[1];
+  const double2 A = make_double2(fma(ca, p2, x0.x), fma(cq, q2, x0.y));
+  const double2 B = make_double2(fma(-ca, p2, x0.x), fma(-cq, q2, x0.y));
+  const double2 E = tan_bracket<S>(make_double2(fma(ca, p3, x1.x), fma(cq, q3, x1.y)), t1);
+  const double2 F = tan_bracket<S>(make_double2(fma(-ca, p3, x1.x), fma(-cq, q3, x1.y)), t1);
+  x[0] = make_double2(fma(c1, E.x, A.x), fma(c1, E.y, A.y));
+  x[2] = make_double2(fma(-c1, E.x, A.x), fma(-c1, E.y, A.y));
+  if (S < 0) {   // B -+ i c1 F
+    x[1] = make_double2(fma(c1, F.y, B.x), fma(-c1, F.x, B.y));
+    x[3] = make_double2(fma(-c1, F.y, B.x), fma(c1, F.x, B.y));
+  } else {       // B +- i c1 F
+    x[1] = make_double2(fma(-c1, F.y, B.x), fma(c1, F.x, B.y));
+    x[3] = make_double2(fma(c1, F.y, B.x), fma(-c1, F.x, B.y));
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void stockham_stage4t(double2* buf, int L, int C, int Ns,
+                                                 const Tan4* tw, double2 (&xs)[8],
+                                                 int (&base)[4], int (&kk)[4]) {
+  const int nb = L / 4;
+  const int total = C * nb;
+  const int g = threadIdx.x;
+  base[0] = -1;
+  if (g < total) {
+    const int c = g / nb, j = g - c * nb;
+    const double2* s = buf + c * L + j;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xs[t] = s[t * nb];
+    kk[0] = j % Ns;
+    base[0] = c * L + (j / Ns) * Ns * 4 + kk[0];
+  }
+  __syncthreads();
+  if (base[0] >= 0) {
+    radix4_tan<S>(xs, tw[kk[0]]);
+    double2* d = buf + base[0];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) d[t * Ns] = xs[t];
   }
 }
 
@@ -441,8 +544,13 @@ template <int S>
 __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p) {
   extern __shared__ double2 smem[];
   const int L = p.L, C = p.C;
-  double2* bufA = smem;
-  double2* bufB = smem + C * L;
+  double2* buf = smem;
+  const int off4 = (C * L + 1) & ~1;    // 32-byte aligned
+  Tan4* tw4s = reinterpret_cast<Tan4*>(smem + off4);
+  double2* tws = smem + off4 + 2 * p.tw4_len;   // omega_L^k, k < L (when needed)
+  for (int t = threadIdx.x; t < p.tw4_len; t += blockDim.x) tw4s[t] = p.tw4[t];
+  if (p.need_wL)
+    for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = __ldg(p.tw_sub + t);
   const long long q0 = (long long)blockIdx.x * C;
   const long long boff = (long long)blockIdx.y * p.batch_stride;
   in += boff;
@@ -458,22 +566,25 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
       const long long qa = q / p.Qc, qc = q - qa * p.Qc;
       val = in[qa * p.IA + qc * p.IC + (long long)j * p.IS];
     }
-    bufA[c * L + j] = val;
+    buf[c * L + j] = val;
   }
   __syncthreads();
   int Ns = 1;
+  double2 xs[8];                        // one register array shared by every radix case
+  int base[4], kk[4];
   for (int st = 0; st < p.nstages; ++st) {
     const int R = p.radix[st];
     switch (R) {
-      case 2: stockham_stage<2, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
-      case 3: stockham_stage<3, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
-      case 4: stockham_stage<4, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
-      case 5: stockham_stage<5, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
-      case 7: stockham_stage<7, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
-      default: stockham_stage<8, S>(bufA, bufB, L, C, Ns, p.tw_sub); break;
+      case 2: stockham_stage<2, S>(buf, L, C, Ns, tws, xs, base, kk); break;
+      case 3: stockham_stage<3, S>(buf, L, C, Ns, tws, xs, base, kk); break;
+      case 4:
+        if (Ns > 1) stockham_stage4t<S>(buf, L, C, Ns, tw4s + p.tw4_off[st], xs, base, kk);
+        else stockham_stage<4, S>(buf, L, C, Ns, tws, xs, base, kk);
+        break;
+      case 5: stockham_stage<5, S>(buf, L, C, Ns, tws, xs, base, kk); break;
+      default: stockham_stage<7, S>(buf, L, C, Ns, tws, xs, base, kk); break;
     }
     __syncthreads();
-    double2* t = bufA; bufA = bufB; bufB = t;
     Ns *= R;
   }
   const bool rowstore = p.OS == 1;
@@ -483,7 +594,7 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
     const long long q = q0 + c;
     if (q >= p.Q) continue;
     const long long qa = q / p.Qc, qc = q - qa * p.Qc;
-    double2 val = bufA[c * L + k];
+    double2 val = buf[c * L + k];
     if (p.Mp) {
       const double2 w = __ldg(p.tw_outer + qc * k);
       val = S < 0 ? cmul(val, w) : cmulc(val, w);
@@ -496,13 +607,16 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
                      int threads, cudaStream_t s) {
   static bool attr_set = false;   // shared memory above 48 KB needs the opt-in
   if (!attr_set) {
-    const int bytes = 2 * kMaxCL * int(sizeof(double2));
-    cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     attr_set = true;
   }
   const unsigned blocks = unsigned((p.Q + p.C - 1) / p.C);
-  const size_t smem = size_t(2) * p.C * p.L * sizeof(double2);
+  const size_t smem = (size_t((p.C * p.L + 1) & ~1) + 2 * size_t(p.tw4_len) +
+                      (p.need_wL ? size_t(p.L) : 0)) * sizeof(double2);
   dim3 grid(blocks, batch);
   if (dir < 0)
     k_fft_pass<-1><<<grid, threads, smem, s>>>(in, out, p);
@@ -947,6 +1061,11 @@ void launch_carry(const CarryArgs& a, cudaStream_t s) {
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s) {
   if (count <= 0) return;
   k_init_twiddles<<<unsigned((count + 255) / 256), 256, 0, s>>>(tab, len, count);
+}
+
+void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s) {
+  if (Ns <= 0) return;
+  k_init_tw4<<<unsigned((Ns + 255) / 256), 256, 0, s>>>(tab, Ns);
 }
 
 void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s) {

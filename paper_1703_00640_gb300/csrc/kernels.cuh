@@ -16,6 +16,11 @@ struct DevStatus {
 constexpr unsigned kFlagPrecision = 1u;  // a distance above the plan's bound
 constexpr unsigned kFlagC0 = 2u;         // 2^b does not divide c_0
 
+// Tangent-form twiddle pair of one radix-4 butterfly (see launch_init_tw4).
+struct __align__(32) Tan4 {
+  double t1, c1, t2, c2s;
+};
+
 // Pass descriptor as seen by the FFT kernel (plan.h's FftPass plus pointers).
 struct PassArgs {
   int L, nstages, C;
@@ -24,6 +29,10 @@ struct PassArgs {
   long long batch_stride;        // complex elements between batch entries
   const double2* tw_sub;         // omega_L^k
   const double2* tw_outer;       // omega_Mp^m (or nullptr)
+  const Tan4* tw4;            // tangent-form radix-4 stage tables
+  int tw4_len;
+  int tw4_off[kMaxStages];
+  int need_wL;
 };
 
 // Digit unpack + forward map parameters.
@@ -82,6 +91,11 @@ struct CarryArgs {
 // table initialisation
 // tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
+// Tangent-form twiddles of one radix-4 Stockham stage with Ns > 1: entry k < Ns
+// holds (t1, c1, t2, c2s) with omega_(4Ns)^k = c1 (1 - i t1) and
+// omega_(4Ns)^(2k) = c2 (1 - i t2) when its angle is below pi/2, else
+// -i c (1 - i t2) stored with c2s = -c.
+void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s);
 void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s);
 
 // pipeline stages

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/truncmul.h"
@@ -249,6 +250,9 @@ int choose_params(int kind, uint64_t n, PlanParams* out) {
 
 namespace {
 
+// Radix stages of one sub-FFT: 7, 5, 3 for the odd part, then 4s and at most
+// one 2. Radix 4 costs the same FP64 instructions per point and level as radix 8
+// (3.5) and keeps one butterfly's points per thread small.
 void radices_of(int L, FftPass* p) {
   p->nstages = 0;
   int rest = L;
@@ -256,24 +260,22 @@ void radices_of(int L, FftPass* p) {
     while (rest % r == 0) { p->radix[p->nstages++] = r; rest /= r; }
   int twos = 0;
   while (rest % 2 == 0) { rest /= 2; ++twos; }
-  while (twos >= 3 && !(twos == 4)) { p->radix[p->nstages++] = 8; twos -= 3; }
-  if (twos == 4) { p->radix[p->nstages++] = 4; p->radix[p->nstages++] = 4; twos = 0; }
-  if (twos == 2) { p->radix[p->nstages++] = 4; twos = 0; }
-  if (twos == 1) { p->radix[p->nstages++] = 2; twos = 0; }
+  for (; twos >= 2; twos -= 2) p->radix[p->nstages++] = 4;
+  if (twos) p->radix[p->nstages++] = 2;
 }
 
 void shape(FftPass* p, int64_t ctas_wanted) {
-  // sequences per CTA: fill about 2048 points, but keep >= ctas_wanted CTAs.
-  int C = std::max(1, 2048 / p->L);
+  // sequences per CTA: fill about kPoints points, keeping >= ctas_wanted CTAs;
+  // one butterfly of the largest radix per thread
+  int target = 1024;
+  if (const char* e = std::getenv("TM_FFT_POINTS")) target = std::atoi(e);
+  int C = std::max(1, target / p->L);
   while (C > 1 && (p->Q + C - 1) / C < ctas_wanted) C /= 2;
-  C = std::min<int64_t>(C, p->Q);
+  C = int(std::min<int64_t>(C, p->Q));
   while (int64_t(C) * p->L > kMaxCL) --C;
   p->C = std::max(1, C);
-  int maxpts = p->C * p->L;
-  int minr = 8;
-  for (int s = 0; s < p->nstages; ++s) minr = std::min(minr, p->radix[s]);
-  int t = (maxpts / std::max(2, minr) + 31) / 32 * 32;   // one butterfly per thread
-  p->threads = std::max(32, std::min(512, t));
+  const int t = (p->C * p->L / 4 + 31) / 32 * 32;   // one radix-4 butterfly per thread
+  p->threads = std::max(32, std::min(1024, t));
 }
 
 }  // namespace
