@@ -25,7 +25,7 @@ struct PlanEntry {
   int64_t M = 0;
   double2* tw = nullptr;       // all twiddle tables
   size_t twN_off = 0;          // omega_N^k, k <= M/2 (real-FFT twist)
-  double* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1
+  long long* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1, fixed point
   double* bwd_tab = nullptr;   // beta rows (low) or delta' rows (high)
   double* bwd_tab2 = nullptr;  // high: delta rows r = 1..lam_bwd-1
   double* small = nullptr;     // high: kappa[nkappa] then rho^-j[ntheta]
@@ -159,7 +159,8 @@ int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<Pl
     const int rb = kind == TM_LO ? e->p.lam_bwd - 1 : e->p.lam_bwd;
     if (rf > 0) {
       TM_CHECK(cudaMalloc(&e->fwd_tab, size_t(rf) * N * 8));
-      launch_init_maptab(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, s);
+      launch_init_maptab_fx(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf,
+                            fx_q(b), s);
       e->table_bytes += size_t(rf) * N * 8;
     }
     if (rb > 0) {
@@ -508,7 +509,7 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   const size_t ws_off = take(ws_bytes);
   if (off > TM_STATIC_SCRATCH_BYTES) return TM_ERANGE;
   e->tw = reinterpret_cast<double2*>(base + tw_off);
-  e->fwd_tab = rf > 0 ? reinterpret_cast<double*>(base + fwd_off) : nullptr;
+  e->fwd_tab = rf > 0 ? reinterpret_cast<long long*>(base + fwd_off) : nullptr;
   e->bwd_tab = rb > 0 ? reinterpret_cast<double*>(base + bwd_off) : nullptr;
   e->bwd_tab2 = r2 > 0 ? reinterpret_cast<double*>(base + bwd2_off) : nullptr;
   e->small = kind == TM_HI ? reinterpret_cast<double*>(base + small_off) : nullptr;
@@ -521,7 +522,8 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   // rebuild every table this call reads
   TM_CHECK(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
   init_twiddles(*e, s);
-  if (rf > 0) launch_init_maptab(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, s);
+  if (rf > 0)
+    launch_init_maptab_fx(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, fx_q(b), s);
   if (rb > 0)
     launch_init_maptab(e->bwd_tab, kind == TM_LO ? kTabBeta : kTabDeltaPrime, N, b,
                        kind == TM_LO ? rb : e->p.lam_bwd, s);

@@ -172,6 +172,17 @@ __global__ void k_init_maptab(double* tab, int which, long long N, int b, int ro
   }
 }
 
+__global__ void k_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const double dk = (double)k, dN = (double)N;
+  for (int r = 1; r <= rows; ++r) {
+    const double v = which == kTabAlpha ? dk / (dk + r) * binom_scaled((dk + r) / dN, r, b)
+                                        : dk / (dk + r) * binom_scaled(-(dk + r) / dN, r, b);
+    tab[(long long)(r - 1) * N + k] = __double2ll_rn(scale2(v, Q + r * b));
+  }
+}
+
 // ------------------------------------------------------------ digits
 
 // bits [pos, pos + cnt) of the n-bit integer in `limbs` (cnt <= 32, pos may be
@@ -214,38 +225,47 @@ constexpr int kFwdThreads = 256;
 constexpr int kMaxLam = 24;
 
 // Low product: U~ = sum_{r<lam} alpha*_r U (Algorithm 2, convert step; Proposition 3.15),
-// U~_j = U_j + sum_{r=1}^{lam-1} alpha_{(j-r) mod N, r} U_{(j-r) mod N}.
+// U~_j = U_j + sum_{r=1}^{lam-1} alpha_{(j-r) mod N, r} U_{(j-r) mod N}, evaluated in
+// fixed point on the integer pipe: with A_{k,r} = round(alpha_{k,r} 2^(Q+rb)),
+// S_j = U_j 2^Q + sum_r (A_{k,r} U_k) >> rb is exact up to the table rounding and
+// the shifts, |S_j| < 2^61, and U~_j = S_j 2^-Q after one rounding conversion.
 // Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1, split step).
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind) {
-  __shared__ double du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
   const int span = kFwdTile + halo;
   for (int t = threadIdx.x; t < span; t += blockDim.x) {
     long long p = j0 - halo + t;                 // digit position, cyclic mod N
     if (p < 0) p += a.N;
-    double xu = 0.0, xv = 0.0;
+    int xu = 0, xv = 0;
     if (p < a.N && p < a.nd) {
-      xu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false));
-      xv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false));
+      xu = balanced_digit(a.u, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
+      xv = balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
     }
     du[t] = xu;
     dv[t] = xv;
   }
   __syncthreads();
+  const int Q = fx_q(a.b);
   for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= a.N) break;
-    double su = du[t + halo], sv = dv[t + halo];
+    if (a.lam == 0) {
+      a.X[j] = i2d_exact(du[t]);
+      a.X[a.N + j] = i2d_exact(dv[t]);
+      continue;
+    }
+    long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
     for (int r = 1; r < a.lam; ++r) {
       long long k = j - r;
       if (k < 0) k += a.N;
-      const double al = __ldg(a.tab + (long long)(r - 1) * a.N + k);
-      su = fma(al, du[t + halo - r], su);
-      sv = fma(al, dv[t + halo - r], sv);
+      const long long A = __ldg(a.tab + (long long)(r - 1) * a.N + k);
+      su += (A * du[t + halo - r]) >> (r * a.b);
+      sv += (A * dv[t + halo - r]) >> (r * a.b);
     }
-    a.X[j] = su;
-    a.X[a.N + j] = sv;
+    a.X[j] = scale2(__ll2double_rn(su), -Q);
+    a.X[a.N + j] = scale2(__ll2double_rn(sv), -Q);
   }
 }
 
@@ -253,13 +273,24 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind
 // F' = F mod C: F'_i = F_i + kappa_i F_N (eq. 4.5), then
 // U~_j = sum_{r<lam} gamma_{(j-r) mod N, r} F'_{(j-r) mod N}, and
 // theta = rho^-N F(rho) = sum_j rho^-j F_(N-j).
+// Outputs that read a kappa-corrected F'_i (j < nkappa + lam - 1, all in the
+// first tile) are evaluated in FP64; the others read integer digits only and use
+// the fixed-point form of the low product's map.
+__device__ __forceinline__ double fx_coef(const long long* tab, long long N, int r, long long k,
+                                          int Q, int b) {
+  return scale2(__ll2double_rn(__ldg(tab + (long long)(r - 1) * N + k)), -(Q + r * b));
+}
+
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a) {
-  __shared__ double du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
   __shared__ double topu, topv;
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam - 1;
   const int span = kFwdTile + halo;
   const long long N = a.N;
+  const bool head = blockIdx.x == 0;
+  const int Q = fx_q(a.b);
   if (threadIdx.x == 0) {
     topu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, N, N, true));
     topv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, N, N, true));
@@ -268,36 +299,52 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a) {
   for (int t = threadIdx.x; t < span; t += blockDim.x) {
     long long p = j0 - halo + t;
     if (p < 0) p += N;
-    double xu = 0.0, xv = 0.0;
+    int xu = 0, xv = 0;
     if (p < N) {
-      xu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, p, N, true));
-      xv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true));
-      if (p < a.nkappa) {
-        const double kp = __ldg(a.kappa + p);
-        xu = fma(kp, topu, xu);
-        xv = fma(kp, topv, xv);
-      }
+      xu = balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, p, N, true);
+      xv = balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true);
     }
     du[t] = xu;
     dv[t] = xv;
+    if (head) {
+      double yu = i2d_exact(xu), yv = i2d_exact(xv);
+      if (p < a.nkappa) {
+        const double kp = __ldg(a.kappa + p);
+        yu = fma(kp, topu, yu);
+        yv = fma(kp, topv, yv);
+      }
+      fu[t] = yu;
+      fv[t] = yv;
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= N) break;
-    double su = du[t + halo], sv = dv[t + halo];
-    for (int r = 1; r < a.lam; ++r) {
-      long long k = j - r;
-      if (k < 0) k += N;
-      const double g = __ldg(a.tab + (long long)(r - 1) * N + k);
-      su = fma(g, du[t + halo - r], su);
-      sv = fma(g, dv[t + halo - r], sv);
+    if (head) {
+      double su = fu[t + halo], sv = fv[t + halo];
+      for (int r = 1; r < a.lam; ++r) {
+        long long k = j - r;
+        if (k < 0) k += N;
+        const double g = fx_coef(a.tab, N, r, k, Q, a.b);
+        su = fma(g, fu[t + halo - r], su);
+        sv = fma(g, fv[t + halo - r], sv);
+      }
+      a.X[j] = su;
+      a.X[N + j] = sv;
+    } else {
+      long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
+      for (int r = 1; r < a.lam; ++r) {
+        const long long A = __ldg(a.tab + (long long)(r - 1) * N + (j - r));
+        su += (A * du[t + halo - r]) >> (r * a.b);
+        sv += (A * dv[t + halo - r]) >> (r * a.b);
+      }
+      a.X[j] = scale2(__ll2double_rn(su), -Q);
+      a.X[N + j] = scale2(__ll2double_rn(sv), -Q);
     }
-    a.X[j] = su;
-    a.X[N + j] = sv;
   }
   // theta: block 0, two threads (u and v), ntheta terms of rho^-j F_(N-j)
-  if (blockIdx.x == 0 && (threadIdx.x == 0 || threadIdx.x == 32)) {
+  if (head && (threadIdx.x == 0 || threadIdx.x == 32)) {
     const unsigned long long* src = threadIdx.x == 0 ? a.u : a.v;
     double th = 0.0;
     for (int j = a.ntheta - 1; j >= 0; --j) {
@@ -1066,6 +1113,12 @@ void launch_init_twiddles(double2* tab, long long len, long long count, cudaStre
 void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s) {
   if (Ns <= 0) return;
   k_init_tw4<<<unsigned((Ns + 255) / 256), 256, 0, s>>>(tab, Ns);
+}
+
+void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,
+                           cudaStream_t s) {
+  if (rows <= 0) return;
+  k_init_maptab_fx<<<unsigned((N + 255) / 256), 256, 0, s>>>(tab, which, N, b, rows, Q);
 }
 
 void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s) {

@@ -45,7 +45,8 @@ struct FwdArgs {
   long long N;                   // transform length (real)
   long long nd;                  // digits per operand
   int lam;                       // map terms (0 for the full product)
-  const double* tab;             // (lam-1) x N coefficient rows, r = 1..lam-1
+  const long long* tab;          // (lam-1) x N fixed-point rows, r = 1..lam-1:
+                                 // round(coef_{k,r} 2^(Q + r b)), Q = fx_q(b)
   const double* kappa;           // high: kappa_i = 2^b / rho^(i+1), i < nkappa
   int nkappa;
   const double* rho_pow;         // high: rho^-j, j < ntheta
@@ -88,6 +89,10 @@ struct CarryArgs {
   unsigned char* cin_block;      // scratch: per-block carry-in (+1 encoded)
 };
 
+// Fraction bits of the fixed-point forward maps: coefficient products
+// (coef 2^(Q + r b)) x digit stay below 2^61.
+__host__ __device__ inline int fx_q(int b) { return 61 - b; }
+
 // table initialisation
 // tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
@@ -97,6 +102,9 @@ void launch_init_twiddles(double2* tab, long long len, long long count, cudaStre
 // -i c (1 - i t2) stored with c2s = -c.
 void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s);
 void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s);
+// The same coefficients in fixed point: tab[(r-1) N + k] = round(coef_{k,r} 2^(Q + r b)).
+void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,
+                           cudaStream_t s);
 
 // pipeline stages
 void launch_fwd(int kind, const FwdArgs& a, cudaStream_t s);
