@@ -166,6 +166,47 @@ int tm_mul_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
                   uint64_t n_bits, void* stream, tm_report* rep);
 
 /*
+ * Batched products (many products of uneven sizes in one launch).
+ *
+ * tm_desc describes one product: kind, n_bits and DEVICE pointers as for tm_mul
+ * (each out must not overlap its own u or v; different products may share
+ * inputs but not outputs).
+ *
+ * tm_batch_create plans every product, builds the resident tables, allocates the
+ * batch's device memory, and records the whole batch as one CUDA graph:
+ * products with the same plan (kind, b, N) run as one launch per phase with the
+ * product index in the grid, different plans run on concurrent branches of the
+ * graph. It waits for `stream` (table set-up) and must not be called while
+ * `stream` is being captured. The descriptors are copied; the pointers they
+ * hold must stay valid for the life of the batch.
+ * tm_batch_launch enqueues the graph on `stream` (one graph launch); the inputs
+ * are read when it runs, so a batch can be relaunched on new operand values.
+ * tm_batch_status waits for `stream` and returns TM_OK or TM_EPRECISION for
+ * everything launched since the last status read; rep->margin is the largest
+ * rounding distance, rep->e_max the smallest bound of the batch's products.
+ * tm_batch_destroy frees the batch (no launch of it may be in flight).
+ * tm_mul_batch is the one-shot form: create, launch, wait, destroy.
+ * Sources: Algorithms 1-3 per product; the batching has no counterpart in the
+ * paper.
+ */
+typedef struct tm_desc {
+  int32_t kind;           /* TM_FULL, TM_LO or TM_HI */
+  int32_t reserved;       /* 0 */
+  uint64_t n_bits;
+  uint64_t* out;
+  const uint64_t* u;
+  const uint64_t* v;
+} tm_desc;
+
+typedef struct tm_batch tm_batch;
+
+int tm_batch_create(tm_batch** batch, const tm_desc* descs, uint32_t count, void* stream);
+int tm_batch_launch(tm_batch* batch, void* stream);
+int tm_batch_status(tm_batch* batch, void* stream, tm_report* rep);
+int tm_batch_destroy(tm_batch* batch);
+int tm_mul_batch(const tm_desc* descs, uint32_t count, void* stream, tm_report* rep);
+
+/*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
  * for checking the method stage by stage:
  *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2,

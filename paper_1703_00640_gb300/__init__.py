@@ -31,6 +31,12 @@ class Report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Desc(ctypes.Structure):
+    """tm_desc (include/truncmul.h)."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_bits", ctypes.c_uint64),
+                ("out", ctypes.c_void_p), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+
+
 class TruncMulError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})")
@@ -41,7 +47,8 @@ NPHASES = 6
 PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "carry"]
 STATIC_MAX_BITS = 65536
 EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
-           "tm_mul_static", "tm_coeffs",
+           "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
+           "tm_batch_destroy", "tm_mul_batch", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -72,10 +79,19 @@ def load(path: str = None):
     lib.tm_mul_events.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P,
                                   ctypes.POINTER(ctypes.c_void_p), R]
     lib.tm_plan_query.argtypes = [ctypes.c_int, ctypes.c_uint64, R]
+    D = ctypes.POINTER(Desc)
+    lib.tm_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), D, ctypes.c_uint32, P]
+    lib.tm_batch_launch.argtypes = [P, P]
+    lib.tm_batch_status.argtypes = [P, P, R]
+    lib.tm_batch_destroy.argtypes = [P]
+    lib.tm_mul_batch.argtypes = [D, ctypes.c_uint32, P, R]
     lib.tm_stream_status.argtypes = [P, R]
     lib.tm_release.argtypes = []
     lib.tm_strerror.argtypes = [ctypes.c_int]
     lib.tm_strerror.restype = ctypes.c_char_p
+    for name in ("tm_batch_create", "tm_batch_launch", "tm_batch_status", "tm_batch_destroy",
+                 "tm_mul_batch"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("tm_mul", "tm_mul_host", "tm_mul_events", "tm_mul_static", "tm_coeffs", "tm_plan_query", "tm_stream_status",
                  "tm_release"):
         getattr(lib, name).restype = ctypes.c_int
@@ -161,6 +177,65 @@ def mul_static(kind, u, v, n_bits: int, out, stream=None, report: bool = True):
     rc = load().tm_mul_static(_kind(kind), _ptr(out), _ptr(u), _ptr(v), int(n_bits),
                               _stream_ptr(stream), ctypes.byref(rep) if rep is not None else None)
     return rc, (rep.as_dict() if rep is not None else None)
+
+
+def _descs(items):
+    arr = (Desc * len(items))()
+    for i, (kind, n_bits, out, u, v) in enumerate(items):
+        arr[i].kind = _kind(kind)
+        arr[i].reserved = 0
+        arr[i].n_bits = int(n_bits)
+        arr[i].out = out.data_ptr()
+        arr[i].u = u.data_ptr()
+        arr[i].v = v.data_ptr()
+    return arr
+
+
+class Batch:
+    """tm_batch: many products recorded once as a CUDA graph, relaunched at will.
+    items: list of (kind, n_bits, out, u, v) with device tensors (kept alive here)."""
+
+    def __init__(self, items, stream=None):
+        self._items = list(items)          # keep the tensors alive
+        self._h = ctypes.c_void_p()
+        arr = _descs(self._items)
+        rc = load().tm_batch_create(ctypes.byref(self._h), arr, len(arr), _stream_ptr(stream))
+        if rc:
+            self._h = None
+            raise TruncMulError(rc, "tm_batch_create")
+
+    def launch(self, stream=None):
+        rc = load().tm_batch_launch(self._h, _stream_ptr(stream))
+        if rc:
+            raise TruncMulError(rc, "tm_batch_launch")
+
+    def status(self, stream=None) -> dict:
+        rep = Report()
+        rc = load().tm_batch_status(self._h, _stream_ptr(stream), ctypes.byref(rep))
+        d = rep.as_dict()
+        d["rc"] = rc
+        return d
+
+    def close(self):
+        if self._h:
+            load().tm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mul_batch(items, stream=None) -> dict:
+    """tm_mul_batch (one shot). items as for Batch. Returns the report."""
+    arr = _descs(items)
+    rep = Report()
+    rc = load().tm_mul_batch(arr, len(arr), _stream_ptr(stream), ctypes.byref(rep))
+    if rc:
+        raise TruncMulError(rc, "tm_mul_batch")
+    return rep.as_dict()
 
 
 def mul_lo(u, v, n_bits, **kw):

@@ -14,35 +14,14 @@
 #include "../../include/truncmul.h"
 #include "kernels.cuh"
 #include "plan.h"
+#include "runtime.h"
 
 namespace tmul {
+
 namespace {
-
-// Resident device tables of one (device, kind, n).
-struct PlanEntry {
-  PlanParams p;
-  FftPlan fft;
-  int64_t M = 0;
-  double2* tw = nullptr;       // all twiddle tables
-  size_t twN_off = 0;          // omega_N^k, k <= M/2 (real-FFT twist)
-  long long* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1, fixed point
-  double* bwd_tab = nullptr;   // beta rows (low) or delta' rows (high)
-  double* bwd_tab2 = nullptr;  // high: delta rows r = 1..lam_bwd-1
-  double* small = nullptr;     // high: kappa[nkappa] then rho^-j[ntheta]
-  int nkappa = 0, ntheta = 0;
-  size_t table_bytes = 0;
-};
-
-struct Workspace {
-  char* base = nullptr;
-  size_t size = 0;
-  DevStatus* status = nullptr;
-  char* io = nullptr;          // staging for tm_mul_host
-  size_t io_size = 0;
-};
-
 std::mutex g_mu;
-std::map<std::tuple<int, int, uint64_t>, std::shared_ptr<PlanEntry>> g_plans;
+std::map<std::tuple<int, int, int, int64_t, int>, std::shared_ptr<PlanEntry>> g_plans;
+std::map<std::pair<int, uint64_t>, PlanParams> g_params;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
 int cuda_fail(cudaError_t e) {
@@ -58,6 +37,8 @@ int cuda_fail(cudaError_t e) {
       return cuda_fail(e_);                           \
     }                                                 \
   } while (0)
+
+}  // namespace
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -141,12 +122,14 @@ void init_twiddles(const PlanEntry& e, cudaStream_t s) {
   launch_init_twiddles(e.tw + e.twN_off, e.p.N, e.M / 2 + 1, s);
 }
 
-int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
+namespace {
+
+int build_tables(const PlanParams& p, bool single, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
   auto e = std::make_shared<PlanEntry>();
-  int rc = choose_params(kind, n, &e->p);
-  if (rc) return rc;
+  e->p = p;
+  const int kind = p.kind;
   e->M = e->p.N / 2;
-  rc = make_fft_plan(e->M, &e->fft);
+  int rc = make_fft_plan(e->M, &e->fft, single);
   if (rc) return rc;
   const size_t cnt = layout_twiddles(e.get());
   TM_CHECK(cudaMalloc(&e->tw, cnt * sizeof(double2)));
@@ -194,25 +177,43 @@ int build_plan(int dev, int kind, uint64_t n, cudaStream_t s, std::shared_ptr<Pl
   }
   TM_CHECK(cudaGetLastError());
   TM_CHECK(cudaStreamSynchronize(s));
-  (void)dev;
   *out = e;
   return TM_OK;
 }
 
-int get_plan(int kind, uint64_t n, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
+}  // namespace
+
+int get_params(int kind, uint64_t n, PlanParams* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_params.find(std::make_pair(kind, n));
+    if (it != g_params.end()) { *out = it->second; return TM_OK; }
+  }
+  PlanParams p;
+  const int rc = choose_params(kind, n, &p);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_params[std::make_pair(kind, n)] = p;
+  *out = p;
+  return TM_OK;
+}
+
+int get_tables(const PlanParams& p, bool single, cudaStream_t s, std::shared_ptr<PlanEntry>* out) {
   int dev = 0;
   TM_CHECK(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_mu);
-  auto key = std::make_tuple(dev, kind, n);
+  auto key = std::make_tuple(dev, p.kind, p.b, p.N, single ? 1 : 0);
   auto it = g_plans.find(key);
   if (it != g_plans.end()) { *out = it->second; return TM_OK; }
   std::shared_ptr<PlanEntry> e;
-  const int rc = build_plan(dev, kind, n, s, &e);
+  const int rc = build_tables(p, single, s, &e);
   if (rc) return rc;
   g_plans[key] = e;
   *out = e;
   return TM_OK;
 }
+
+namespace {
 
 int get_workspace(cudaStream_t s, size_t bytes, Workspace** out) {
   int dev = 0;
@@ -262,140 +263,40 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
-// Enqueues the whole product; `coeff_out` receives the rounded coefficients and
-// stops the pipeline before the carry scan when non-null.
-int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
-            cudaStream_t s, const PlanEntry& pe, Workspace& ws, int64_t* coeff_out,
-            void* const* events) {
-  auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
-  };
-  mark(0);
-  const PlanParams& p = pe.p;
-  const int64_t N = p.N, M = pe.M;
-  const size_t region = std::max(align_up(size_t(2) * M * sizeof(double2)),
-                                 align_up(size_t(N + 2) * 8));
-  double2* R0 = reinterpret_cast<double2*>(ws.base);
-  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
-  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
-  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
-  FwdArgs fa{};
-  fa.u = reinterpret_cast<const unsigned long long*>(u);
-  fa.v = reinterpret_cast<const unsigned long long*>(v);
-  fa.n = n;
-  fa.nlimbs = limbs_of(n);
-  fa.b = p.b;
-  fa.N = N;
-  fa.nd = p.n_digits;
-  fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
-  fa.tab = pe.fwd_tab;
-  fa.kappa = pe.small;
-  fa.nkappa = pe.nkappa;
-  fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
-  fa.ntheta = pe.ntheta;
-  fa.s0 = int64_t(N + 1) * p.b - int64_t(n);
-  fa.X = reinterpret_cast<double*>(R0);
-  fa.theta = theta;
-  launch_fwd(kind, fa, s);
-  mark(1);
-  // 2. forward FFTs of both operands (complex length M, batch 2)
-  double2* bufs[2] = {R0, R1};
-  int cur = 0;
-  for (int i = 0; i < pe.fft.npass; ++i) {
-    const FftPass& fp = pe.fft.pass[i];
-    PassArgs a{};
-    a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
-    std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
-    a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
-    a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
-    a.batch_stride = M;
-    a.tw_sub = pe.tw + fp.tw_sub;
-    a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
-    a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
-    a.tw4_len = fp.tw4_len;
-    std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
-    a.need_wL = fp.need_wL ? 1 : 0;
-    launch_fft_pass(-1, bufs[cur], bufs[cur ^ 1], a, 2, fp.threads, s);
-    cur ^= 1;
-  }
-  mark(2);
-  // 3. real-FFT twist, pointwise product, inverse pre-twist
-  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), s);
-  cur ^= 1;
-  mark(3);
-  // 4. inverse FFT (batch 1)
-  for (int i = 0; i < pe.fft.npass; ++i) {
-    const FftPass& fp = pe.fft.pass[i];
-    PassArgs a{};
-    a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
-    std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
-    a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
-    a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
-    a.batch_stride = M;
-    a.tw_sub = pe.tw + fp.tw_sub;
-    a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
-    a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
-    a.tw4_len = fp.tw4_len;
-    std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
-    a.need_wL = fp.need_wL ? 1 : 0;
-    launch_fft_pass(1, bufs[cur], bufs[cur ^ 1], a, 1, fp.threads, s);
-    cur ^= 1;
-  }
-  mark(4);
-  // 5. back map + round (convert-back and rounding of Algorithms 1-3)
-  double2* wbuf = bufs[cur];
-  long long* cbuf = reinterpret_cast<long long*>(bufs[cur ^ 1]);
-  BackArgs ba{};
-  ba.w = reinterpret_cast<const double*>(wbuf);
-  ba.N = N;
-  ba.b = p.b;
-  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
-  ba.tab = pe.bwd_tab;
-  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
-  ba.kappa = pe.small;
-  ba.nkappa = pe.nkappa;
-  ba.theta = theta;
-  ba.rho = p.rho;
-  ba.c = cbuf;
-  ba.count = kind == TM_HI ? N + 1 : N;
-  ba.emax_fx = (unsigned long long)std::ldexp(p.e_max, 63);
-  ba.status = ws.status;
-  launch_back(kind, ba, s);
-  mark(5);
-  if (coeff_out) {
-    TM_CHECK(cudaMemcpyAsync(coeff_out, cbuf, size_t(ba.count) * 8, cudaMemcpyDeviceToDevice, s));
-    TM_CHECK(cudaGetLastError());
-    return TM_OK;
-  }
-  // 6. overlap-add and carries into the output limbs
-  int64_t nS, shift, rbit;
-  carry_shape(p, &nS, &shift, &rbit);
-  char* scratch = reinterpret_cast<char*>(wbuf);   // the inverse output is consumed
-  CarryArgs ca{};
-  ca.c = cbuf;
-  ca.K = kind == TM_HI ? N + 1 : N;
-  ca.b = p.b;
-  ca.kind = kind;
-  ca.nS = nS;
-  ca.round_bit = rbit;
-  ca.shift_bits = shift;
-  ca.nout = out_limbs(kind, n);
-  ca.top_mask = (kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
-  ca.out = reinterpret_cast<unsigned long long*>(out);
-  ca.r = reinterpret_cast<unsigned long long*>(scratch);
-  ca.fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
-  ca.cin_block = ca.fblock + align_up(size_t(nS / 512 + 2));
-  launch_carry(ca, s);
-  mark(6);
-  TM_CHECK(cudaGetLastError());
-  return TM_OK;
+}  // namespace
+
+void ensure_kernel_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] { set_fft_smem_attribute(); });
 }
 
-int read_status(cudaStream_t s, Workspace& ws, tm_report* rep) {
+int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
+               long long stride, cudaStream_t s) {
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    const FftPass& fp = pe.fft.pass[i];
+    PassArgs a{};
+    a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
+    std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
+    a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
+    a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
+    a.batch_stride = stride;
+    a.tw_sub = pe.tw + fp.tw_sub;
+    a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+    a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
+    a.tw4_len = fp.tw4_len;
+    std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
+    a.need_wL = fp.need_wL ? 1 : 0;
+    launch_fft_pass(dir, bufs[cur], bufs[cur ^ 1], a, batch, fp.threads, s);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+int read_status(cudaStream_t s, DevStatus* status, tm_report* rep) {
   TM_CHECK(cudaStreamSynchronize(s));
   DevStatus st{};
-  TM_CHECK(cudaMemcpyAsync(&st, ws.status, sizeof(st), cudaMemcpyDeviceToHost, s));
-  TM_CHECK(cudaMemsetAsync(ws.status, 0, sizeof(DevStatus), s));
+  TM_CHECK(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  TM_CHECK(cudaMemsetAsync(status, 0, sizeof(DevStatus), s));
   TM_CHECK(cudaStreamSynchronize(s));
   const int code = st.flags ? TM_EPRECISION : TM_OK;
   if (rep) {
@@ -420,6 +321,106 @@ void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
   rep->table_bytes = 0;
 }
 
+namespace {
+
+// Enqueues one whole product with parameters p and tables pe; `coeff_out`
+// receives the rounded coefficients and stops the pipeline before the carry
+// scan when non-null.
+int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+            cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
+            int64_t* coeff_out, void* const* events) {
+  auto mark = [&](int i) {
+    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
+  };
+  ensure_kernel_attributes();
+  mark(0);
+  const int64_t N = p.N, M = pe.M;
+  const size_t region = std::max(align_up(size_t(2) * M * sizeof(double2)),
+                                 align_up(size_t(N + 2) * 8));
+  double2* R0 = reinterpret_cast<double2*>(ws.base);
+  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
+  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
+  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
+  FwdArgs fa{};
+  fa.u = reinterpret_cast<const unsigned long long*>(u);
+  fa.v = reinterpret_cast<const unsigned long long*>(v);
+  fa.n = n;
+  fa.nlimbs = limbs_of(n);
+  fa.b = p.b;
+  fa.N = N;
+  fa.nd = p.n_digits;
+  fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
+  fa.tab = pe.fwd_tab;
+  fa.kappa = pe.small;
+  fa.nkappa = pe.nkappa;
+  fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
+  fa.ntheta = pe.ntheta;
+  fa.s0 = int64_t(N + 1) * p.b - int64_t(n);
+  fa.X = reinterpret_cast<double*>(R0);
+  fa.theta = theta;
+  launch_fwd(kind, fa, 1, s);
+  mark(1);
+  // 2. forward FFTs of both operands (complex length M, batch 2)
+  double2* bufs[2] = {R0, R1};
+  int cur = launch_fft(pe, bufs, 0, -1, 2, M, s);
+  mark(2);
+  // 3. real-FFT twist, pointwise product, inverse pre-twist
+  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), 1, 0,
+               0, s);
+  cur ^= 1;
+  mark(3);
+  // 4. inverse FFT (batch 1)
+  cur = launch_fft(pe, bufs, cur, 1, 1, M, s);
+  mark(4);
+  // 5. back map + round (convert-back and rounding of Algorithms 1-3)
+  double2* wbuf = bufs[cur];
+  long long* cbuf = reinterpret_cast<long long*>(bufs[cur ^ 1]);
+  BackArgs ba{};
+  ba.w = reinterpret_cast<const double*>(wbuf);
+  ba.N = N;
+  ba.b = p.b;
+  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
+  ba.tab = pe.bwd_tab;
+  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  ba.kappa = pe.small;
+  ba.nkappa = pe.nkappa;
+  ba.theta = theta;
+  ba.rho = p.rho;
+  ba.c = cbuf;
+  ba.count = kind == TM_HI ? N + 1 : N;
+  ba.emax_fx = (unsigned long long)std::ldexp(p.e_max, 63);
+  ba.status = ws.status;
+  launch_back(kind, ba, 1, s);
+  mark(5);
+  if (coeff_out) {
+    TM_CHECK(cudaMemcpyAsync(coeff_out, cbuf, size_t(ba.count) * 8, cudaMemcpyDeviceToDevice, s));
+    TM_CHECK(cudaGetLastError());
+    return TM_OK;
+  }
+  // 6. overlap-add and carries into the output limbs
+  int64_t nS, shift, rbit;
+  carry_shape(p, &nS, &shift, &rbit);
+  char* scratch = reinterpret_cast<char*>(wbuf);   // the inverse output is consumed
+  CarryArgs ca{};
+  ca.c = cbuf;
+  ca.K = kind == TM_HI ? N + 1 : N;
+  ca.b = p.b;
+  ca.kind = kind;
+  ca.nS = nS;
+  ca.round_bit = rbit;
+  ca.shift_bits = shift;
+  ca.nout = out_limbs(kind, n);
+  ca.top_mask = (kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+  ca.out = reinterpret_cast<unsigned long long*>(out);
+  ca.r = reinterpret_cast<unsigned long long*>(scratch);
+  ca.fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
+  ca.cin_block = ca.fblock + align_up(size_t(nS / 512 + 2));
+  launch_carry(ca, 1, s);
+  mark(6);
+  TM_CHECK(cudaGetLastError());
+  return TM_OK;
+}
+
 int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n, void* stream,
         tm_report* rep, int64_t* coeff_out, void* const* events = nullptr) {
   if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
@@ -431,18 +432,21 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
     if (overlaps(out, ob, u, in_bytes) || overlaps(out, ob, v, in_bytes)) return TM_EALIAS;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PlanParams p;
+  int rc = get_params(kind, n, &p);
+  if (rc) return rc;
   std::shared_ptr<PlanEntry> pe;
-  int rc = get_plan(kind, n, s, &pe);
+  rc = get_tables(p, false, s, &pe);
   if (rc) return rc;
   Workspace* ws = nullptr;
-  rc = get_workspace(s, workspace_bytes(pe->p), &ws);
+  rc = get_workspace(s, workspace_bytes(p), &ws);
   if (rc) return rc;
-  rc = enqueue(kind, out, u, v, n, s, *pe, *ws, coeff_out, events);
+  rc = enqueue(kind, out, u, v, n, s, p, *pe, *ws, coeff_out, events);
   if (rc) return rc;
   if (!rep) return TM_OK;
-  fill_plan_report(pe->p, pe->fft, rep);
+  fill_plan_report(p, pe->fft, rep);
   rep->table_bytes = pe->table_bytes;
-  return read_status(s, *ws, rep);
+  return read_status(s, ws->status, rep);
 }
 
 // ------------------------------------------- products without allocation
@@ -560,12 +564,12 @@ int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, ui
   Workspace ws;
   rc = static_plan(kind, base, s, &pe, &ws);
   if (rc) return rc;
-  rc = enqueue(kind, out, u, v, n, s, pe, ws, nullptr, nullptr);
+  rc = enqueue(kind, out, u, v, n, s, pe.p, pe, ws, nullptr, nullptr);
   if (rc) return rc;
   if (!rep) return TM_OK;
   fill_plan_report(pe.p, pe.fft, rep);
   rep->table_bytes = 0;
-  return read_status(s, ws, rep);
+  return read_status(s, ws.status, rep);
 }
 
 }  // namespace
@@ -642,7 +646,7 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
 int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep) {
   if (!rep) return TM_EINVAL;
   tmul::PlanParams p;
-  int rc = tmul::choose_params(kind, n_bits, &p);
+  int rc = tmul::get_params(kind, n_bits, &p);
   if (rc) return rc;
   tmul::FftPlan f;
   rc = tmul::make_fft_plan(p.N / 2, &f);
@@ -664,7 +668,7 @@ int tm_stream_status(void* stream, tm_report* rep) {
     }
     ws = &it->second;
   }
-  return tmul::read_status(static_cast<cudaStream_t>(stream), *ws, rep);
+  return tmul::read_status(static_cast<cudaStream_t>(stream), ws->status, rep);
 }
 
 int tm_release(void) {

@@ -1,0 +1,335 @@
+// Batched products: plan groups, one workspace per group, one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/truncmul.h"
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace tmul {
+namespace {
+
+constexpr int kBranches = 4;   // concurrent graph branches
+
+#define TB_CHECK(x)                                    \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) {                           \
+      (void)cudaGetLastError();                        \
+      return e_ == cudaErrorMemoryAllocation ? TM_ENOMEM : TM_ECUDA; \
+    }                                                  \
+  } while (0)
+
+struct Group {
+  PlanParams p;                        // kind, b, N, lambdas of the group
+  std::shared_ptr<PlanEntry> pe;
+  std::vector<uint32_t> members;       // indices into the descriptor array
+  size_t carry_bytes = 0;              // per-product carry scratch
+  size_t off = 0;                      // offset of the group's memory
+  size_t bytes = 0;
+  long long nblocks_max = 0;
+  unsigned long long emax_fx_min = ~0ull;
+};
+
+size_t carry_scratch(const PlanParams& p) {
+  int64_t nS, sh, rb;
+  carry_shape(p, &nS, &sh, &rb);
+  return align_up(size_t(2) * nS * 8) + 2 * align_up(size_t(nS / 512 + 2));
+}
+
+}  // namespace
+}  // namespace tmul
+
+struct tm_batch {
+  int dev = 0;
+  std::vector<tm_desc> descs;
+  std::vector<tmul::PlanParams> params;
+  std::vector<tmul::Group> groups;
+  char* mem = nullptr;
+  tmul::DevStatus* status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double e_max_min = 1.0;
+};
+
+namespace tmul {
+namespace {
+
+// Enqueues every phase of one group as batched launches.
+int enqueue_group(tm_batch* B, const Group& g, cudaStream_t s) {
+  const PlanParams& p = g.p;
+  const PlanEntry& pe = *g.pe;
+  const int kind = p.kind;
+  const int64_t N = p.N, M = pe.M;
+  const int cnt = int(g.members.size());
+  char* base = B->mem + g.off;
+  const size_t slab = size_t(cnt) * 2 * M * sizeof(double2);
+  double2* R0 = reinterpret_cast<double2*>(base);
+  double2* R1 = reinterpret_cast<double2*>(base + align_up(slab));
+  char* items = base + 2 * align_up(slab);
+  FwdItem* fi = reinterpret_cast<FwdItem*>(items);
+  BackItem* bi = reinterpret_cast<BackItem*>(items + align_up(cnt * sizeof(FwdItem)));
+  CarryItem* ci = reinterpret_cast<CarryItem*>(reinterpret_cast<char*>(bi) +
+                                               align_up(cnt * sizeof(BackItem)));
+  FwdArgs fa{};
+  fa.items = fi;
+  fa.b = p.b;
+  fa.N = N;
+  fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
+  fa.tab = pe.fwd_tab;
+  fa.kappa = pe.small;
+  fa.nkappa = pe.nkappa;
+  fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
+  fa.ntheta = pe.ntheta;
+  launch_fwd(kind, fa, cnt, s);
+  double2* bufs[2] = {R0, R1};
+  int cur = launch_fft(pe, bufs, 0, -1, 2 * cnt, M, s);
+  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), cnt,
+               2 * M, 2 * M, s);
+  cur ^= 1;
+  cur = launch_fft(pe, bufs, cur, 1, cnt, 2 * M, s);
+  if (cur != 1) return TM_EINVAL;       // the item layout assumes the output in R1
+  BackArgs ba{};
+  ba.items = bi;
+  ba.N = N;
+  ba.b = p.b;
+  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
+  ba.tab = pe.bwd_tab;
+  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  ba.kappa = pe.small;
+  ba.nkappa = pe.nkappa;
+  ba.rho = p.rho;
+  ba.count = kind == TM_HI ? N + 1 : N;
+  ba.status = B->status;
+  launch_back(kind, ba, cnt, s);
+  CarryArgs ca{};
+  ca.items = ci;
+  ca.nblocks_max = g.nblocks_max;
+  ca.K = kind == TM_HI ? N + 1 : N;
+  ca.b = p.b;
+  ca.kind = kind;
+  launch_carry(ca, cnt, s);
+  TB_CHECK(cudaGetLastError());
+  return TM_OK;
+}
+
+// Host images of the per-product items of one group.
+void build_items(tm_batch* B, const Group& g, std::vector<char>* host) {
+  const PlanParams& p = g.p;
+  const int64_t N = p.N, M = g.pe->M;
+  const int cnt = int(g.members.size());
+  char* base = B->mem + g.off;
+  const size_t slab = size_t(cnt) * 2 * M * sizeof(double2);
+  char* R0 = base;
+  char* R1 = base + align_up(slab);
+  const size_t items_off = 2 * align_up(slab);
+  const size_t fbytes = align_up(cnt * sizeof(FwdItem));
+  const size_t bbytes = align_up(cnt * sizeof(BackItem));
+  const size_t cbytes = align_up(cnt * sizeof(CarryItem));
+  double* theta = reinterpret_cast<double*>(base + items_off + fbytes + bbytes + cbytes);
+  char* carry = reinterpret_cast<char*>(theta) + align_up(size_t(cnt) * 2 * 8);
+  host->assign(fbytes + bbytes + cbytes, 0);
+  FwdItem* fi = reinterpret_cast<FwdItem*>(host->data());
+  BackItem* bi = reinterpret_cast<BackItem*>(host->data() + fbytes);
+  CarryItem* ci = reinterpret_cast<CarryItem*>(host->data() + fbytes + bbytes);
+  for (int i = 0; i < cnt; ++i) {
+    const tm_desc& d = B->descs[g.members[i]];
+    const PlanParams& q = B->params[g.members[i]];
+    const uint64_t n = d.n_bits;
+    double* X = reinterpret_cast<double*>(R0 + size_t(i) * 2 * M * sizeof(double2));
+    fi[i].u = reinterpret_cast<const unsigned long long*>(d.u);
+    fi[i].v = reinterpret_cast<const unsigned long long*>(d.v);
+    fi[i].n = n;
+    fi[i].nlimbs = limbs_of(n);
+    fi[i].nd = q.n_digits;
+    fi[i].s0 = int64_t(N + 1) * p.b - int64_t(n);
+    fi[i].X = X;
+    fi[i].theta = theta + 2 * i;
+    bi[i].w = reinterpret_cast<const double*>(R1 + size_t(i) * 2 * M * sizeof(double2));
+    bi[i].c = reinterpret_cast<long long*>(X);
+    bi[i].theta = theta + 2 * i;
+    bi[i].emax_fx = (unsigned long long)std::ldexp(q.e_max, 63);
+    int64_t nS, shift, rbit;
+    carry_shape(q, &nS, &shift, &rbit);
+    char* scratch = carry + size_t(i) * g.carry_bytes;
+    ci[i].c = reinterpret_cast<const long long*>(X);
+    ci[i].nS = nS;
+    ci[i].round_bit = rbit;
+    ci[i].shift_bits = shift;
+    ci[i].nout = out_limbs(p.kind, n);
+    ci[i].top_mask = (p.kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+    ci[i].out = reinterpret_cast<unsigned long long*>(d.out);
+    ci[i].r = reinterpret_cast<unsigned long long*>(scratch);
+    ci[i].fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
+    ci[i].cin_block = ci[i].fblock + align_up(size_t(nS / 512 + 2));
+  }
+}
+
+size_t group_bytes(const Group& g) {
+  const int cnt = int(g.members.size());
+  const size_t slab = size_t(cnt) * 2 * g.pe->M * sizeof(double2);
+  return 2 * align_up(slab) + align_up(cnt * sizeof(FwdItem)) + align_up(cnt * sizeof(BackItem)) +
+         align_up(cnt * sizeof(CarryItem)) + align_up(size_t(cnt) * 2 * 8) +
+         size_t(cnt) * g.carry_bytes + 256;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
+void destroy(tm_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  cudaFree(B->mem);
+  delete B;
+}
+
+int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s) {
+  if (!out || (!descs && count)) return TM_EINVAL;
+  std::unique_ptr<tm_batch, void (*)(tm_batch*)> B(new tm_batch(), destroy);
+  TB_CHECK(cudaGetDevice(&B->dev));
+  B->descs.assign(descs, descs + count);
+  B->params.resize(count);
+  std::map<std::tuple<int, int, int64_t>, size_t> index;
+  for (uint32_t i = 0; i < count; ++i) {
+    const tm_desc& d = B->descs[i];
+    if (d.kind != TM_FULL && d.kind != TM_LO && d.kind != TM_HI) return TM_EINVAL;
+    if (d.n_bits == 0 || !d.u || !d.v || !d.out) return TM_EINVAL;
+    if (d.n_bits > TM_MAX_BITS) return TM_ERANGE;
+    const size_t ib = size_t(limbs_of(d.n_bits)) * 8, ob = size_t(out_limbs(d.kind, d.n_bits)) * 8;
+    if (overlap(d.out, ob, d.u, ib) || overlap(d.out, ob, d.v, ib)) return TM_EALIAS;
+    int rc = get_params(d.kind, d.n_bits, &B->params[i]);
+    if (rc) return rc;
+    const PlanParams& q = B->params[i];
+    B->e_max_min = std::min(B->e_max_min, q.e_max);
+    auto key = std::make_tuple(q.kind, q.b, q.N);
+    auto it = index.find(key);
+    if (it == index.end()) {
+      Group g;
+      g.p = q;
+      rc = get_tables(q, false, s, &g.pe);
+      if (rc) return rc;
+      index[key] = B->groups.size();
+      B->groups.push_back(std::move(g));
+      it = index.find(key);
+    }
+    Group& g = B->groups[it->second];
+    g.members.push_back(i);
+    g.carry_bytes = std::max(g.carry_bytes, carry_scratch(q));
+    int64_t nS, sh, rb;
+    carry_shape(q, &nS, &sh, &rb);
+    g.nblocks_max = std::max<long long>(g.nblocks_max, (nS + 511) / 512);
+  }
+  // device memory: status word, then one region per group
+  size_t total = 256;
+  for (Group& g : B->groups) {
+    g.off = total;
+    g.bytes = group_bytes(g);
+    total += align_up(g.bytes);
+  }
+  TB_CHECK(cudaMalloc(&B->mem, total));
+  B->status = reinterpret_cast<DevStatus*>(B->mem);
+  TB_CHECK(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), s));
+  std::vector<char> host;
+  for (Group& g : B->groups) {
+    build_items(B.get(), g, &host);
+    const int cnt = int(g.members.size());
+    const size_t items_off = 2 * align_up(size_t(cnt) * 2 * g.pe->M * sizeof(double2));
+    TB_CHECK(cudaMemcpyAsync(B->mem + g.off + items_off, host.data(), host.size(),
+                             cudaMemcpyHostToDevice, s));
+    TB_CHECK(cudaStreamSynchronize(s));
+  }
+  ensure_kernel_attributes();
+  // record the graph: groups spread over kBranches forked capture streams
+  cudaStream_t cs[kBranches];
+  cudaEvent_t fork, join[kBranches];
+  for (int i = 0; i < kBranches; ++i) {
+    TB_CHECK(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking));
+    TB_CHECK(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+  }
+  TB_CHECK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  int rc = TM_OK;
+  cudaError_t ce = cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    cudaEventRecord(fork, cs[0]);
+    for (int i = 1; i < kBranches; ++i) cudaStreamWaitEvent(cs[i], fork, 0);
+    // largest groups first, round robin over the branches
+    std::vector<size_t> order(B->groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+      return B->groups[x].members.size() * B->groups[x].p.N >
+             B->groups[y].members.size() * B->groups[y].p.N;
+    });
+    for (size_t i = 0; i < order.size() && rc == TM_OK; ++i)
+      rc = enqueue_group(B.get(), B->groups[order[i]], cs[i % kBranches]);
+    for (int i = 1; i < kBranches; ++i) {
+      cudaEventRecord(join[i], cs[i]);
+      cudaStreamWaitEvent(cs[0], join[i], 0);
+    }
+    ce = cudaStreamEndCapture(cs[0], &B->graph);
+    if (ce == cudaSuccess && rc == TM_OK) ce = cudaGraphInstantiate(&B->exec, B->graph, 0);
+  }
+  for (int i = 0; i < kBranches; ++i) {
+    cudaStreamDestroy(cs[i]);
+    cudaEventDestroy(join[i]);
+  }
+  cudaEventDestroy(fork);
+  if (rc) return rc;
+  TB_CHECK(ce);
+  *out = B.release();
+  return TM_OK;
+}
+
+}  // namespace
+}  // namespace tmul
+
+extern "C" {
+
+int tm_batch_create(tm_batch** batch, const tm_desc* descs, uint32_t count, void* stream) {
+  return tmul::create(batch, descs, count, static_cast<cudaStream_t>(stream));
+}
+
+int tm_batch_launch(tm_batch* batch, void* stream) {
+  if (!batch) return TM_EINVAL;
+  if (!batch->exec) return TM_OK;
+  const cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TM_ECUDA;
+  }
+  return TM_OK;
+}
+
+int tm_batch_status(tm_batch* batch, void* stream, tm_report* rep) {
+  if (!batch) return TM_EINVAL;
+  const int rc = tmul::read_status(static_cast<cudaStream_t>(stream), batch->status, rep);
+  if (rep) rep->e_max = batch->e_max_min;
+  return rc;
+}
+
+int tm_batch_destroy(tm_batch* batch) {
+  tmul::destroy(batch);
+  return TM_OK;
+}
+
+int tm_mul_batch(const tm_desc* descs, uint32_t count, void* stream, tm_report* rep) {
+  tm_batch* b = nullptr;
+  int rc = tm_batch_create(&b, descs, count, stream);
+  if (rc) return rc;
+  rc = tm_batch_launch(b, stream);
+  if (rc == TM_OK) rc = tm_batch_status(b, stream, rep);
+  tm_batch_destroy(b);
+  return rc;
+}
+
+}  // extern "C"

@@ -230,7 +230,13 @@ constexpr int kMaxLam = 24;
 // S_j = U_j 2^Q + sum_r (A_{k,r} U_k) >> rb is exact up to the table rounding and
 // the shifts, |S_j| < 2^61, and U~_j = S_j 2^-Q after one rounding conversion.
 // Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1, split step).
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a, int kind) {
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kind) {
+  FwdArgs a = a0;
+  if (a0.items) {
+    const FwdItem it = a0.items[blockIdx.y];
+    a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
+    a.X = it.X; a.theta = it.theta;
+  }
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
@@ -281,7 +287,13 @@ __device__ __forceinline__ double fx_coef(const long long* tab, long long N, int
   return scale2(__ll2double_rn(__ldg(tab + (long long)(r - 1) * N + k)), -(Q + r * b));
 }
 
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
+  FwdArgs a = a0;
+  if (a0.items) {
+    const FwdItem it = a0.items[blockIdx.y];
+    a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
+    a.X = it.X; a.theta = it.theta;
+  }
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
   __shared__ double topu, topv;
@@ -357,12 +369,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a) {
   }
 }
 
-void launch_fwd(int kind, const FwdArgs& a, cudaStream_t s) {
-  const unsigned blocks = unsigned((a.N + kFwdTile - 1) / kFwdTile);
+void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s) {
+  const dim3 grid(unsigned((a.N + kFwdTile - 1) / kFwdTile), unsigned(batch));
   if (kind == TM_HI)
-    k_fwd_hi<<<blocks, kFwdThreads, 0, s>>>(a);
+    k_fwd_hi<<<grid, kFwdThreads, 0, s>>>(a);
   else
-    k_fwd_lo_full<<<blocks, kFwdThreads, 0, s>>>(a, kind);
+    k_fwd_lo_full<<<grid, kFwdThreads, 0, s>>>(a, kind);
 }
 
 // ------------------------------------------------------------ FFT pass
@@ -650,17 +662,18 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   }
 }
 
+// Shared memory above 48 KB per CTA needs the opt-in; set once before any launch
+// (outside stream capture).
+void set_fft_smem_attribute() {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
                      int threads, cudaStream_t s) {
-  static bool attr_set = false;   // shared memory above 48 KB needs the opt-in
-  if (!attr_set) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    attr_set = true;
-  }
   const unsigned blocks = unsigned((p.Q + p.C - 1) / p.C);
   const size_t smem = (size_t((p.C * p.L + 1) & ~1) + 2 * size_t(p.tw4_len) +
                       (p.need_wL ? size_t(p.L) : 0)) * sizeof(double2);
@@ -681,9 +694,12 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
 // FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
 // S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
 __global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, long long M,
-                        const double2* __restrict__ twN, double scale) {
+                        const double2* __restrict__ twN, double scale, long long zstride,
+                        long long qstride) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k > M / 2) return;
+  Z += blockIdx.y * zstride;
+  Q += blockIdx.y * qstride;
   const long long km = k == 0 ? 0 : M - k;
   const double2 w = __ldg(twN + k);
   double2 Xk[2], Xm[2];
@@ -707,9 +723,10 @@ __global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, 
 }
 
 void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
-                  cudaStream_t s) {
+                  int batch, long long zstride, long long qstride, cudaStream_t s) {
   const long long n = M / 2 + 1;
-  k_twist<<<unsigned((n + 255) / 256), 256, 0, s>>>(Z, Q, M, twN, scale);
+  const dim3 grid(unsigned((n + 255) / 256), unsigned(batch));
+  k_twist<<<grid, 256, 0, s>>>(Z, Q, M, twN, scale, zstride, qstride);
 }
 
 // ------------------------------------------------ back maps and rounding
@@ -741,7 +758,12 @@ __device__ __forceinline__ void emit(const BackArgs& a, long long i, double x, b
 }
 
 // Full product (Algorithm 1, overlap-add): c_i = round(W_i).
-__global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a) {
+__global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
@@ -772,7 +794,12 @@ __device__ double lo_overflow(const BackArgs& a, int m) {   // P_(N+m)
   return acc;
 }
 
-__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a) {
+__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
@@ -819,7 +846,12 @@ __device__ double hi_H(const BackArgs& a, long long i, const double* P) {   // r
   return acc;
 }
 
-__global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a) {
+__global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   __shared__ double P[kMaxLam];
@@ -880,8 +912,14 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a) {
 // down, and for the high product psi by eq. (4.6) in the scaled form
 // psi = (theta - rho^-2N H(rho)) / (1 - N 2^b rho^-(N+1)).
 constexpr int kSmallMax = 160;
-__global__ void k_back_small(BackArgs a, int kind) {
+__global__ void k_back_small(BackArgs a0, int kind) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
+
   double P[kSmallMax + kMaxLam];
   const long long N = a.N;
   const int tot = int(N) + a.lam - 1;
@@ -941,19 +979,20 @@ __global__ void k_back_small(BackArgs a, int kind) {
   if (flags) atomicOr(&a.status->flags, flags);
 }
 
-void launch_back(int kind, const BackArgs& a, cudaStream_t s) {
+void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
   const long long n = a.count;
   unsigned blocks = unsigned((n + kBackThreads - 1) / kBackThreads);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks == 0) blocks = 1;
+  const dim3 grid(blocks, unsigned(batch));
   if (kind == TM_FULL) {
-    k_back_full<<<blocks, kBackThreads, 0, s>>>(a);
+    k_back_full<<<grid, kBackThreads, 0, s>>>(a);
   } else if (a.N <= 64 || a.N < 2 * a.lam + a.nkappa + 2) {
-    k_back_small<<<1, 32, 0, s>>>(a, kind);
+    k_back_small<<<dim3(1, unsigned(batch)), 32, 0, s>>>(a, kind);
   } else if (kind == TM_LO) {
-    k_back_lo<<<blocks, kBackThreads, 0, s>>>(a);
+    k_back_lo<<<grid, kBackThreads, 0, s>>>(a);
   } else {
-    k_back_hi<<<blocks, kBackThreads, 0, s>>>(a);
+    k_back_hi<<<grid, kBackThreads, 0, s>>>(a);
   }
 }
 
@@ -1025,7 +1064,16 @@ __device__ void block_compose_scan(unsigned* s, int n) {
   }
 }
 
-__global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a) {
+__global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
+  CarryArgs a = a0;
+  if (a0.items) {
+    const CarryItem it = a0.items[blockIdx.y];
+    a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
+    a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
+    a.fblock = it.fblock; a.cin_block = it.cin_block;
+  }
+  const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
+  if (blockIdx.x >= my_blocks) return;     // uniform per block
   __shared__ unsigned fs[kCarryThreads];
   const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
   unsigned f = kIdentityFn;
@@ -1043,7 +1091,16 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a) {
 }
 
 // carry into every block: cin_0 = 0, cin_(B+1) = F_B(cin_B)
-__global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a, long long nblocks) {
+__global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
+  CarryArgs a = a0;
+  if (a0.items) {
+    const CarryItem it = a0.items[blockIdx.y];
+    a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
+    a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
+    a.fblock = it.fblock; a.cin_block = it.cin_block;
+  }
+  const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
+  const long long nblocks = my_blocks;
   __shared__ unsigned fs[1024];
   const long long per = (nblocks + 1023) / 1024;
   const long long b0 = threadIdx.x * per;
@@ -1066,7 +1123,16 @@ __device__ __forceinline__ unsigned long long resolved(const CarryArgs& a, long 
   return (unsigned long long)(r + cin);
 }
 
-__global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a) {
+__global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
+  CarryArgs a = a0;
+  if (a0.items) {
+    const CarryItem it = a0.items[blockIdx.y];
+    a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
+    a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
+    a.fblock = it.fblock; a.cin_block = it.cin_block;
+  }
+  const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
+  if (blockIdx.x >= my_blocks) return;     // uniform per block
   __shared__ unsigned fs[kCarryThreads];
   const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
   unsigned f = kIdentityFn;
@@ -1096,11 +1162,13 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a) {
   a.out[j] = o;
 }
 
-void launch_carry(const CarryArgs& a, cudaStream_t s) {
-  const long long nblocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
-  k_carry_local<<<unsigned(nblocks), kCarryThreads, 0, s>>>(a);
-  k_carry_blocks<<<1, 1024, 0, s>>>(a, nblocks);
-  k_carry_apply<<<unsigned(nblocks), kCarryThreads, 0, s>>>(a);
+void launch_carry(const CarryArgs& a, int batch, cudaStream_t s) {
+  const long long nblocks =
+      a.items ? a.nblocks_max : (a.nS + kCarryThreads - 1) / kCarryThreads;
+  const dim3 grid(static_cast<unsigned>(nblocks), static_cast<unsigned>(batch));
+  k_carry_local<<<grid, kCarryThreads, 0, s>>>(a);
+  k_carry_blocks<<<dim3(1, unsigned(batch)), 1024, 0, s>>>(a);
+  k_carry_apply<<<grid, kCarryThreads, 0, s>>>(a);
 }
 
 // ------------------------------------------------------------ tables

@@ -35,8 +35,21 @@ struct PassArgs {
   int need_wL;
 };
 
+// Per-product fields of the forward map, back map and carry kernels. A batch of
+// products with the same plan passes an array of items indexed by blockIdx.y;
+// a single product passes items = nullptr and the fields of the args block.
+struct FwdItem {
+  const unsigned long long* u;
+  const unsigned long long* v;
+  unsigned long long n;
+  long long nlimbs, nd, s0;
+  double* X;
+  double* theta;
+};
+
 // Digit unpack + forward map parameters.
 struct FwdArgs {
+  const FwdItem* items;
   const unsigned long long* u;
   const unsigned long long* v;
   unsigned long long n;          // operand bits
@@ -56,7 +69,15 @@ struct FwdArgs {
   double* theta;                 // high: theta_U, theta_V
 };
 
+struct BackItem {
+  const double* w;
+  long long* c;
+  const double* theta;
+  unsigned long long emax_fx;
+};
+
 struct BackArgs {
+  const BackItem* items;
   const double* w;               // N real values (inverse FFT output)
   long long N;
   int b;
@@ -73,7 +94,19 @@ struct BackArgs {
   DevStatus* status;
 };
 
+struct CarryItem {
+  const long long* c;
+  long long nS, round_bit, shift_bits, nout;
+  unsigned long long top_mask;
+  unsigned long long* out;
+  unsigned long long* r;
+  unsigned char* fblock;
+  unsigned char* cin_block;
+};
+
 struct CarryArgs {
+  const CarryItem* items;
+  long long nblocks_max;         // grid width of the batched carry kernels
   const long long* c;
   long long K;                   // number of coefficients
   int b;
@@ -107,13 +140,15 @@ void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int ro
                            cudaStream_t s);
 
 // pipeline stages
-void launch_fwd(int kind, const FwdArgs& a, cudaStream_t s);
+void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s);
+void set_fft_smem_attribute();
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
                      int threads, cudaStream_t s);
+// Z + y zstride -> Q + y qstride for product y < batch
 void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
-                  cudaStream_t s);
-void launch_back(int kind, const BackArgs& a, cudaStream_t s);
-void launch_carry(const CarryArgs& a, cudaStream_t s);
+                  int batch, long long zstride, long long qstride, cudaStream_t s);
+void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s);
+void launch_carry(const CarryArgs& a, int batch, cudaStream_t s);
 
 // map table selectors for launch_init_maptab
 constexpr int kTabAlpha = 0, kTabBeta = 1, kTabGamma = 2, kTabDelta = 3, kTabDeltaPrime = 4;

@@ -280,7 +280,7 @@ void shape(FftPass* p, int64_t ctas_wanted) {
 
 }  // namespace
 
-int make_fft_plan(int64_t M, FftPlan* out) {
+int make_fft_plan(int64_t M, FftPlan* out, bool single) {
   FftPlan f;
   f.M = M;
   std::vector<int> primes;
@@ -288,7 +288,7 @@ int make_fft_plan(int64_t M, FftPlan* out) {
   for (int p : {7, 5, 3, 2})
     while (rest % p == 0) { primes.push_back(p); rest /= p; }
   if (rest != 1) return TM_EINVAL;
-  int np = M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3);
+  int np = single ? 1 : (M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3));
   int64_t Ls[kMaxPasses] = {1, 1, 1};
   for (int p : primes) {       // largest primes first, each to the smallest factor
     int best = 0;

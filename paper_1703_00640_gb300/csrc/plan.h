@@ -58,7 +58,8 @@ int choose_params(int kind, uint64_t n, PlanParams* out);
 
 // Splits the complex length M into at most kMaxPasses sub-FFT passes and picks
 // their radices and launch shapes. Twiddle offsets are left for the caller.
-int make_fft_plan(int64_t M, FftPlan* out);
+// single = true: one sub-FFT of length M (M <= kMaxSubLen), for CTA-resident products.
+int make_fft_plan(int64_t M, FftPlan* out, bool single = false);
 
 // The same two plans computed without any heap allocation (for the entry point
 // whose callers cannot allocate): identical choice of (b, N, lambda); the FFT

@@ -1,0 +1,56 @@
+// Internal runtime of the library shared by api.cu and batch.cu: resident plan
+// tables, workspaces, the per-product launch sequence.
+#pragma once
+#include <cstdint>
+#include <memory>
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace tmul {
+
+// Resident device tables of one (device, kind, n).
+struct PlanEntry {
+  PlanParams p;
+  FftPlan fft;
+  int64_t M = 0;
+  double2* tw = nullptr;       // all twiddle tables
+  size_t twN_off = 0;          // omega_N^k, k <= M/2 (real-FFT twist)
+  long long* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1, fixed point
+  double* bwd_tab = nullptr;   // beta rows (low) or delta' rows (high)
+  double* bwd_tab2 = nullptr;  // high: delta rows r = 1..lam_bwd-1
+  double* small = nullptr;     // high: kappa[nkappa] then rho^-j[ntheta]
+  int nkappa = 0, ntheta = 0;
+  size_t table_bytes = 0;
+};
+
+struct Workspace {
+  char* base = nullptr;
+  size_t size = 0;
+  DevStatus* status = nullptr;
+  char* io = nullptr;          // staging for tm_mul_host
+  size_t io_size = 0;
+};
+
+size_t align_up(size_t x);
+int64_t limbs_of(uint64_t n);
+int64_t out_limbs(int kind, uint64_t n);
+void carry_shape(const PlanParams& p, int64_t* nS, int64_t* shift, int64_t* round_bit);
+size_t workspace_bytes(const PlanParams& p);
+// (kind, n) -> parameters, cached (host only)
+int get_params(int kind, uint64_t n, PlanParams* out);
+// resident tables for the plan's (kind, b, N) on the current device; single_pass
+// lays the FFT out as one sub-FFT of length N/2 (for CTA-resident products)
+int get_tables(const PlanParams& p, bool single_pass, cudaStream_t s,
+               std::shared_ptr<PlanEntry>* out);
+// FFT passes of a batch of `batch` sequences of length M (stride `stride`),
+// ping-ponging bufs[cur] <-> bufs[cur ^ 1]; returns the buffer index holding the result
+int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
+               long long stride, cudaStream_t s);
+void ensure_kernel_attributes();
+int read_status(cudaStream_t s, DevStatus* status, tm_report* rep);
+void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep);
+
+}  // namespace tmul
