@@ -52,6 +52,11 @@ struct tm_batch {
   std::vector<tm_desc> descs;
   std::vector<tmul::PlanParams> params;
   std::vector<tmul::Group> groups;
+  // CTA-resident products
+  std::vector<uint32_t> small;
+  std::vector<tmul::SmallPlan> small_plans;
+  std::vector<std::shared_ptr<tmul::PlanEntry>> small_tables;
+  size_t small_off = 0, small_smem = 0;
   char* mem = nullptr;
   tmul::DevStatus* status = nullptr;
   cudaGraph_t graph = nullptr;
@@ -194,6 +199,56 @@ void destroy(tm_batch* B) {
   delete B;
 }
 
+SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
+  SmallPlan sp{};
+  const FftPass& fp = pe.fft.pass[0];
+  sp.kind = p.kind;
+  sp.b = p.b;
+  sp.lam_fwd = p.lam_fwd;
+  sp.lam_bwd = p.lam_bwd;
+  sp.nkappa = pe.nkappa;
+  sp.ntheta = pe.ntheta;
+  sp.N = p.N;
+  sp.M = pe.M;
+  sp.rho = p.rho;
+  sp.nstages = fp.nstages;
+  std::copy(fp.radix, fp.radix + kMaxStages, sp.radix);
+  std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, sp.tw4_off);
+  sp.tw4_len = fp.tw4_len;
+  sp.need_wL = fp.need_wL ? 1 : 0;
+  sp.tw_sub = pe.tw + fp.tw_sub;
+  sp.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
+  sp.twN = pe.tw + pe.twN_off;
+  sp.fwd_tab = pe.fwd_tab;
+  sp.bwd_tab = pe.bwd_tab;
+  sp.bwd_tab2 = p.kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  sp.kappa = pe.small;
+  sp.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
+  return sp;
+}
+
+SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
+  SmallItem it{};
+  const uint64_t n = d.n_bits;
+  it.u = reinterpret_cast<const unsigned long long*>(d.u);
+  it.v = reinterpret_cast<const unsigned long long*>(d.v);
+  it.out = reinterpret_cast<unsigned long long*>(d.out);
+  it.n = n;
+  it.nlimbs = limbs_of(n);
+  it.nd = q.n_digits;
+  it.s0 = int64_t(q.N + 1) * q.b - int64_t(n);
+  int64_t nS, shift, rbit;
+  carry_shape(q, &nS, &shift, &rbit);
+  it.nS = nS;
+  it.round_bit = rbit;
+  it.shift_bits = shift;
+  it.nout = out_limbs(q.kind, n);
+  it.top_mask = (q.kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+  it.emax_fx = (unsigned long long)std::ldexp(q.e_max, 63);
+  it.plan = plan;
+  return it;
+}
+
 int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s) {
   if (!out || (!descs && count)) return TM_EINVAL;
   std::unique_ptr<tm_batch, void (*)(tm_batch*)> B(new tm_batch(), destroy);
@@ -212,6 +267,10 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
     if (rc) return rc;
     const PlanParams& q = B->params[i];
     B->e_max_min = std::min(B->e_max_min, q.e_max);
+    if (q.N / 2 <= kSmallMaxM) {          // CTA-resident
+      B->small.push_back(i);
+      continue;
+    }
     auto key = std::make_tuple(q.kind, q.b, q.N);
     auto it = index.find(key);
     if (it == index.end()) {
@@ -230,8 +289,32 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
     carry_shape(q, &nS, &sh, &rb);
     g.nblocks_max = std::max<long long>(g.nblocks_max, (nS + 511) / 512);
   }
-  // device memory: status word, then one region per group
+  // plans of the CTA-resident products (single-pass tables)
+  std::map<std::tuple<int, int, int64_t>, int> small_index;
+  std::vector<SmallItem> small_items;
+  for (uint32_t i : B->small) {
+    const PlanParams& q = B->params[i];
+    auto key = std::make_tuple(q.kind, q.b, q.N);
+    auto it = small_index.find(key);
+    if (it == small_index.end()) {
+      std::shared_ptr<PlanEntry> pe;
+      const int rc = get_tables(q, true, s, &pe);
+      if (rc) return rc;
+      small_index[key] = int(B->small_plans.size());
+      B->small_plans.push_back(small_plan_of(q, *pe));
+      B->small_tables.push_back(pe);
+      const FftPass& fp = pe->fft.pass[0];
+      B->small_smem = std::max(B->small_smem,
+                               small_smem_bytes(q.N, pe->M, fp.tw4_len, fp.need_wL));
+      it = small_index.find(key);
+    }
+    small_items.push_back(small_item_of(B->descs[i], q, it->second));
+  }
+  // device memory: status word, CTA-resident items and plans, one region per group
   size_t total = 256;
+  B->small_off = total;
+  total += align_up(small_items.size() * sizeof(SmallItem)) +
+           align_up(B->small_plans.size() * sizeof(SmallPlan)) + 256;
   for (Group& g : B->groups) {
     g.off = total;
     g.bytes = group_bytes(g);
@@ -240,6 +323,22 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
   TB_CHECK(cudaMalloc(&B->mem, total));
   B->status = reinterpret_cast<DevStatus*>(B->mem);
   TB_CHECK(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), s));
+  SmallArgs sa{};
+  if (!small_items.empty()) {
+    char* sbase = B->mem + B->small_off;
+    const size_t ib = align_up(small_items.size() * sizeof(SmallItem));
+    const size_t pb = align_up(B->small_plans.size() * sizeof(SmallPlan));
+    TB_CHECK(cudaMemcpyAsync(sbase, small_items.data(), small_items.size() * sizeof(SmallItem),
+                             cudaMemcpyHostToDevice, s));
+    TB_CHECK(cudaMemcpyAsync(sbase + ib, B->small_plans.data(),
+                             B->small_plans.size() * sizeof(SmallPlan), cudaMemcpyHostToDevice, s));
+    TB_CHECK(cudaStreamSynchronize(s));
+    sa.items = reinterpret_cast<const SmallItem*>(sbase);
+    sa.count = int(small_items.size());
+    sa.plans = reinterpret_cast<const SmallPlan*>(sbase + ib);
+    sa.counter = reinterpret_cast<int*>(sbase + ib + pb);
+    sa.status = B->status;
+  }
   std::vector<char> host;
   for (Group& g : B->groups) {
     build_items(B.get(), g, &host);
@@ -263,6 +362,10 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
   if (ce == cudaSuccess) {
     cudaEventRecord(fork, cs[0]);
     for (int i = 1; i < kBranches; ++i) cudaStreamWaitEvent(cs[i], fork, 0);
+    if (sa.count > 0) {                     // CTA-resident products on branch 0
+      cudaMemsetAsync(sa.counter, 0, sizeof(int), cs[0]);
+      launch_small(sa, std::min(sa.count, 152), B->small_smem, cs[0]);
+    }
     // largest groups first, round robin over the branches
     std::vector<size_t> order(B->groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
@@ -271,7 +374,8 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
              B->groups[y].members.size() * B->groups[y].p.N;
     });
     for (size_t i = 0; i < order.size() && rc == TM_OK; ++i)
-      rc = enqueue_group(B.get(), B->groups[order[i]], cs[i % kBranches]);
+      rc = enqueue_group(B.get(), B->groups[order[i]],
+                         cs[sa.count > 0 ? 1 + i % (kBranches - 1) : i % kBranches]);
     for (int i = 1; i < kBranches; ++i) {
       cudaEventRecord(join[i], cs[i]);
       cudaStreamWaitEvent(cs[0], join[i], 0);

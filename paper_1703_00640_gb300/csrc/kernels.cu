@@ -662,6 +662,8 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   }
 }
 
+void set_small_smem_attribute(int bytes);
+
 // Shared memory above 48 KB per CTA needs the opt-in; set once before any launch
 // (outside stream capture).
 void set_fft_smem_attribute() {
@@ -670,6 +672,7 @@ void set_fft_smem_attribute() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  set_small_smem_attribute(optin);
 }
 
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
@@ -693,13 +696,8 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
 // product of the Convolution step); then the pre-twist of the inverse real
 // FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
 // S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
-__global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, long long M,
-                        const double2* __restrict__ twN, double scale, long long zstride,
-                        long long qstride) {
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k > M / 2) return;
-  Z += blockIdx.y * zstride;
-  Q += blockIdx.y * qstride;
+__device__ __forceinline__ void twist_pair(const double2* Z, double2* Q, long long M, long long k,
+                                           const double2* __restrict__ twN, double scale) {
   const long long km = k == 0 ? 0 : M - k;
   const double2 w = __ldg(twN + k);
   double2 Xk[2], Xm[2];
@@ -718,8 +716,17 @@ __global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, 
   const double2 Dm = csub(Pk, cconj(Pm));
   const double2 iwD = mul_si<1>(cmulc(Dm, w));          // i conj(w) D
   const double2 qk = cadd(Sm, iwD), qm = cconj(csub(Sm, iwD));
+  // (reads of Z precede the writes, so Q may alias Z's first half)
   Q[k] = make_double2(qk.x * scale, qk.y * scale);
   if (k != 0 && km != k) Q[km] = make_double2(qm.x * scale, qm.y * scale);
+}
+
+__global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, long long M,
+                        const double2* __restrict__ twN, double scale, long long zstride,
+                        long long qstride) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k > M / 2) return;
+  twist_pair(Z + blockIdx.y * zstride, Q + blockIdx.y * qstride, M, k, twN, scale);
 }
 
 void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
@@ -758,6 +765,11 @@ __device__ __forceinline__ void emit(const BackArgs& a, long long i, double x, b
 }
 
 // Full product (Algorithm 1, overlap-add): c_i = round(W_i).
+__device__ void back_full_loop(const BackArgs& a, long long start, long long stride,
+                               unsigned long long* bmax) {
+  for (long long i = start; i < a.count; i += stride) emit(a, i, a.w[i], false, bmax);
+}
+
 __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
   BackArgs a = a0;
   if (a0.items) {
@@ -768,9 +780,8 @@ __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
   __shared__ unsigned bflags;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.count;
-       i += (long long)gridDim.x * blockDim.x)
-    emit(a, i, a.w[i], false, &bmax);
+  back_full_loop(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x, &bmax);
   finish_block(&bmax, &bflags, a);
 }
 
@@ -794,19 +805,10 @@ __device__ double lo_overflow(const BackArgs& a, int m) {   // P_(N+m)
   return acc;
 }
 
-__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
-  BackArgs a = a0;
-  if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
-    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
-  }
-  __shared__ unsigned long long bmax;
-  __shared__ unsigned bflags;
-  if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
-  __syncthreads();
+__device__ void back_lo_loop(const BackArgs& a, long long start, long long stride,
+                             unsigned long long* bmax, unsigned* bflags) {
   const long long N = a.N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = start; i < N; i += stride) {
     double acc = a.w[i];
     const int rmax = i < a.lam ? int(i) + 1 : a.lam;
     for (int r = 1; r < rmax; ++r) acc = fma(beta_at(a, i - r, r), a.w[i - r], acc);
@@ -817,9 +819,23 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
     unsigned long long d;
     const long long c = round_dist(scale2(acc, a.b), &d);
     a.c[i] = c;
-    note_distance(d, &bmax);
-    if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(&bflags, kFlagC0);
+    note_distance(d, bmax);
+    if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(bflags, kFlagC0);
   }
+}
+
+__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
+  __shared__ unsigned long long bmax;
+  __shared__ unsigned bflags;
+  if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
+  __syncthreads();
+  back_lo_loop(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+               (long long)gridDim.x * blockDim.x, &bmax, &bflags);
   finish_block(&bmax, &bflags, a);
 }
 
@@ -846,6 +862,60 @@ __device__ double hi_H(const BackArgs& a, long long i, const double* P) {   // r
   return acc;
 }
 
+// Interior J_i, i >= lam + nkappa, one stencil with the delta' rows.
+__device__ void back_hi_interior(const BackArgs& a, long long start, long long stride,
+                                 unsigned long long* bmax) {
+  const long long N = a.N;
+  const int head = a.lam + a.nkappa;
+  for (long long i = head + start; i < N; i += stride) {
+    double acc = a.w[i];
+    for (int r = 1; r <= a.lam; ++r)
+      acc = fma(__ldg(a.tab + (long long)(r - 1) * N + (i - r)), a.w[i - r], acc);
+    unsigned long long d;
+    a.c[i] = round_dist(scale2(acc, a.b), &d);
+    note_distance(d, bmax);
+  }
+}
+
+// Head J_i, i < lam + nkappa, and J_N: one warp (lane 0..31), shared P and Hh.
+__device__ void back_hi_head(const BackArgs& a, int lane, double* P, double* Hh,
+                             unsigned long long* bmax, unsigned* bflags) {
+  const long long N = a.N;
+  const int head = a.lam + a.nkappa;
+  const double twmb = scale2(1.0, -a.b);
+  const double psi = a.theta[0] * a.theta[1];
+  // overflow coefficients P_(N+m), m = 0..lam-2
+  for (int m = lane; m <= a.lam - 2; m += 32) {
+    double acc = 0.0;
+    for (int r = m + 1; r < a.lam; ++r) {
+      const long long k = N + m - r;
+      acc = fma(delta_at(a, k, r), a.w[k], acc);
+    }
+    P[m] = acc;
+  }
+  __syncwarp();
+  for (int i = lane; i < head; i += 32) Hh[i] = hi_H(a, i, P);
+  __syncwarp();
+  for (int i = lane; i < head; i += 32) {
+    double J = Hh[i];
+    if (i >= 1) J = fma(-twmb, Hh[i - 1], J);
+    if (i < a.nkappa) J = fma(-psi, __ldg(a.kappa + i), J);
+    unsigned long long d;
+    const long long c = round_dist(scale2(J, a.b), &d);
+    a.c[i] = c;
+    note_distance(d, bmax);
+    if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(bflags, kFlagC0);
+  }
+  if (lane == 0) {   // J_N = -2^-b H_(N-1) + psi (H_(N-1) is an interior value)
+    double H = 0.0;
+    for (int r = 0; r < a.lam; ++r) H = fma(delta_at(a, N - 1 - r, r), a.w[N - 1 - r], H);
+    const double J = fma(-twmb, H, psi);
+    unsigned long long d;
+    a.c[N] = round_dist(scale2(J, a.b), &d);
+    note_distance(d, bmax);
+  }
+}
+
 __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
   BackArgs a = a0;
   if (a0.items) {
@@ -858,52 +928,9 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
   __shared__ double Hh[kMaxLam + 64 + 1];
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
-  const long long N = a.N;
-  const int head = a.lam + a.nkappa;     // J_i for i < head computed by the head warp
-  const double twmb = scale2(1.0, -a.b);
-  for (long long i = head + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    double acc = a.w[i];
-    for (int r = 1; r <= a.lam; ++r)
-      acc = fma(__ldg(a.tab + (long long)(r - 1) * N + (i - r)), a.w[i - r], acc);
-    unsigned long long d;
-    a.c[i] = round_dist(scale2(acc, a.b), &d);
-    note_distance(d, &bmax);
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const double psi = a.theta[0] * a.theta[1];
-    // overflow coefficients P_(N+m), m = 0..lam-2
-    for (int m = lane; m <= a.lam - 2; m += 32) {
-      double acc = 0.0;
-      for (int r = m + 1; r < a.lam; ++r) {
-        const long long k = N + m - r;
-        acc = fma(delta_at(a, k, r), a.w[k], acc);
-      }
-      P[m] = acc;
-    }
-    __syncwarp();
-    for (int i = lane; i < head; i += 32) Hh[i] = hi_H(a, i, P);
-    __syncwarp();
-    for (int i = lane; i < head; i += 32) {
-      double J = Hh[i];
-      if (i >= 1) J = fma(-twmb, Hh[i - 1], J);
-      if (i < a.nkappa) J = fma(-psi, __ldg(a.kappa + i), J);
-      unsigned long long d;
-      const long long c = round_dist(scale2(J, a.b), &d);
-      a.c[i] = c;
-      note_distance(d, &bmax);
-      if (i == 0 && (c & ((1ll << a.b) - 1)) != 0) atomicOr(&bflags, kFlagC0);
-    }
-    if (lane == 0) {   // J_N = -2^-b H_(N-1) + psi (H_(N-1) is an interior value)
-      double H = 0.0;
-      for (int r = 0; r < a.lam; ++r) H = fma(delta_at(a, N - 1 - r, r), a.w[N - 1 - r], H);
-      const double J = fma(-twmb, H, psi);
-      unsigned long long d;
-      a.c[N] = round_dist(scale2(J, a.b), &d);
-      note_distance(d, &bmax);
-    }
-  }
+  back_hi_interior(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                   (long long)gridDim.x * blockDim.x, &bmax);
+  if (blockIdx.x == 0 && threadIdx.x < 32) back_hi_head(a, threadIdx.x, P, Hh, &bmax, &bflags);
   finish_block(&bmax, &bflags, a);
 }
 
@@ -912,14 +939,8 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
 // down, and for the high product psi by eq. (4.6) in the scaled form
 // psi = (theta - rho^-2N H(rho)) / (1 - N 2^b rho^-(N+1)).
 constexpr int kSmallMax = 160;
-__global__ void k_back_small(BackArgs a0, int kind) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  BackArgs a = a0;
-  if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
-    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
-  }
-
+// One thread; reports into the status word directly.
+__device__ void back_small_body(const BackArgs& a, int kind) {
   double P[kSmallMax + kMaxLam];
   const long long N = a.N;
   const int tot = int(N) + a.lam - 1;
@@ -977,6 +998,17 @@ __global__ void k_back_small(BackArgs a0, int kind) {
   if (bm) atomicMax(&a.status->margin_fx, bm);
   if (bm > a.emax_fx) flags |= kFlagPrecision;
   if (flags) atomicOr(&a.status->flags, flags);
+}
+
+
+__global__ void k_back_small(BackArgs a0, int kind) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  BackArgs a = a0;
+  if (a0.items) {
+    const BackItem it = a0.items[blockIdx.y];
+    a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
+  }
+  back_small_body(a, kind);
 }
 
 void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
@@ -1169,6 +1201,243 @@ void launch_carry(const CarryArgs& a, int batch, cudaStream_t s) {
   k_carry_local<<<grid, kCarryThreads, 0, s>>>(a);
   k_carry_blocks<<<dim3(1, unsigned(batch)), 1024, 0, s>>>(a);
   k_carry_apply<<<grid, kCarryThreads, 0, s>>>(a);
+}
+
+
+// ------------------------------------------------ CTA-resident products
+
+// In-shared-memory FFT of C sequences of length M (single pass, natural order).
+template <int S>
+__device__ void smem_fft(double2* Z, int M, int C, const SmallPlan& P, const double2* tws,
+                         const Tan4* tw4s) {
+  int Ns = 1;
+  double2 xs[8];
+  int base[4], kk[4];
+  for (int st = 0; st < P.nstages; ++st) {
+    const int R = P.radix[st];
+    switch (R) {
+      case 2: stockham_stage<2, S>(Z, M, C, Ns, tws, xs, base, kk); break;
+      case 3: stockham_stage<3, S>(Z, M, C, Ns, tws, xs, base, kk); break;
+      case 4:
+        if (Ns > 1) stockham_stage4t<S>(Z, M, C, Ns, tw4s + P.tw4_off[st], xs, base, kk);
+        else stockham_stage<4, S>(Z, M, C, Ns, tws, xs, base, kk);
+        break;
+      case 5: stockham_stage<5, S>(Z, M, C, Ns, tws, xs, base, kk); break;
+      default: stockham_stage<7, S>(Z, M, C, Ns, tws, xs, base, kk); break;
+    }
+    __syncthreads();
+    Ns *= R;
+  }
+}
+
+// r_L = (A_L mod 2^64) + floor(A_(L-1) / 2^64), see the carry scan kernels
+__device__ __forceinline__ __int128 limb_r(const CarryArgs& a, long long L) {
+  if (L >= a.nS) return 0;
+  const __int128 AL = limb_sum(a, L), Ap = limb_sum(a, L - 1);
+  return (__int128)(unsigned long long)AL + (Ap >> 64);
+}
+
+size_t small_smem_bytes(long long N, long long M, int tw4_len, bool need_wL) {
+  const size_t z = size_t((2 * M + 1) & ~1LL) + 2 * size_t(tw4_len) + (need_wL ? size_t(M) : 0);
+  return z * sizeof(double2) + size_t(N + 2) * 8;
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_products(SmallArgs A) {
+  extern __shared__ double2 sm[];
+  __shared__ int s_item;
+  __shared__ unsigned long long s_bmax;
+  __shared__ unsigned s_flags;
+  __shared__ unsigned fs[kSmallThreads];
+  __shared__ double s_theta[2], s_top[2];
+  __shared__ double Pw[kMaxLam];
+  __shared__ double Hh[kMaxLam + 64 + 1];
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      s_item = atomicAdd(A.counter, 1);
+      s_bmax = 0;
+      s_flags = 0;
+    }
+    __syncthreads();
+    const int idx = s_item;
+    if (idx >= A.count) return;                       // uniform
+    const SmallItem& it = A.items[idx];
+    const SmallPlan& P = A.plans[it.plan];
+    const int kind = P.kind, b = P.b;
+    const int N = int(P.N), M = int(P.M);
+    double2* Z = sm;
+    const int off4 = (2 * M + 1) & ~1;
+    Tan4* tw4s = reinterpret_cast<Tan4*>(sm + off4);
+    double2* tws = sm + off4 + 2 * P.tw4_len;
+    char* scratch = reinterpret_cast<char*>(tws + (P.need_wL ? M : 0));
+    int* du = reinterpret_cast<int*>(scratch);
+    int* dv = du + N;
+    long long* cc = reinterpret_cast<long long*>(scratch);
+    // 1. digits (split step) and the tables of this plan
+    for (int p = tid; p < N; p += kSmallThreads) {
+      int xu = 0, xv = 0;
+      if (kind == TM_HI) {
+        xu = balanced_digit(it.u, it.nlimbs, it.n, it.s0, b, p, N, true);
+        xv = balanced_digit(it.v, it.nlimbs, it.n, it.s0, b, p, N, true);
+      } else if (p < it.nd) {
+        xu = balanced_digit(it.u, it.nlimbs, it.n, 0, b, p, it.nd - 1, false);
+        xv = balanced_digit(it.v, it.nlimbs, it.n, 0, b, p, it.nd - 1, false);
+      }
+      du[p] = xu;
+      dv[p] = xv;
+    }
+    if (kind == TM_HI && tid < 2) {
+      const unsigned long long* src = tid == 0 ? it.u : it.v;
+      s_top[tid] = i2d_exact(balanced_digit(src, it.nlimbs, it.n, it.s0, b, N, N, true));
+    }
+    for (int t = tid; t < P.tw4_len; t += kSmallThreads) tw4s[t] = P.tw4[t];
+    if (P.need_wL)
+      for (int t = tid; t < M; t += kSmallThreads) tws[t] = __ldg(P.tw_sub + t);
+    __syncthreads();
+    // 2. forward map (convert step): U~ at Z as doubles [0, N), V~ at [N, 2N)
+    double* X = reinterpret_cast<double*>(Z);
+    const int lam = kind == TM_FULL ? 0 : P.lam_fwd;
+    const int Q = fx_q(b);
+    const int headj = kind == TM_HI ? P.nkappa + lam - 1 : 0;
+    for (int j = tid; j < N; j += kSmallThreads) {
+      if (kind == TM_FULL) {
+        X[j] = i2d_exact(du[j]);
+        X[N + j] = i2d_exact(dv[j]);
+      } else if (j < headj) {                        // high product, kappa-corrected F'
+        double su = 0.0, sv = 0.0;
+        for (int r = 0; r < lam; ++r) {
+          int k = j - r;
+          if (k < 0) k += N;
+          double fu = i2d_exact(du[k]), fv = i2d_exact(dv[k]);
+          if (k < P.nkappa) {
+            const double kp = __ldg(P.kappa + k);
+            fu = fma(kp, s_top[0], fu);
+            fv = fma(kp, s_top[1], fv);
+          }
+          if (r == 0) {
+            su = fu;
+            sv = fv;
+          } else {
+            const double g = fx_coef(P.fwd_tab, N, r, k, Q, b);
+            su = fma(g, fu, su);
+            sv = fma(g, fv, sv);
+          }
+        }
+        X[j] = su;
+        X[N + j] = sv;
+      } else {
+        long long su = (long long)du[j] << Q, sv = (long long)dv[j] << Q;
+        for (int r = 1; r < lam; ++r) {
+          int k = j - r;
+          if (k < 0) k += N;
+          const long long Ac = __ldg(P.fwd_tab + (long long)(r - 1) * N + k);
+          su += (Ac * du[k]) >> (r * b);
+          sv += (Ac * dv[k]) >> (r * b);
+        }
+        X[j] = scale2(__ll2double_rn(su), -Q);
+        X[N + j] = scale2(__ll2double_rn(sv), -Q);
+      }
+    }
+    if (kind == TM_HI && (tid == 0 || tid == 32)) {   // theta = sum_j rho^-j F_(N-j)
+      const int* d = tid == 0 ? du : dv;
+      const double top = s_top[tid == 0 ? 0 : 1];
+      double th = 0.0;
+      for (int j = P.ntheta - 1; j >= 0; --j) {
+        const int p = N - j;
+        if (p < 0) continue;
+        const double f = p == N ? top : i2d_exact(d[p]);
+        th = fma(__ldg(P.rho_pow + j), f, th);
+      }
+      s_theta[tid == 0 ? 0 : 1] = th;
+    }
+    __syncthreads();
+    // 3.-5. forward FFTs, twist + pointwise product, inverse FFT (convolution)
+    smem_fft<-1>(Z, M, 2, P, tws, tw4s);
+    for (int k = tid; k <= M / 2; k += kSmallThreads)
+      twist_pair(Z, Z, M, k, P.twN, 1.0 / (4.0 * double(N)));
+    __syncthreads();
+    smem_fft<1>(Z, M, 1, P, tws, tw4s);
+    // 6. back map and rounding (convert back)
+    BackArgs ba{};
+    ba.w = X;
+    ba.N = N;
+    ba.b = b;
+    ba.lam = kind == TM_FULL ? 0 : P.lam_bwd;
+    ba.tab = P.bwd_tab;
+    ba.tab2 = kind == TM_HI ? P.bwd_tab2 : P.bwd_tab;
+    ba.kappa = P.kappa;
+    ba.nkappa = P.nkappa;
+    ba.theta = s_theta;
+    ba.rho = P.rho;
+    ba.c = cc;
+    ba.count = kind == TM_HI ? N + 1 : N;
+    ba.emax_fx = it.emax_fx;
+    ba.status = A.status;
+    if (kind == TM_FULL) {
+      back_full_loop(ba, tid, kSmallThreads, &s_bmax);
+    } else if (N <= 64 || N < 2 * ba.lam + ba.nkappa + 2) {
+      if (tid == 0) back_small_body(ba, kind);
+    } else if (kind == TM_LO) {
+      back_lo_loop(ba, tid, kSmallThreads, &s_bmax, &s_flags);
+    } else {
+      back_hi_interior(ba, tid, kSmallThreads, &s_bmax);
+      if (tid < 32) back_hi_head(ba, tid, Pw, Hh, &s_bmax, &s_flags);
+    }
+    __syncthreads();
+    // 7. overlap-add and carries (one chunk of limbs per thread)
+    CarryArgs ca{};
+    ca.c = cc;
+    ca.K = kind == TM_HI ? N + 1 : N;
+    ca.b = b;
+    ca.kind = kind;
+    ca.nS = it.nS;
+    ca.round_bit = it.round_bit;
+    const long long chunk = (it.nS + kSmallThreads - 1) / kSmallThreads;
+    const long long L0 = tid * chunk, L1 = L0 + chunk < it.nS ? L0 + chunk : it.nS;
+    unsigned f = kIdentityFn;
+    for (long long L = L0; L < L1; ++L) f = compose(carry_fn(limb_r(ca, L)), f);
+    fs[tid] = f;
+    __syncthreads();
+    block_compose_scan(fs, kSmallThreads);
+    int cin = apply_fn(tid ? fs[tid - 1] : kIdentityFn, 0);
+    const long long sw = it.shift_bits >> 6;
+    const int sb = int(it.shift_bits & 63);
+    for (long long L = L0; L < L1; ++L) {
+      const __int128 r = limb_r(ca, L);
+      const unsigned long long limb = (unsigned long long)(r + cin);
+      const int cnext = apply_fn(carry_fn(r), cin);
+      const long long j = L - sw;
+      if (j >= 0 && j < it.nout) {
+        unsigned long long o = limb >> sb;
+        if (sb) o |= (unsigned long long)(limb_r(ca, L + 1) + cnext) << (64 - sb);
+        if (j == it.nout - 1) o &= it.top_mask;
+        it.out[j] = o;
+      }
+      cin = cnext;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned fl = s_flags;
+      if (s_bmax) atomicMax(&A.status->margin_fx, s_bmax);
+      if (s_bmax > it.emax_fx) fl |= kFlagPrecision;
+      if (fl) atomicOr(&A.status->flags, fl);
+    }
+    __syncthreads();
+  }
+}
+
+void set_small_smem_attribute(int bytes) {
+  // the opt-in limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_small_products) == cudaSuccess)
+    cudaFuncSetAttribute(k_small_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes - int(fa.sharedSizeBytes));
+  (void)cudaGetLastError();
+}
+
+void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s) {
+  if (a.count <= 0 || grid <= 0) return;
+  k_small_products<<<grid, kSmallThreads, smem, s>>>(a);
 }
 
 // ------------------------------------------------------------ tables

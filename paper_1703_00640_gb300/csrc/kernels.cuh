@@ -126,6 +126,52 @@ struct CarryArgs {
 // (coef 2^(Q + r b)) x digit stay below 2^61.
 __host__ __device__ inline int fx_q(int b) { return 61 - b; }
 
+// CTA-resident products: one CTA computes a whole product of complex length
+// M <= kSmallMaxM in shared memory (single-pass FFT tables).
+constexpr long long kSmallMaxM = 2048;
+constexpr int kSmallThreads = 1024;
+
+struct SmallPlan {
+  int kind, b, lam_fwd, lam_bwd, nkappa, ntheta;
+  long long N, M;
+  double rho;
+  int nstages;
+  int radix[kMaxStages];
+  int tw4_off[kMaxStages];
+  int tw4_len, need_wL;
+  const double2* tw_sub;         // omega_M^k, k < M
+  const Tan4* tw4;
+  const double2* twN;            // omega_N^k, k <= M/2
+  const long long* fwd_tab;
+  const double* bwd_tab;
+  const double* bwd_tab2;
+  const double* kappa;
+  const double* rho_pow;
+};
+
+struct SmallItem {
+  const unsigned long long* u;
+  const unsigned long long* v;
+  unsigned long long* out;
+  unsigned long long n;
+  long long nlimbs, nd, s0;
+  long long nS, round_bit, shift_bits, nout;
+  unsigned long long top_mask, emax_fx;
+  int plan;
+};
+
+struct SmallArgs {
+  const SmallItem* items;
+  int count;
+  const SmallPlan* plans;
+  int* counter;                  // next item to take (zeroed before the launch)
+  DevStatus* status;
+};
+
+// shared memory a CTA-resident product of this plan needs
+size_t small_smem_bytes(long long N, long long M, int tw4_len, bool need_wL);
+void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s);
+
 // table initialisation
 // tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
