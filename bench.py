@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -164,6 +166,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ batched configuration
+
+def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
+    """count products, n log-uniform in [2^12, 2^20] bits, half low / half high,
+    uniform random operands: one graph launch (tm_batch_launch) per step against
+    `count` individual tm_mul launches per step, both timed with CUDA events."""
+    import workloads
+    sizes = workloads.log_uniform_sizes(count, 12, 20, seed=seed)
+    items = []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        kind = "lo" if i % 2 == 0 else "hi"
+        u, v = workloads.pattern_limbs("random", n, seed=10000 * seed + i)
+        du = torch.from_numpy(u.view(np.int64)).cuda()
+        dv = torch.from_numpy(v.view(np.int64)).cuda()
+        out = torch.empty(pkg.out_limbs(kind, n), dtype=torch.int64, device="cuda")
+        items.append((kind, n, out, du, dv))
+    batch = pkg.Batch(items, stream=stream)
+    ref = [torch.empty_like(it[2]) for it in items]
+    for _ in range(max(1, warmup)):
+        batch.launch(stream)
+        for it, r in zip(items, ref):
+            pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
+    torch.cuda.synchronize()
+    same = all(torch.equal(it[2], r) for it, r in zip(items, ref))
+    g_ms, p_ms = [], []
+    for _ in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        batch.launch(stream)
+        e1.record(stream)
+        for it, r in zip(items, ref):
+            pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
+        e2.record(stream)
+        e2.synchronize()
+        g_ms.append(e0.elapsed_time(e1))
+        p_ms.append(e1.elapsed_time(e2))
+    st = batch.status(stream)
+    pkg.stream_status(stream)
+    batch.close()
+    bits = float(sum(int(n) for n in sizes))
+    med_g, med_p = float(np.median(g_ms)), float(np.median(p_ms))
+    return {
+        "products": count, "n_bits": "log-uniform in [2^12, 2^20]", "kinds": "50/50 low/high",
+        "graph_launch_ms": {"p50": med_g, "p99": float(np.percentile(g_ms, 99))},
+        "per_product_launches_ms": {"p50": med_p, "p99": float(np.percentile(p_ms, 99))},
+        "products_per_s": count / (med_g * 1e-3),
+        "gbit_s": bits / (med_g * 1e-3) / 1e9,
+        "speedup_vs_per_product_launches": med_p / med_g,
+        "bit_exact_vs_single": bool(same), "status": st["rc"], "margin": st["margin"],
+    }
+
+
 # ------------------------------------------------------------ CUDA arm
 
 def run_cuda(args):
@@ -273,6 +328,11 @@ def run_cuda(args):
     e2e_val = 2 * n * len(e2e_t) * world / sum(e2e_t) / 1e9
     assert np.array_equal(hout["lo"].numpy(), outs["lo"].cpu().numpy())
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(pkg, torch, np, args.batch_count, max(3, min(args.steps, 10)),
+                              args.warmup, stream, seed=4 + rank)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -309,6 +369,7 @@ def run_cuda(args):
                      "traffic": None,
                      "note": "FP64; 5 M log2 M flops per complex FFT of length M = N/2, 3 per "
                              "product; peak = nominal FP64 (recipe), not measured"},
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 2 * nl * 8,
