@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--served", action="store_true",
+                    help="run the served-stream configuration instead of the default")
+    ap.add_argument("--served-count", type=int, default=20000)
     ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
@@ -219,6 +222,106 @@ def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
     }
 
 
+# ------------------------------------------------------------ served configuration
+
+def served_requests(pkg, torch, np, count, seed, k=1 << 24):
+    """count requests, n log-uniform in [2^10, 2^k]; 40% high products of x with
+    the top n bits of a fixed k-bit Barrett-shaped reciprocal, 30% random low,
+    30% random high."""
+    import workloads
+    _, R = workloads.barrett_reciprocal(k, seed)
+    sizes = workloads.log_uniform_sizes(count, 10, 24, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cls = rng.uniform(size=count)
+    reqs = []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        u, v = workloads.pattern_limbs("random", n, seed=seed * 100000 + i)
+        if cls[i] < 0.4:
+            kind, v = "hi", workloads.top_bits(R, k, n)
+        else:
+            kind = "lo" if cls[i] < 0.7 else "hi"
+        du = torch.from_numpy(u.view(np.int64)).cuda()
+        dv = torch.from_numpy(np.ascontiguousarray(v).view(np.int64)).cuda()
+        out = torch.empty(pkg.out_limbs(kind, n), dtype=torch.int64, device="cuda")
+        reqs.append((kind, n, out, du, dv))
+    return reqs
+
+
+def serve(pkg, reqs, arrivals, budget, slots):
+    """Request loop: submits each request at its arrival time (host clock),
+    polls progress, and records completion latencies."""
+    import time as _t
+    srv = pkg.Server(budget, slots)
+    order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
+    t_of, lat = {}, {}
+    j = 0
+    t0 = _t.perf_counter()
+    while len(lat) < len(reqs):
+        now = _t.perf_counter() - t0
+        while j < len(order) and arrivals[order[j]] <= now:
+            i = order[j]
+            kind, n, out, u, v = reqs[i]
+            t_of[srv.submit(kind, out, u, v, n)] = i
+            j += 1
+        for t, st in srv.progress():
+            if st != 0:
+                raise RuntimeError(f"request {t_of[t]} failed with status {st}")
+            lat[t_of[t]] = (_t.perf_counter() - t0) - arrivals[t_of[t]]
+    total = _t.perf_counter() - t0
+    srv.close()
+    return total, [lat[i] for i in range(len(reqs))]
+
+
+def run_served(args):
+    import numpy as np
+    import torch
+    import paper_1703_00640_gb300 as pkg
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    pkg.build()
+    pkg.load()
+    count = args.served_count
+    reqs = served_requests(pkg, torch, np, count, seed=5 + rank)
+    budget = 2 << 30                        # device bytes for workspaces in flight
+    slots = 8
+    bits = float(sum(r[1] for r in reqs))
+    # warm: plans and tables of every request
+    total_w, _ = serve(pkg, reqs, [0.0] * count, budget, slots)
+    # saturated: every request arrives at once
+    total_s, lat_s = serve(pkg, reqs, [0.0] * count, budget, slots)
+    rate_sat = count / total_s
+    loads = {}
+    for frac in (0.5, 0.8):
+        arr = np.asarray(__import__("workloads").poisson_arrivals(count, frac * rate_sat, seed=9))
+        arr -= arr[0]
+        total, lat = serve(pkg, reqs, list(arr), budget, slots)
+        loads[f"{frac}x"] = {"rate_per_s": frac * rate_sat, "wall_s": total,
+                             "throughput_per_s": count / total,
+                             "gbit_s": bits / total / 1e9,
+                             "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                            "p99": 1e3 * float(np.percentile(lat, 99))}}
+    # results in the mix equal the same products alone (a sample)
+    same = True
+    for i in np.random.default_rng(1).choice(count, 64, replace=False):
+        kind, n, out, u, v = reqs[int(i)]
+        ref, _ = pkg.mul(kind, u, v, n)
+        same = same and bool(torch.equal(out, ref))
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "config": {"workload": f"served stream: {count} requests, Poisson "
+                "arrivals, n log-uniform in [2^10, 2^24] bits, 40% high products with the top n "
+                "bits of a fixed 2^24-bit Barrett reciprocal, 30% low, 30% high; device-memory "
+                f"budget {budget >> 20} MiB, {slots} slots"},
+            "unit": UNIT, "value": bits / total_s / 1e9, "higher_is_better": True,
+            "saturated": {"wall_s": total_s, "throughput_per_s": rate_sat,
+                          "gbit_s": bits / total_s / 1e9,
+                          "latency_ms": {"p50": 1e3 * float(np.percentile(lat_s, 50)),
+                                         "p99": 1e3 * float(np.percentile(lat_s, 99))}},
+            "loads": loads, "bit_exact_sample_vs_alone": same, "n_gpus": world,
+            "dtype": "f64", "data": "synthetic"}), flush=True)
+
+
 # ------------------------------------------------------------ CUDA arm
 
 def run_cuda(args):
@@ -387,6 +490,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.served:
+        run_served(args)
     else:
         run_cuda(args)
 

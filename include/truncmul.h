@@ -207,6 +207,39 @@ int tm_batch_destroy(tm_batch* batch);
 int tm_mul_batch(const tm_desc* descs, uint32_t count, void* stream, tm_report* rep);
 
 /*
+ * Serving: a request queue with continuous batching under a device-memory
+ * budget. Requests (kind, n_bits, DEVICE pointers as for tm_mul) are queued by
+ * tm_server_submit and identified by the returned ticket (>= 0; a negative
+ * value is a TM_E* code and nothing was queued). tm_server_progress never
+ * blocks: it retires finished work (filling up to max_done completions with
+ * their ticket and status), then admits queued requests, in arrival order,
+ * into free slots: each slot is a CUDA stream, so admitted work overlaps on the
+ * device with work already running. Consecutive small requests (transform
+ * length N <= 4096) leave together as one launch of CTA-resident products;
+ * a larger request takes a slot alone and is admitted only while the
+ * workspaces of the requests in flight stay within budget_bytes (one request
+ * is always admitted when nothing is in flight). Plan tables stay resident.
+ * Results are bit-identical to tm_mul of the same request. Call from one
+ * thread at a time per server (the calls lock). tm_server_pending returns the
+ * number of requests queued or in flight; tm_server_destroy waits for the
+ * work in flight and frees the server. The paper has no counterpart; this is
+ * the library's serving layer.
+ */
+typedef struct tm_server tm_server;
+typedef struct tm_completion {
+  int64_t ticket;
+  int32_t status;         /* TM_OK, TM_EPRECISION or TM_ECUDA */
+  int32_t reserved;
+} tm_completion;
+
+int tm_server_create(tm_server** server, uint64_t budget_bytes, int slots);
+int64_t tm_server_submit(tm_server* server, int kind, uint64_t* out, const uint64_t* u,
+                         const uint64_t* v, uint64_t n_bits);
+int tm_server_progress(tm_server* server, tm_completion* done, int max_done);
+int tm_server_pending(tm_server* server);
+int tm_server_destroy(tm_server* server);
+
+/*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
  * for checking the method stage by stage:
  *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2,

@@ -37,6 +37,11 @@ class Desc(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
 
+class Completion(ctypes.Structure):
+    """tm_completion (include/truncmul.h)."""
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class TruncMulError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})")
@@ -48,7 +53,8 @@ PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "car
 STATIC_MAX_BITS = 65536
 EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
-           "tm_batch_destroy", "tm_mul_batch", "tm_coeffs",
+           "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
+           "tm_server_progress", "tm_server_pending", "tm_server_destroy", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -85,6 +91,16 @@ def load(path: str = None):
     lib.tm_batch_status.argtypes = [P, P, R]
     lib.tm_batch_destroy.argtypes = [P]
     lib.tm_mul_batch.argtypes = [D, ctypes.c_uint32, P, R]
+    lib.tm_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64, ctypes.c_int]
+    lib.tm_server_create.restype = ctypes.c_int
+    lib.tm_server_submit.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_uint64]
+    lib.tm_server_submit.restype = ctypes.c_int64
+    lib.tm_server_progress.argtypes = [P, ctypes.POINTER(Completion), ctypes.c_int]
+    lib.tm_server_progress.restype = ctypes.c_int
+    lib.tm_server_pending.argtypes = [P]
+    lib.tm_server_pending.restype = ctypes.c_int
+    lib.tm_server_destroy.argtypes = [P]
+    lib.tm_server_destroy.restype = ctypes.c_int
     lib.tm_stream_status.argtypes = [P, R]
     lib.tm_release.argtypes = []
     lib.tm_strerror.argtypes = [ctypes.c_int]
@@ -236,6 +252,51 @@ def mul_batch(items, stream=None) -> dict:
     if rc:
         raise TruncMulError(rc, "tm_mul_batch")
     return rep.as_dict()
+
+
+class Server:
+    """tm_server: queued requests with continuous batching under a memory budget.
+    submit() queues (device tensors must stay alive until completion);
+    progress() retires finished work and admits queued requests, never blocking."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4):
+        self._h = ctypes.c_void_p()
+        rc = load().tm_server_create(ctypes.byref(self._h), int(budget_bytes), int(slots))
+        if rc:
+            self._h = None
+            raise TruncMulError(rc, "tm_server_create")
+        self._buf = (Completion * 4096)()
+        self._keep = {}
+
+    def submit(self, kind, out, u, v, n_bits: int) -> int:
+        t = load().tm_server_submit(self._h, _kind(kind), _ptr(out), _ptr(u), _ptr(v), int(n_bits))
+        if t < 0:
+            raise TruncMulError(int(t), "tm_server_submit")
+        self._keep[t] = (out, u, v)
+        return t
+
+    def progress(self):
+        rc = load().tm_server_progress(self._h, self._buf, len(self._buf))
+        if rc < 0:
+            raise TruncMulError(rc, "tm_server_progress")
+        done = [(self._buf[i].ticket, self._buf[i].status) for i in range(rc)]
+        for t, _ in done:
+            self._keep.pop(t, None)
+        return done
+
+    def pending(self) -> int:
+        return load().tm_server_pending(self._h)
+
+    def close(self):
+        if self._h:
+            load().tm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mul_lo(u, v, n_bits, **kw):

@@ -321,8 +321,6 @@ void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
   rep->table_bytes = 0;
 }
 
-namespace {
-
 // Enqueues one whole product with parameters p and tables pe; `coeff_out`
 // receives the rounded coefficients and stops the pipeline before the carry
 // scan when non-null.
@@ -420,6 +418,8 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   TM_CHECK(cudaGetLastError());
   return TM_OK;
 }
+
+namespace {
 
 int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n, void* stream,
         tm_report* rep, int64_t* coeff_out, void* const* events = nullptr) {

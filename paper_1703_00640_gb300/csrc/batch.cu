@@ -199,6 +199,8 @@ void destroy(tm_batch* B) {
   delete B;
 }
 
+}  // namespace
+
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
   SmallPlan sp{};
   const FftPass& fp = pe.fft.pass[0];
@@ -226,6 +228,8 @@ SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
   sp.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
   return sp;
 }
+
+namespace {
 
 SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
   SmallItem it{};

@@ -50,6 +50,12 @@ int get_tables(const PlanParams& p, bool single_pass, cudaStream_t s,
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
                long long stride, cudaStream_t s);
 void ensure_kernel_attributes();
+// One whole product on stream s with workspace ws (see api.cu).
+int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+            cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
+            int64_t* coeff_out, void* const* events);
+// Single-pass plan tables of a CTA-resident product, and its per-product item.
+SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe);
 int read_status(cudaStream_t s, DevStatus* status, tm_report* rep);
 void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep);
 

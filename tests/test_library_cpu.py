@@ -23,7 +23,7 @@ def pkg():
 
 def _declared():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(tm_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(tm_\w+)\s*\(", text, re.M)))
 
 
 def test_exports_every_declared_symbol(pkg):

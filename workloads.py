@@ -83,3 +83,27 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson process with the given rate."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.cumsum(rng.exponential(1.0 / rate_per_s, count))
+
+
+def barrett_reciprocal(k: int, seed: int):
+    """A fixed k-bit modulus m (top bit set, uniform random below) and the
+    Barrett-shaped reciprocal R = min(floor(2^(2k-1) / m), 2^k - 1), as uint64
+    limb arrays (plain integer division; no part of the multiplication method)."""
+    mbits = random_limbs(k, seed)
+    mbits[(k - 1) // 64] |= np.uint64(1 << ((k - 1) % 64))
+    m = int.from_bytes(mbits.astype("<u8").tobytes(), "little")
+    R = min((1 << (2 * k - 1)) // m, (1 << k) - 1)
+    nl = nlimbs(k)
+    r = np.frombuffer(R.to_bytes(8 * nl, "little"), dtype="<u8").astype(np.uint64)
+    return mbits, r
+
+
+def top_bits(limbs: np.ndarray, k: int, n: int) -> np.ndarray:
+    """The top n bits of the k-bit integer in `limbs`, as ceil(n/64) limbs."""
+    s = k - n
+    q, r = s // 64, s % 64
+    out_n = nlimbs(n)
+    src = np.concatenate([limbs, np.zeros(2, dtype=np.uint64)])
+    lo = src[q:q + out_n] >> np.uint64(r)
+    hi = (src[q + 1:q + 1 + out_n] << np.uint64(64 - r)) if r else np.zeros(out_n, np.uint64)
+    return mask_top((lo | hi).astype(np.uint64), n)
