@@ -27,6 +27,9 @@ sys.path.insert(0, ROOT)
 METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50/p99 ms"
 UNIT = "Gbit/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs)
+FP64_DFMA_MEASURED = 1.008   # DFMA/DADD/DMUL issue ceiling measured on this GB300 pool
+# DRAM bytes per k_fft_pass launch from profiles/k_fft_pass_n2p24.md (n = 2^24 only)
+FFT_TRAFFIC_N2P24 = 32.4e6
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -469,9 +472,13 @@ def run_cuda(args):
         "margin": margin, "status_after_timed_region": st["rc"],
         "roofline": {"bound": "alu", "kernel": "k_fft_pass", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": FFT_TRAFFIC_N2P24 if n == 1 << 24 else None,
+                     "peak_measured_dfma": FP64_DFMA_MEASURED,
+                     "frac_of_measured": achieved / FP64_DFMA_MEASURED,
                      "note": "FP64; 5 M log2 M flops per complex FFT of length M = N/2, 3 per "
-                             "product; peak = nominal FP64 (recipe), not measured"},
+                             "product; peak = nominal FP64 (recipe table), frac_of_measured "
+                             "against the measured DFMA issue ceiling; traffic = ncu DRAM "
+                             "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
