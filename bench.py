@@ -46,6 +46,8 @@ def parse():
                     help="run the served-stream configuration instead of the default")
     ap.add_argument("--served-count", type=int, default=20000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the square / kept-operand timings")
     return ap.parse_args()
 
 
@@ -434,6 +436,40 @@ def run_cuda(args):
     e2e_val = 2 * n * len(e2e_t) * world / sum(e2e_t) / 1e9
     assert np.array_equal(hout["lo"].numpy(), outs["lo"].cpu().numpy())
 
+    # squares (u == v) and kept operand transforms: one forward map and one forward
+    # FFT per product instead of two; per-product device time, L2 flushed before each
+    def timed(fn, reps):
+        ts = []
+        for i in range(args.warmup + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            if i >= args.warmup:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ts)
+
+    variants = None
+    if not args.no_variants:
+        reps = max(5, min(args.steps, 20))
+        variants = {"square_ms": {}, "kept_operand_ms": {}, "two_operand_ms": {}}
+        for k in kinds:
+            variants["two_operand_ms"][k] = timed(
+                lambda: pkg.mul(k, u, v, n, out=outs[k], report=False), reps)
+            variants["square_ms"][k] = timed(
+                lambda: pkg.mul(k, u, u, n, out=outs[k], report=False), reps)
+            op = pkg.Operand(k, v, n)
+            variants["kept_operand_ms"][k] = timed(
+                lambda: op.mul(u, out=outs[k], report=False), reps)
+            ref, _ = pkg.mul(k, u, v, n)
+            got, _ = op.mul(u)
+            assert torch.equal(ref, got)
+            op.close()
+        st2 = pkg.stream_status(stream)
+        assert st2["rc"] == 0, st2
+
     batched = None
     if not args.no_batched:
         batched = run_batched(pkg, torch, np, args.batch_count, max(3, min(args.steps, 10)),
@@ -480,6 +516,7 @@ def run_cuda(args):
                              "against the measured DFMA issue ceiling; traffic = ncu DRAM "
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
+        "square_and_kept_operand": variants,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 2 * nl * 8,

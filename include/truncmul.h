@@ -30,7 +30,7 @@
  *
  * Memory and ownership. Unless a function says otherwise, u, v and out are
  * DEVICE pointers owned by the caller; out must not overlap u or v (u == v is
- * allowed). The library owns a plan cache (twiddle and map tables, kept
+ * allowed and squares: one forward map and one forward FFT instead of two). The library owns a plan cache (twiddle and map tables, kept
  * resident per (kind, n) and device) and a workspace per (device, stream),
  * both grown on demand and kept until tm_release() or process exit. Calls on
  * the same stream are ordered; calls on different streams use different
@@ -238,6 +238,36 @@ int64_t tm_server_submit(tm_server* server, int kind, uint64_t* out, const uint6
 int tm_server_progress(tm_server* server, tm_completion* done, int max_done);
 int tm_server_pending(tm_server* server);
 int tm_server_destroy(tm_server* server);
+
+/*
+ * Kept operand transforms. The paper has no counterpart; it splits the
+ * convolution of Algorithms 1-3 at its forward transforms. When one operand v is
+ * multiplied by many u (a fixed Barrett reciprocal, a fixed modulus), its split,
+ * forward map (alpha* for low, gamma-dagger with theta_V for high, none for full)
+ * and forward FFT are computed once and kept on the device; each later product
+ * then runs one forward map and one forward FFT, two transforms instead of three.
+ *
+ * tm_operand_create: plans (kind, n_bits), allocates the operand (8 N + 256
+ * bytes of device memory, N the plan's transform length; tm_plan_query reports
+ * N) and enqueues v's transform on `stream`. v is a device pointer with
+ * ceil(n_bits/64) limbs; it is read by that enqueued work only and may be reused
+ * once the stream has passed it. *out receives the handle (NULL on error). Use
+ * the operand on the same stream, or order other streams after it (events).
+ * tm_mul_operand: the product of the operand's kind and n_bits of u (device,
+ * ceil(n_bits/64) limbs) and the kept v, into out (limb count as for tm_mul of
+ * that kind). Same stream, status and rep conventions as tm_mul; TM_EINVAL when
+ * the current device is not the one the operand was made on, TM_EALIAS when out
+ * overlaps u. Results are bit-identical to tm_mul(kind, out, u, v, n_bits, ...).
+ * tm_operand_destroy: frees the operand. No enqueued product may still read it.
+ * The handle is not tied to the plan cache: tm_release() leaves it valid.
+ * Returns TM_OK or a negative TM_E* code.
+ */
+typedef struct tm_operand tm_operand;
+int tm_operand_create(int kind, uint64_t n_bits, const uint64_t* v, void* stream,
+                      tm_operand** out);
+int tm_mul_operand(uint64_t* out, const uint64_t* u, const tm_operand* v, void* stream,
+                   tm_report* rep);
+int tm_operand_destroy(tm_operand* op);
 
 /*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),

@@ -54,7 +54,8 @@ STATIC_MAX_BITS = 65536
 EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
-           "tm_server_progress", "tm_server_pending", "tm_server_destroy", "tm_coeffs",
+           "tm_server_progress", "tm_server_pending", "tm_server_destroy",
+           "tm_operand_create", "tm_mul_operand", "tm_operand_destroy", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -101,6 +102,12 @@ def load(path: str = None):
     lib.tm_server_pending.restype = ctypes.c_int
     lib.tm_server_destroy.argtypes = [P]
     lib.tm_server_destroy.restype = ctypes.c_int
+    lib.tm_operand_create.argtypes = [ctypes.c_int, ctypes.c_uint64, P, P,
+                                      ctypes.POINTER(ctypes.c_void_p)]
+    lib.tm_mul_operand.argtypes = [P, P, P, P, R]
+    lib.tm_operand_destroy.argtypes = [P]
+    for name in ("tm_operand_create", "tm_mul_operand", "tm_operand_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.tm_stream_status.argtypes = [P, R]
     lib.tm_release.argtypes = []
     lib.tm_strerror.argtypes = [ctypes.c_int]
@@ -252,6 +259,47 @@ def mul_batch(items, stream=None) -> dict:
     if rc:
         raise TruncMulError(rc, "tm_mul_batch")
     return rep.as_dict()
+
+
+class Operand:
+    """tm_operand: the forward transform of a fixed operand v, kept on the device.
+    mul(u) then computes the product of this kind and n_bits with two transforms
+    instead of three; results are bit-identical to mul(kind, u, v, n_bits)."""
+
+    def __init__(self, kind, v, n_bits: int, stream=None):
+        self.kind = _kind(kind)
+        self.n_bits = int(n_bits)
+        self.device = v.device
+        self._h = ctypes.c_void_p()
+        rc = load().tm_operand_create(self.kind, self.n_bits, _ptr(v), _stream_ptr(stream),
+                                      ctypes.byref(self._h))
+        if rc:
+            self._h = None
+            raise TruncMulError(rc, "tm_operand_create")
+
+    def mul(self, u, out=None, stream=None, report: bool = True, check: bool = True):
+        """tm_mul_operand. Returns (out, report dict or None)."""
+        import torch
+        if out is None:
+            out = torch.empty(out_limbs(self.kind, self.n_bits), dtype=torch.int64,
+                              device=u.device)
+        rep = Report() if report else None
+        rc = load().tm_mul_operand(_ptr(out), _ptr(u), self._h, _stream_ptr(stream),
+                                   ctypes.byref(rep) if rep is not None else None)
+        if check and rc:
+            raise TruncMulError(rc, "tm_mul_operand")
+        return out, (rep.as_dict() if rep is not None else None)
+
+    def close(self):
+        if self._h:
+            load().tm_operand_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

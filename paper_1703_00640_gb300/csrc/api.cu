@@ -324,28 +324,20 @@ void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
 // Enqueues one whole product with parameters p and tables pe; `coeff_out`
 // receives the rounded coefficients and stops the pipeline before the carry
 // scan when non-null.
-int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
-            cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
-            int64_t* coeff_out, void* const* events) {
-  auto mark = [&](int i) {
-    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
-  };
-  ensure_kernel_attributes();
-  mark(0);
-  const int64_t N = p.N, M = pe.M;
-  const size_t region = std::max(align_up(size_t(2) * M * sizeof(double2)),
-                                 align_up(size_t(N + 2) * 8));
-  double2* R0 = reinterpret_cast<double2*>(ws.base);
-  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
-  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
-  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
+namespace {
+
+// Digits and forward map (split and convert steps of Algorithms 1-3) of u and v,
+// or of u alone (one_operand), into X.
+void fwd_args(int kind, const uint64_t* u, const uint64_t* v, uint64_t n, const PlanParams& p,
+              const PlanEntry& pe, double* X, double* theta, bool one_operand,
+              const double* theta_v, FwdArgs* out) {
   FwdArgs fa{};
   fa.u = reinterpret_cast<const unsigned long long*>(u);
   fa.v = reinterpret_cast<const unsigned long long*>(v);
   fa.n = n;
   fa.nlimbs = limbs_of(n);
   fa.b = p.b;
-  fa.N = N;
+  fa.N = p.N;
   fa.nd = p.n_digits;
   fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
   fa.tab = pe.fwd_tab;
@@ -353,18 +345,69 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   fa.nkappa = pe.nkappa;
   fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
   fa.ntheta = pe.ntheta;
-  fa.s0 = int64_t(N + 1) * p.b - int64_t(n);
-  fa.X = reinterpret_cast<double*>(R0);
+  fa.s0 = int64_t(p.N + 1) * p.b - int64_t(n);
+  fa.X = X;
   fa.theta = theta;
+  fa.one_operand = one_operand ? 1 : 0;
+  fa.theta_v = theta_v;
+  *out = fa;
+}
+
+size_t region_bytes(const PlanParams& p, int64_t M) {
+  return std::max(align_up(size_t(2) * M * sizeof(double2)), align_up(size_t(p.N + 2) * 8));
+}
+
+}  // namespace
+
+int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
+                      const PlanParams& p, const PlanEntry& pe, Workspace& ws, double2* spec,
+                      double* theta) {
+  ensure_kernel_attributes();
+  const int64_t M = pe.M;
+  double2* R0 = reinterpret_cast<double2*>(ws.base);
+  double2* R1 = reinterpret_cast<double2*>(ws.base + region_bytes(p, M));
+  // the passes alternate buffers: start where the last pass lands in spec
+  double2* bufs[2] = {R0, R1};
+  bufs[pe.fft.npass & 1] = spec;
+  FwdArgs fa;
+  fwd_args(kind, v, v, n, p, pe, reinterpret_cast<double*>(bufs[0]), theta, true, nullptr, &fa);
+  launch_fwd(kind, fa, 1, s);
+  const int cur = launch_fft(pe, bufs, 0, -1, 1, M, s);
+  if (bufs[cur] != spec) return TM_ECUDA;   // (cannot happen: npass passes alternate)
+  TM_CHECK(cudaGetLastError());
+  return TM_OK;
+}
+
+int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+            cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
+            int64_t* coeff_out, void* const* events, const KeptOperand* kept) {
+  auto mark = [&](int i) {
+    if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
+  };
+  ensure_kernel_attributes();
+  mark(0);
+  const int64_t N = p.N, M = pe.M;
+  const size_t region = region_bytes(p, M);
+  double2* R0 = reinterpret_cast<double2*>(ws.base);
+  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
+  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
+  const bool square = !kept && u == v;
+  const bool one = square || kept;
+  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
+  FwdArgs fa;
+  fwd_args(kind, u, v, n, p, pe, reinterpret_cast<double*>(R0), theta, one,
+           kept ? kept->theta : nullptr, &fa);
   launch_fwd(kind, fa, 1, s);
   mark(1);
-  // 2. forward FFTs of both operands (complex length M, batch 2)
+  // 2. forward FFTs of both operands (complex length M, batch 2), or of u alone
   double2* bufs[2] = {R0, R1};
-  int cur = launch_fft(pe, bufs, 0, -1, 2, M, s);
+  int cur = launch_fft(pe, bufs, 0, -1, one ? 1 : 2, M, s);
   mark(2);
   // 3. real-FFT twist, pointwise product, inverse pre-twist
-  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), 1, 0,
-               0, s);
+  const double2* Zu = bufs[cur];
+  const double2* Zv = kept ? kept->spec : (square ? Zu : Zu + M);
+  launch_twist(Zu, Zv, bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), 1, 0, 0,
+               s);
   cur ^= 1;
   mark(3);
   // 4. inverse FFT (batch 1)
@@ -575,6 +618,18 @@ int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, ui
 }  // namespace
 }  // namespace tmul
 
+// A kept forward transform (tm_operand_create): one device allocation holding the
+// spectrum of V~ and theta_V.
+struct tm_operand {
+  int kind;
+  uint64_t n;
+  int device;
+  tmul::PlanParams p;
+  double2* spec;
+  double* theta;
+  size_t bytes;
+};
+
 extern "C" {
 
 int tm_mul_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
@@ -641,6 +696,89 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
       cudaStreamSynchronize(s) != cudaSuccess)
     return TM_ECUDA;
   return rc;
+}
+
+int tm_operand_create(int kind, uint64_t n_bits, const uint64_t* v, void* stream,
+                      tm_operand** out) {
+  if (!out || !v) return TM_EINVAL;
+  *out = nullptr;
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  tmul::PlanParams p;
+  int rc = tmul::get_params(kind, n_bits, &p);
+  if (rc) return rc;
+  std::shared_ptr<tmul::PlanEntry> pe;
+  rc = tmul::get_tables(p, false, s, &pe);
+  if (rc) return rc;
+  tmul::Workspace* ws = nullptr;
+  rc = tmul::get_workspace(s, tmul::workspace_bytes(p), &ws);
+  if (rc) return rc;
+  const size_t spec_bytes = tmul::align_up(size_t(pe->M) * sizeof(double2));
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, spec_bytes + 256);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TM_ENOMEM : TM_ECUDA;
+  }
+  tm_operand* op = new tm_operand;
+  op->kind = kind;
+  op->n = n_bits;
+  op->device = dev;
+  op->p = p;
+  op->spec = reinterpret_cast<double2*>(base);
+  op->theta = reinterpret_cast<double*>(base + spec_bytes);
+  op->bytes = spec_bytes + 256;
+  rc = tmul::enqueue_transform(kind, v, n_bits, s, p, *pe, *ws, op->spec, op->theta);
+  if (rc) {
+    cudaFree(base);
+    delete op;
+    return rc;
+  }
+  *out = op;
+  return TM_OK;
+}
+
+int tm_mul_operand(uint64_t* out, const uint64_t* u, const tm_operand* v, void* stream,
+                   tm_report* rep) {
+  if (!out || !u || !v) return TM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  if (dev != v->device) return TM_EINVAL;
+  const int kind = v->kind;
+  const uint64_t n = v->n;
+  const size_t in_bytes = size_t(tmul::limbs_of(n)) * 8;
+  const size_t ob = size_t(tmul::out_limbs(kind, n)) * 8;
+  if (tmul::overlaps(out, ob, u, in_bytes) || tmul::overlaps(out, ob, v->spec, v->bytes))
+    return TM_EALIAS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::shared_ptr<tmul::PlanEntry> pe;
+  int rc = tmul::get_tables(v->p, false, s, &pe);
+  if (rc) return rc;
+  tmul::Workspace* ws = nullptr;
+  rc = tmul::get_workspace(s, tmul::workspace_bytes(v->p), &ws);
+  if (rc) return rc;
+  const tmul::KeptOperand kept{v->spec, v->theta};
+  rc = tmul::enqueue(kind, out, u, u, n, s, v->p, *pe, *ws, nullptr, nullptr, &kept);
+  if (rc) return rc;
+  if (!rep) return TM_OK;
+  tmul::fill_plan_report(v->p, pe->fft, rep);
+  rep->table_bytes = pe->table_bytes;
+  return tmul::read_status(s, ws->status, rep);
+}
+
+int tm_operand_destroy(tm_operand* op) {
+  if (!op) return TM_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  if (dev != op->device && cudaSetDevice(op->device) != cudaSuccess) return TM_ECUDA;
+  const cudaError_t e = cudaFree(op->spec);
+  if (dev != op->device) cudaSetDevice(dev);
+  delete op;
+  return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
 int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep) {

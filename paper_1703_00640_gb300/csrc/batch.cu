@@ -96,8 +96,8 @@ int enqueue_group(tm_batch* B, const Group& g, cudaStream_t s) {
   launch_fwd(kind, fa, cnt, s);
   double2* bufs[2] = {R0, R1};
   int cur = launch_fft(pe, bufs, 0, -1, 2 * cnt, M, s);
-  launch_twist(bufs[cur], bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), cnt,
-               2 * M, 2 * M, s);
+  launch_twist(bufs[cur], bufs[cur] + M, bufs[cur ^ 1], M, pe.tw + pe.twN_off,
+               1.0 / (4.0 * double(N)), cnt, 2 * M, 2 * M, s);
   cur ^= 1;
   cur = launch_fft(pe, bufs, cur, 1, cnt, 2 * M, s);
   if (cur != 1) return TM_EINVAL;       // the item layout assumes the output in R1

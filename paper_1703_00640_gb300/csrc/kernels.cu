@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
     a.X = it.X; a.theta = it.theta;
   }
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  const bool two = !a.one_operand;
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
   const int span = kFwdTile + halo;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
     int xu = 0, xv = 0;
     if (p < a.N && p < a.nd) {
       xu = balanced_digit(a.u, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
-      xv = balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
+      if (two) xv = balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
     }
     du[t] = xu;
     dv[t] = xv;
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
     if (j >= a.N) break;
     if (a.lam == 0) {
       a.X[j] = i2d_exact(du[t]);
-      a.X[a.N + j] = i2d_exact(dv[t]);
+      if (two) a.X[a.N + j] = i2d_exact(dv[t]);
       continue;
     }
     long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
@@ -268,10 +269,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
       if (k < 0) k += a.N;
       const long long A = __ldg(a.tab + (long long)(r - 1) * a.N + k);
       su += (A * du[t + halo - r]) >> (r * a.b);
-      sv += (A * dv[t + halo - r]) >> (r * a.b);
+      if (two) sv += (A * dv[t + halo - r]) >> (r * a.b);
     }
     a.X[j] = scale2(__ll2double_rn(su), -Q);
-    a.X[a.N + j] = scale2(__ll2double_rn(sv), -Q);
+    if (two) a.X[a.N + j] = scale2(__ll2double_rn(sv), -Q);
   }
 }
 
@@ -297,6 +298,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
   __shared__ double topu, topv;
+  const bool two = !a.one_operand;
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam - 1;
   const int span = kFwdTile + halo;
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
   const int Q = fx_q(a.b);
   if (threadIdx.x == 0) {
     topu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, N, N, true));
-    topv = i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, N, N, true));
+    topv = two ? i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, N, N, true)) : 0.0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < span; t += blockDim.x) {
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     int xu = 0, xv = 0;
     if (p < N) {
       xu = balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, p, N, true);
-      xv = balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true);
+      if (two) xv = balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true);
     }
     du[t] = xu;
     dv[t] = xv;
@@ -343,20 +345,23 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
         sv = fma(g, fv[t + halo - r], sv);
       }
       a.X[j] = su;
-      a.X[N + j] = sv;
+      if (two) a.X[N + j] = sv;
     } else {
       long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
       for (int r = 1; r < a.lam; ++r) {
         const long long A = __ldg(a.tab + (long long)(r - 1) * N + (j - r));
         su += (A * du[t + halo - r]) >> (r * a.b);
-        sv += (A * dv[t + halo - r]) >> (r * a.b);
+        if (two) sv += (A * dv[t + halo - r]) >> (r * a.b);
       }
       a.X[j] = scale2(__ll2double_rn(su), -Q);
-      a.X[N + j] = scale2(__ll2double_rn(sv), -Q);
+      if (two) a.X[N + j] = scale2(__ll2double_rn(sv), -Q);
     }
   }
-  // theta: block 0, two threads (u and v), ntheta terms of rho^-j F_(N-j)
-  if (head && (threadIdx.x == 0 || threadIdx.x == 32)) {
+  // theta: block 0, two threads (u and v), ntheta terms of rho^-j F_(N-j); with one
+  // operand theta_V is copied (a kept transform) or equals theta_U (a square)
+  if (head && !two && threadIdx.x == 32) {
+    if (a.theta_v) a.theta[1] = *a.theta_v;
+  } else if (head && (threadIdx.x == 0 || threadIdx.x == 32)) {
     const unsigned long long* src = threadIdx.x == 0 ? a.u : a.v;
     double th = 0.0;
     for (int j = a.ntheta - 1; j >= 0; --j) {
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
       th = fma(__ldg(a.rho_pow + j), f, th);
     }
     a.theta[threadIdx.x == 0 ? 0 : 1] = th;
+    if (!two && !a.theta_v) a.theta[1] = th;
   }
 }
 
@@ -696,44 +702,55 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
 // product of the Convolution step); then the pre-twist of the inverse real
 // FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
 // S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
-__device__ __forceinline__ void twist_pair(const double2* Z, double2* Q, long long M, long long k,
+template <bool SQ>
+__device__ __forceinline__ void twist_pair(const double2* Zu, const double2* Zv, double2* Q,
+                                           long long M, long long k,
                                            const double2* __restrict__ twN, double scale) {
   const long long km = k == 0 ? 0 : M - k;
   const double2 w = __ldg(twN + k);
   double2 Xk[2], Xm[2];
 #pragma unroll
-  for (int o = 0; o < 2; ++o) {
-    const double2 A = Z[o * M + k];
-    const double2 B = cconj(Z[o * M + km]);
+  for (int o = 0; o < (SQ ? 1 : 2); ++o) {
+    const double2* Z = o == 0 ? Zu : Zv;
+    const double2 A = Z[k];
+    const double2 B = cconj(Z[km]);
     const double2 E = cadd(A, B);
     const double2 T = mul_si<-1>(cmul(csub(A, B), w));
     Xk[o] = cadd(E, T);
     Xm[o] = cconj(csub(E, T));
   }
+  if (SQ) { Xk[1] = Xk[0]; Xm[1] = Xm[0]; }
   const double2 Pk = cmul(Xk[0], Xk[1]);
   const double2 Pm = cmul(Xm[0], Xm[1]);
   const double2 Sm = cadd(Pk, cconj(Pm));
   const double2 Dm = csub(Pk, cconj(Pm));
   const double2 iwD = mul_si<1>(cmulc(Dm, w));          // i conj(w) D
   const double2 qk = cadd(Sm, iwD), qm = cconj(csub(Sm, iwD));
-  // (reads of Z precede the writes, so Q may alias Z's first half)
+  // (reads of Z precede the writes, so Q may alias Zu)
   Q[k] = make_double2(qk.x * scale, qk.y * scale);
   if (k != 0 && km != k) Q[km] = make_double2(qm.x * scale, qm.y * scale);
 }
 
-__global__ void k_twist(const double2* __restrict__ Z, double2* __restrict__ Q, long long M,
+template <bool SQ>
+__global__ void k_twist(const double2* __restrict__ Zu, const double2* __restrict__ Zv,
+                        double2* __restrict__ Q, long long M,
                         const double2* __restrict__ twN, double scale, long long zstride,
                         long long qstride) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k > M / 2) return;
-  twist_pair(Z + blockIdx.y * zstride, Q + blockIdx.y * qstride, M, k, twN, scale);
+  twist_pair<SQ>(Zu + blockIdx.y * zstride, Zv + blockIdx.y * zstride, Q + blockIdx.y * qstride,
+                 M, k, twN, scale);
 }
 
-void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
-                  int batch, long long zstride, long long qstride, cudaStream_t s) {
+void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
+                  const double2* twN, double scale, int batch, long long zstride,
+                  long long qstride, cudaStream_t s) {
   const long long n = M / 2 + 1;
   const dim3 grid(unsigned((n + 255) / 256), unsigned(batch));
-  k_twist<<<grid, 256, 0, s>>>(Z, Q, M, twN, scale, zstride, qstride);
+  if (Zv == Zu)
+    k_twist<true><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, twN, scale, zstride, qstride);
+  else
+    k_twist<false><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, twN, scale, zstride, qstride);
 }
 
 // ------------------------------------------------ back maps and rounding
@@ -1354,7 +1371,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_products(SmallArgs A
     // 3.-5. forward FFTs, twist + pointwise product, inverse FFT (convolution)
     smem_fft<-1>(Z, M, 2, P, tws, tw4s);
     for (int k = tid; k <= M / 2; k += kSmallThreads)
-      twist_pair(Z, Z, M, k, P.twN, 1.0 / (4.0 * double(N)));
+      twist_pair<false>(Z, Z + M, Z, M, k, P.twN, 1.0 / (4.0 * double(N)));
     __syncthreads();
     smem_fft<1>(Z, M, 1, P, tws, tw4s);
     // 6. back map and rounding (convert back)

@@ -67,6 +67,8 @@ struct FwdArgs {
   long long s0;                  // high: (N+1) b - n
   double* X;                     // out: u at X[0..N), v at X[N..2N)
   double* theta;                 // high: theta_U, theta_V
+  int one_operand;               // 1: map u only (v == u, or v's transform is kept)
+  const double* theta_v;         // one_operand: theta_V to copy (nullptr: theta_V = theta_U)
 };
 
 struct BackItem {
@@ -190,9 +192,11 @@ void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s);
 void set_fft_smem_attribute();
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
                      int threads, cudaStream_t s);
-// Z + y zstride -> Q + y qstride for product y < batch
-void launch_twist(const double2* Z, double2* Q, long long M, const double2* twN, double scale,
-                  int batch, long long zstride, long long qstride, cudaStream_t s);
+// Spectra Zu + y zstride (u) and Zv + y zstride (v) -> Q + y qstride for product
+// y < batch. Zv == Zu squares u's spectrum.
+void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
+                  const double2* twN, double scale, int batch, long long zstride,
+                  long long qstride, cudaStream_t s);
 void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s);
 void launch_carry(const CarryArgs& a, int batch, cudaStream_t s);
 

@@ -265,11 +265,11 @@ void radices_of(int L, FftPass* p) {
 }
 
 void shape(FftPass* p, int64_t ctas_wanted) {
-  // sequences per CTA: fill about kPoints points, keeping >= ctas_wanted CTAs;
-  // one butterfly of the largest radix per thread
-  int target = 1024;
-  if (const char* e = std::getenv("TM_FFT_POINTS")) target = std::atoi(e);
-  int C = std::max(1, target / p->L);
+  // sequences per CTA: fill about kPoints points (1024 measured best against 512,
+  // 2048 and 4096 at M = 2^20), keeping >= ctas_wanted CTAs; one radix-4
+  // butterfly per thread
+  constexpr int kPoints = 1024;
+  int C = std::max(1, kPoints / p->L);
   while (C > 1 && (p->Q + C - 1) / C < ctas_wanted) C /= 2;
   C = int(std::min<int64_t>(C, p->Q));
   while (int64_t(C) * p->L > kMaxCL) --C;

@@ -50,10 +50,23 @@ int get_tables(const PlanParams& p, bool single_pass, cudaStream_t s,
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
                long long stride, cudaStream_t s);
 void ensure_kernel_attributes();
-// One whole product on stream s with workspace ws (see api.cu).
+// Forward transform of one operand kept on the device: the spectrum of V~ (complex
+// length M, the order the forward FFT leaves it in) and theta_V (high product).
+struct KeptOperand {
+  const double2* spec;
+  const double* theta;
+};
+// One whole product on stream s with workspace ws (see api.cu). u == v squares
+// (one forward map and one forward FFT); kept != nullptr takes v's transform from
+// it (v is then ignored).
 int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
             cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
-            int64_t* coeff_out, void* const* events);
+            int64_t* coeff_out, void* const* events, const KeptOperand* kept = nullptr);
+// Split, forward map and forward FFT of v alone into spec (M complex) and theta (2
+// doubles), through workspace ws.
+int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
+                      const PlanParams& p, const PlanEntry& pe, Workspace& ws, double2* spec,
+                      double* theta);
 // Single-pass plan tables of a CTA-resident product, and its per-product item.
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe);
 int read_status(cudaStream_t s, DevStatus* status, tm_report* rep);

@@ -78,5 +78,17 @@ def test_host_side_errors(pkg):
     # null operands are rejected before any CUDA call
     assert lib.tm_mul(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_lo(None, None, None, 0, None, None) == pkg.TM_EINVAL
+    # kept operands: argument checks precede any CUDA call
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.tm_operand_create(1, 100, None, None, ctypes.byref(h)) == pkg.TM_EINVAL
+    assert lib.tm_operand_create(1, 100, fake, None, None) == pkg.TM_EINVAL
+    assert lib.tm_operand_create(7, 100, fake, None, ctypes.byref(h)) == pkg.TM_EINVAL
+    assert lib.tm_operand_create(1, 0, fake, None, ctypes.byref(h)) == pkg.TM_EINVAL
+    assert lib.tm_operand_create(2, (1 << 31) + 1, fake, None, ctypes.byref(h)) == pkg.TM_ERANGE
+    assert not h.value                                   # no handle on error
+    assert lib.tm_mul_operand(None, fake, fake, None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_operand(fake, fake, None, None, None) == pkg.TM_EINVAL
+    assert lib.tm_operand_destroy(None) == pkg.TM_OK
     for code in (0, -1, -2, -3, -4, -5, -6, -7, 99):
         assert pkg.strerror(code)
