@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the square / kept-operand timings")
+    ap.add_argument("--no-division", action="store_true",
+                    help="skip the division timings")
     return ap.parse_args()
 
 
@@ -470,6 +472,37 @@ def run_cuda(args):
         st2 = pkg.stream_status(stream)
         assert st2["rc"] == 0, st2
 
+    # division by a fixed n-bit divisor (Barrett, kept transforms of R and m) and the
+    # Newton reciprocal; per call, L2 flushed before each division
+    division = None
+    if not args.no_division:
+        k = n
+        m_np = workloads.random_limbs(k, 500 + rank)
+        m_np[(k - 1) // 64] |= np.uint64(1 << ((k - 1) % 64))
+        dm = torch.from_numpy(m_np.view(np.int64)).cuda()
+        x_np = workloads.random_limbs(2 * k, 600 + rank)
+        dx = torch.from_numpy(x_np.view(np.int64)).cuda()
+        rts = []
+        for i in range(3):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            R = pkg.reciprocal(dm, k)
+            rts.append(time.perf_counter() - t1)
+        bar = pkg.Barrett(dm, k)
+        assert torch.equal(bar.reciprocal(), R)
+        dq = torch.empty((k + 64) // 64, dtype=torch.int64, device="cuda")
+        dr = torch.empty((k + 63) // 64, dtype=torch.int64, device="cuda")
+        reps = max(5, min(args.steps, 20))
+        div_ms = timed(lambda: bar.divrem(dx, q=dq, r=dr, report=False), reps)
+        _, _, drep = bar.divrem(dx, q=dq, r=dr)
+        assert drep["status"] == 0, drep
+        bar.close()
+        division = {"k_bits": k, "divrem_ms": div_ms, "reciprocal_ms": 1e3 * min(rts),
+                    "note": "x of 2k bits by a fixed k-bit m: one high (n = k+1) and one "
+                            "low (n = k+3) product against kept transforms plus the limb "
+                            "corrections; reciprocal by Newton iteration, host-timed "
+                            "(it waits for the stream)"}
+
     batched = None
     if not args.no_batched:
         batched = run_batched(pkg, torch, np, args.batch_count, max(3, min(args.steps, 10)),
@@ -517,6 +550,7 @@ def run_cuda(args):
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
         "square_and_kept_operand": variants,
+        "division": division,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 2 * nl * 8,

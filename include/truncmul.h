@@ -270,6 +270,46 @@ int tm_mul_operand(uint64_t* out, const uint64_t* u, const tm_operand* v, void* 
 int tm_operand_destroy(tm_operand* op);
 
 /*
+ * Division by a k-bit divisor m (bit k-1 set, 1 <= k <= TM_MAX_BITS - 16), built on
+ * the products above. The paper has no counterpart; its Section 1 names Barrett's
+ * reduction as an application of the high product.
+ *
+ * tm_reciprocal: R = floor((2^(2k) - 1) / m) into R (device, ceil((k+1)/64)
+ * limbs), m device with ceil(k/64) limbs. Newton's iteration for 1/m doubles the
+ * precision h -> H <= 2h - 9 per step with one low product (E = 2^(H+h) - m_H X,
+ * from its low H + 5 bits) and one high product (X E / 2^(2h)); the last step's
+ * approximation is corrected exactly from e = 2^(2k) - 1 - m R (a low product mod
+ * 2^(k+4)). Waits for the stream. Returns TM_OK, TM_EINVAL (NULL pointer, k = 0,
+ * bit k-1 of m clear), TM_ERANGE, TM_ENOMEM, TM_ECUDA, or TM_EPRECISION (a product
+ * on the stream failed its bound, or the final range check did not hold).
+ *
+ * tm_barrett_create: R = tm_reciprocal(m), plus kept transforms (tm_operand) of R
+ * for high products of n = k + 1 bits and of m for low products of n = k + 3 bits,
+ * plus scratch; about 40 k / 8 bytes of device memory. Waits for the stream. m
+ * is read during the call only.
+ * tm_barrett_divrem: q = floor(x / m) (ceil((k+1)/64) limbs) and r = x mod m
+ * (ceil(k/64) limbs) for 0 <= x < 2^(2k) (ceil(2k/64) limbs; bits >= 2k ignored);
+ * either output may be NULL, not both; outputs must not overlap x. Barrett's
+ * quotient: x1 = floor(x / 2^(k-1)), q^ = the high product of x1 and R (n = k + 1),
+ * so q - 3 <= q^ <= q + 1; r^ = x - q^ m from x and the low product of q^ and m
+ * (n = k + 3), then at most one addition and three subtractions of m, taken on
+ * the device by sign tests. Enqueued on `stream`; rep as for tm_mul: the high
+ * product's plan, e_max the larger bound of the two products and margin the
+ * largest rounding distance of both (with rep, TM_EPRECISION also reports a
+ * failed final range check 0 <= r < m). Calls on one
+ * context share its scratch: order them on one stream.
+ * tm_barrett_reciprocal: copies R (ceil((k+1)/64) limbs, device) on `stream`.
+ * tm_barrett_destroy: waits for the device, then frees the context.
+ */
+typedef struct tm_barrett tm_barrett;
+int tm_reciprocal(uint64_t* R, const uint64_t* m, uint64_t k_bits, void* stream);
+int tm_barrett_create(const uint64_t* m, uint64_t k_bits, void* stream, tm_barrett** out);
+int tm_barrett_divrem(tm_barrett* b, uint64_t* q, uint64_t* r, const uint64_t* x, void* stream,
+                      tm_report* rep);
+int tm_barrett_reciprocal(const tm_barrett* b, uint64_t* R, void* stream);
+int tm_barrett_destroy(tm_barrett* b);
+
+/*
  * tm_coeffs: the rounded coefficients c_i of one product (device pointers),
  * for checking the method stage by stage:
  *   low:  c_i = round(2^b Wbar_i) = 2^b L_i, i < N       (Algorithm 2,

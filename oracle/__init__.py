@@ -21,6 +21,9 @@ Contents (each function cites the passage of the paper it follows):
 - ``fp64_ref`` Algorithms 1-3 step by step in numpy float64, with numpy's FFT as
                the Convolution black box (Section 2.1).
 - ``plan``     the oracle's own choice of (b, N, lambda) from the FP64 error bound.
+- ``division`` the reciprocal floor((2^(2k) - 1) / m) and floor division by
+               definition, plus binary long division as a cross-check (Section 1
+               names Barrett's reduction as an application of the high product).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py``; none is "parity unpinned".

@@ -55,7 +55,9 @@ EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
-           "tm_operand_create", "tm_mul_operand", "tm_operand_destroy", "tm_coeffs",
+           "tm_operand_create", "tm_mul_operand", "tm_operand_destroy", "tm_reciprocal",
+           "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
+           "tm_barrett_destroy", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
 
 _lib = None
@@ -106,7 +108,14 @@ def load(path: str = None):
                                       ctypes.POINTER(ctypes.c_void_p)]
     lib.tm_mul_operand.argtypes = [P, P, P, P, R]
     lib.tm_operand_destroy.argtypes = [P]
-    for name in ("tm_operand_create", "tm_mul_operand", "tm_operand_destroy"):
+    lib.tm_reciprocal.argtypes = [P, P, ctypes.c_uint64, P]
+    lib.tm_barrett_create.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.tm_barrett_divrem.argtypes = [P, P, P, P, P, R]
+    lib.tm_barrett_reciprocal.argtypes = [P, P, P]
+    lib.tm_barrett_destroy.argtypes = [P]
+    for name in ("tm_operand_create", "tm_mul_operand", "tm_operand_destroy", "tm_reciprocal",
+                 "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
+                 "tm_barrett_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     lib.tm_stream_status.argtypes = [P, R]
     lib.tm_release.argtypes = []
@@ -293,6 +302,67 @@ class Operand:
     def close(self):
         if self._h:
             load().tm_operand_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reciprocal(m, k_bits: int, out=None, stream=None):
+    """tm_reciprocal: floor((2^(2k) - 1) / m) for a k-bit m (bit k-1 set), as a
+    device tensor of ceil((k+1)/64) limbs. Waits for the stream."""
+    import torch
+    if out is None:
+        out = torch.empty((k_bits + 1 + 63) // 64, dtype=torch.int64, device=m.device)
+    rc = load().tm_reciprocal(_ptr(out), _ptr(m), int(k_bits), _stream_ptr(stream))
+    if rc:
+        raise TruncMulError(rc, "tm_reciprocal")
+    return out
+
+
+class Barrett:
+    """tm_barrett: division by a fixed k-bit divisor m (bit k-1 set) with its
+    reciprocal and the kept transforms of the reciprocal and of m."""
+
+    def __init__(self, m, k_bits: int, stream=None):
+        self.k_bits = int(k_bits)
+        self._h = ctypes.c_void_p()
+        rc = load().tm_barrett_create(_ptr(m), self.k_bits, _stream_ptr(stream),
+                                      ctypes.byref(self._h))
+        if rc:
+            self._h = None
+            raise TruncMulError(rc, "tm_barrett_create")
+
+    def divrem(self, x, q=None, r=None, stream=None, report: bool = True, want=("q", "r")):
+        """q = floor(x / m), r = x mod m for x < 2^(2k) (ceil(2k/64) limbs).
+        Returns (q or None, r or None, report dict or None)."""
+        import torch
+        k = self.k_bits
+        if q is None and "q" in want:
+            q = torch.empty((k + 1 + 63) // 64, dtype=torch.int64, device=x.device)
+        if r is None and "r" in want:
+            r = torch.empty((k + 63) // 64, dtype=torch.int64, device=x.device)
+        rep = Report() if report else None
+        rc = load().tm_barrett_divrem(self._h, _ptr(q), _ptr(r), _ptr(x), _stream_ptr(stream),
+                                      ctypes.byref(rep) if rep is not None else None)
+        if rc:
+            raise TruncMulError(rc, "tm_barrett_divrem")
+        return q, r, (rep.as_dict() if rep is not None else None)
+
+    def reciprocal(self, stream=None):
+        import torch
+        out = torch.empty((self.k_bits + 1 + 63) // 64, dtype=torch.int64, device="cuda")
+        rc = load().tm_barrett_reciprocal(self._h, _ptr(out), _stream_ptr(stream))
+        if rc:
+            raise TruncMulError(rc, "tm_barrett_reciprocal")
+        return out
+
+    def close(self):
+        if self._h:
+            load().tm_barrett_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtruncmul.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["plan.cpp", "kernels.cu", "api.cu", "batch.cu", "server.cu"]
+UNITS = ["plan.cpp", "kernels.cu", "api.cu", "batch.cu", "server.cu", "division.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2"]
 

@@ -90,5 +90,17 @@ def test_host_side_errors(pkg):
     assert lib.tm_mul_operand(None, fake, fake, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_operand(fake, fake, None, None, None) == pkg.TM_EINVAL
     assert lib.tm_operand_destroy(None) == pkg.TM_OK
+    # division: argument checks precede any CUDA call
+    assert lib.tm_reciprocal(None, fake, 100, None) == pkg.TM_EINVAL
+    assert lib.tm_reciprocal(fake, None, 100, None) == pkg.TM_EINVAL
+    assert lib.tm_reciprocal(fake, fake, 0, None) == pkg.TM_EINVAL
+    assert lib.tm_reciprocal(fake, fake, 1 << 31, None) == pkg.TM_ERANGE
+    assert lib.tm_barrett_create(fake, 100, None, None) == pkg.TM_EINVAL
+    assert lib.tm_barrett_create(None, 100, None, ctypes.byref(h)) == pkg.TM_EINVAL
+    assert lib.tm_barrett_create(fake, 0, None, ctypes.byref(h)) == pkg.TM_EINVAL
+    assert not h.value
+    assert lib.tm_barrett_divrem(None, fake, fake, fake, None, None) == pkg.TM_EINVAL
+    assert lib.tm_barrett_reciprocal(None, fake, None) == pkg.TM_EINVAL
+    assert lib.tm_barrett_destroy(None) == pkg.TM_OK
     for code in (0, -1, -2, -3, -4, -5, -6, -7, 99):
         assert pkg.strerror(code)
