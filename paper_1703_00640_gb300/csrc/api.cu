@@ -76,7 +76,8 @@ size_t workspace_bytes(const PlanParams& p) {
 
 // Offsets of every twiddle table of a plan inside one double2 allocation:
 // per pass omega_L (when a stage needs it), omega_Mp, the radix-4 tangent
-// tables; then omega_N^k, k <= M/2, for the real-FFT twist. Returns the count.
+// tables; then the twist coefficients (1 + omega_N^(2k)) / (2N), k <= M/2.
+// Returns the count.
 size_t layout_twiddles(PlanEntry* e) {
   size_t cnt = 0;
   for (int i = 0; i < e->fft.npass; ++i) {
@@ -102,7 +103,7 @@ size_t layout_twiddles(PlanEntry* e) {
     fp.tw4_len = len4;
     cnt += 2 * size_t(len4);
   }
-  e->twN_off = cnt;
+  e->twc_off = cnt;
   cnt += size_t(e->M / 2 + 1);
   return cnt;
 }
@@ -119,7 +120,7 @@ void init_twiddles(const PlanEntry& e, cudaStream_t s) {
       Ns *= fp.radix[st];
     }
   }
-  launch_init_twiddles(e.tw + e.twN_off, e.p.N, e.M / 2 + 1, s);
+  launch_init_twist_coef(e.tw + e.twc_off, e.p.N, e.M / 2 + 1, s);
 }
 
 namespace {
@@ -406,8 +407,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   // 3. real-FFT twist, pointwise product, inverse pre-twist
   const double2* Zu = bufs[cur];
   const double2* Zv = kept ? kept->spec : (square ? Zu : Zu + M);
-  launch_twist(Zu, Zv, bufs[cur ^ 1], M, pe.tw + pe.twN_off, 1.0 / (4.0 * double(N)), 1, 0, 0,
-               s);
+  launch_twist(Zu, Zv, bufs[cur ^ 1], M, pe.tw + pe.twc_off, N, 1, 0, 0, s);
   cur ^= 1;
   mark(3);
   // 4. inverse FFT (batch 1)

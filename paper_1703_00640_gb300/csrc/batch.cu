@@ -96,8 +96,8 @@ int enqueue_group(tm_batch* B, const Group& g, cudaStream_t s) {
   launch_fwd(kind, fa, cnt, s);
   double2* bufs[2] = {R0, R1};
   int cur = launch_fft(pe, bufs, 0, -1, 2 * cnt, M, s);
-  launch_twist(bufs[cur], bufs[cur] + M, bufs[cur ^ 1], M, pe.tw + pe.twN_off,
-               1.0 / (4.0 * double(N)), cnt, 2 * M, 2 * M, s);
+  launch_twist(bufs[cur], bufs[cur] + M, bufs[cur ^ 1], M, pe.tw + pe.twc_off, N, cnt, 2 * M,
+               2 * M, s);
   cur ^= 1;
   cur = launch_fft(pe, bufs, cur, 1, cnt, 2 * M, s);
   if (cur != 1) return TM_EINVAL;       // the item layout assumes the output in R1
@@ -220,7 +220,7 @@ SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
   sp.need_wL = fp.need_wL ? 1 : 0;
   sp.tw_sub = pe.tw + fp.tw_sub;
   sp.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
-  sp.twN = pe.tw + pe.twN_off;
+  sp.twc = pe.tw + pe.twc_off;
   sp.fwd_tab = pe.fwd_tab;
   sp.bwd_tab = pe.bwd_tab;
   sp.bwd_tab2 = p.kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;

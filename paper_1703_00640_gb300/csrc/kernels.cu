@@ -94,12 +94,9 @@ __device__ __forceinline__ long long round_dist(double x, unsigned long long* di
 
 // -------------------------------------------------------- table kernels
 
-// tab[m] = exp(-2 pi i m / len), m < count. The angle is reduced to the first
-// half-quadrant with integer arithmetic, then sincospi of an argument in
-// [0, 1/4].
-__global__ void k_init_twiddles(double2* tab, long long len, long long count) {
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (m >= count) return;
+// cos and sin of 2 pi m / len. The angle is reduced to the first half-quadrant
+// with integer arithmetic, then sincospi of an argument in [0, 1/4].
+__device__ void cossin_2pi(long long m, long long len, double* cs, double* sn) {
   const long long m4 = 4 * m;
   const long long q = m4 / len;              // quadrant 0..3
   long long r = m4 - q * len;                // angle = pi/2 (q + r/len)
@@ -108,14 +105,31 @@ __global__ void k_init_twiddles(double2* tab, long long len, long long count) {
   double s, c;
   sincospi((double)r / (2.0 * (double)len), &s, &c);   // angle pi r / (2 len)
   if (swap) { const double t = s; s = c; c = t; }
-  double cs, sn;                               // cos, sin of 2 pi m / len
   switch (q) {
-    case 0: cs = c; sn = s; break;
-    case 1: cs = -s; sn = c; break;
-    case 2: cs = -c; sn = -s; break;
-    default: cs = s; sn = -c; break;
+    case 0: *cs = c; *sn = s; break;
+    case 1: *cs = -s; *sn = c; break;
+    case 2: *cs = -c; *sn = -s; break;
+    default: *cs = s; *sn = -c; break;
   }
+}
+
+// tab[m] = exp(-2 pi i m / len), m < count.
+__global__ void k_init_twiddles(double2* tab, long long len, long long count) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  double cs, sn;
+  cossin_2pi(m, len, &cs, &sn);
   tab[m] = make_double2(cs, -sn);
+}
+
+// tab[k] = (1 + w^2) / (2N) = cos(2 pi k / N) w / N, w = exp(-2 pi i k / N), k < count:
+// the one twiddle of the fused real-FFT twist (see twist_pair).
+__global__ void k_init_twist_coef(double2* tab, long long N, long long count) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  double cs, sn;
+  cossin_2pi(k, N, &cs, &sn);
+  tab[k] = make_double2(cs * cs / (double)N, -(cs * sn) / (double)N);
 }
 
 // Tangent-form twiddles of a radix-4 stage (see launch_init_tw4).
@@ -220,9 +234,93 @@ __device__ __forceinline__ int balanced_digit(const unsigned long long* limbs, l
 
 // ----------------------------------------------------- forward maps
 
+// Launches KERNEL<ROWS> with ROWS = rows for the map row counts the planner
+// produces (3..12 for b = 5..14), else KERNEL<0> (any count up to kMaxLam).
+#define TM_LAUNCH_ROWS(R, KERNEL, CFG, ARGS) \
+  case R: KERNEL<R><<<TM_UNPAREN CFG>>>(TM_UNPAREN ARGS); break;
+#define TM_UNPAREN(...) __VA_ARGS__
+#define TM_ROWS_DISPATCH(rows, KERNEL, CFG, ARGS)                                     \
+  switch (rows) {                                                                    \
+    TM_LAUNCH_ROWS(3, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(4, KERNEL, CFG, ARGS)        \
+    TM_LAUNCH_ROWS(5, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(6, KERNEL, CFG, ARGS)        \
+    TM_LAUNCH_ROWS(7, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(8, KERNEL, CFG, ARGS)        \
+    TM_LAUNCH_ROWS(9, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(10, KERNEL, CFG, ARGS)       \
+    TM_LAUNCH_ROWS(11, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(12, KERNEL, CFG, ARGS)      \
+    default: KERNEL<0><<<TM_UNPAREN CFG>>>(TM_UNPAREN ARGS); break;                  \
+  }
+
 constexpr int kFwdTile = 1024;
 constexpr int kFwdThreads = 256;
 constexpr int kMaxLam = 24;
+constexpr int kMaxB = 24;
+// limbs holding the bits of one tile's digits (plus the carry bit below them)
+constexpr int kStageLimbs = ((kFwdTile + kMaxLam) * kMaxB + 64) / 64 + 4;
+
+// Limbs of x = u 2^shift staged in shared memory for the digits p in [p_lo, p_hi):
+// st[i] = limb w0 + i of u (bits at and above n cleared, zero outside the limbs).
+struct DigitStage {
+  long long w0;
+  bool ok;            // false: the range did not fit; digits come from get_bits
+};
+
+__device__ DigitStage stage_digits(unsigned long long* st, const unsigned long long* limbs,
+                                   long long nlimbs, unsigned long long n, long long shift,
+                                   int b, long long p_lo, long long p_hi) {
+  DigitStage g{0, true};
+  if (p_hi <= p_lo) return g;
+  const long long ulo = p_lo * b - 1 - shift, uhi = p_hi * b - shift;   // bits of u
+  g.w0 = ulo >= 0 ? ulo / 64 : -((-ulo + 63) / 64);
+  const long long cnt = (uhi - 1 - 64 * g.w0) / 64 + 2;
+  if (cnt > kStageLimbs) {
+    g.ok = false;
+    return g;
+  }
+  for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const long long w = g.w0 + t;
+    unsigned long long x = 0;
+    if (w >= 0 && w < nlimbs && (unsigned long long)(64 * w) < n) {
+      x = __ldg(limbs + w);
+      const unsigned long long rem = n - (unsigned long long)(64 * w);
+      if (rem < 64) x &= (1ull << rem) - 1ull;
+    }
+    st[t] = x;
+  }
+  return g;
+}
+
+// cnt <= 32 bits of the staged limbs from local bit lb
+__device__ __forceinline__ unsigned stage_bits(const unsigned long long* st, long long lb,
+                                               int cnt) {
+  const long long w = lb >> 6;
+  const int off = int(lb & 63);
+  const unsigned long long x = (st[w] >> off) | ((st[w + 1] << 1) << (63 - off));
+  return unsigned(x & ((1ull << cnt) - 1ull));
+}
+
+// Balanced digits d[t] of positions p = j0 - halo + t (cyclic mod N), t < span, of
+// x = u 2^shift: positions below `limit` get the digit of Section 5, the others 0.
+// Staged limbs serve positions p >= 0; wrapped positions (first tile) use get_bits.
+__device__ void fill_digits(int* d, const unsigned long long* st, DigitStage g,
+                            const unsigned long long* limbs, long long nlimbs,
+                            unsigned long long n, long long shift, int b, long long N,
+                            long long limit, long long top, bool top_unbalanced, long long j0,
+                            int halo, int span) {
+  const unsigned half = 1u << (b - 1);
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    long long p = j0 - halo + t;
+    int x = 0;
+    if (p < 0 || !g.ok) {
+      if (p < 0) p += N;
+      if (p < limit) x = balanced_digit(limbs, nlimbs, n, shift, b, p, top, top_unbalanced);
+    } else if (p < limit) {
+      const long long lb = p * b - shift - 64 * g.w0;
+      const unsigned dp = stage_bits(st, lb, b);
+      const int c = p > 0 ? int(stage_bits(st, lb - 1, 1)) : 0;
+      x = int(dp) - (dp >= half ? (1 << b) : 0) + c;
+    }
+    d[t] = x;
+  }
+}
 
 // Low product: U~ = sum_{r<lam} alpha*_r U (Algorithm 2, convert step; Proposition 3.15),
 // U~_j = U_j + sum_{r=1}^{lam-1} alpha_{(j-r) mod N, r} U_{(j-r) mod N}, evaluated in
@@ -230,6 +328,7 @@ constexpr int kMaxLam = 24;
 // S_j = U_j 2^Q + sum_r (A_{k,r} U_k) >> rb is exact up to the table rounding and
 // the shifts, |S_j| < 2^61, and U~_j = S_j 2^-Q after one rounding conversion.
 // Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1, split step).
+template <int ROWS>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kind) {
   FwdArgs a = a0;
   if (a0.items) {
@@ -238,20 +337,24 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
     a.X = it.X; a.theta = it.theta;
   }
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
   const bool two = !a.one_operand;
   const long long j0 = (long long)blockIdx.x * kFwdTile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
   const int span = kFwdTile + halo;
-  for (int t = threadIdx.x; t < span; t += blockDim.x) {
-    long long p = j0 - halo + t;                 // digit position, cyclic mod N
-    if (p < 0) p += a.N;
-    int xu = 0, xv = 0;
-    if (p < a.N && p < a.nd) {
-      xu = balanced_digit(a.u, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
-      if (two) xv = balanced_digit(a.v, a.nlimbs, a.n, 0, a.b, p, a.nd - 1, false);
-    }
-    du[t] = xu;
-    dv[t] = xv;
+  const long long limit = a.N < a.nd ? a.N : a.nd;
+  {
+    const long long p_lo = j0 - halo > 0 ? j0 - halo : 0;
+    const long long p_hi = j0 + kFwdTile < limit ? j0 + kFwdTile : limit;
+    const DigitStage gu = stage_digits(stu, a.u, a.nlimbs, a.n, 0, a.b, p_lo, p_hi);
+    DigitStage gv{0, true};
+    if (two) gv = stage_digits(stv, a.v, a.nlimbs, a.n, 0, a.b, p_lo, p_hi);
+    __syncthreads();
+    fill_digits(du, stu, gu, a.u, a.nlimbs, a.n, 0, a.b, a.N, limit, a.nd - 1, false, j0, halo,
+                span);
+    if (two)
+      fill_digits(dv, stv, gv, a.v, a.nlimbs, a.n, 0, a.b, a.N, limit, a.nd - 1, false, j0,
+                  halo, span);
   }
   __syncthreads();
   const int Q = fx_q(a.b);
@@ -264,12 +367,28 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
       continue;
     }
     long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
-    for (int r = 1; r < a.lam; ++r) {
-      long long k = j - r;
-      if (k < 0) k += a.N;
-      const long long A = __ldg(a.tab + (long long)(r - 1) * a.N + k);
-      su += (A * du[t + halo - r]) >> (r * a.b);
-      if (two) sv += (A * dv[t + halo - r]) >> (r * a.b);
+    if (j >= halo) {                 // no wrap: row r, index j - r; loads first
+      const long long* tp = a.tab + (j - 1);
+      constexpr int RM = ROWS > 0 ? ROWS : kMaxLam;
+      long long A[RM + 1];
+#pragma unroll
+      for (int r = 1; r <= RM; ++r)
+        A[r] = (ROWS > 0 || r < a.lam) ? __ldg(tp + (long long)(r - 1) * (a.N - 1)) : 0;
+#pragma unroll
+      for (int r = 1; r <= RM; ++r) {
+        if (ROWS > 0 || r < a.lam) {
+          su += (A[r] * du[t + halo - r]) >> (r * a.b);
+          if (two) sv += (A[r] * dv[t + halo - r]) >> (r * a.b);
+        }
+      }
+    } else {
+      for (int r = 1; r < a.lam; ++r) {
+        long long k = j - r;
+        if (k < 0) k += a.N;
+        const long long A = __ldg(a.tab + (long long)(r - 1) * a.N + k);
+        su += (A * du[t + halo - r]) >> (r * a.b);
+        if (two) sv += (A * dv[t + halo - r]) >> (r * a.b);
+      }
     }
     a.X[j] = scale2(__ll2double_rn(su), -Q);
     if (two) a.X[a.N + j] = scale2(__ll2double_rn(sv), -Q);
@@ -288,6 +407,7 @@ __device__ __forceinline__ double fx_coef(const long long* tab, long long N, int
   return scale2(__ll2double_rn(__ldg(tab + (long long)(r - 1) * N + k)), -(Q + r * b));
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
   FwdArgs a = a0;
   if (a0.items) {
@@ -297,6 +417,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
   }
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
+  __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
   __shared__ double topu, topv;
   const bool two = !a.one_operand;
   const long long j0 = (long long)blockIdx.x * kFwdTile;
@@ -309,19 +430,24 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     topu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, N, N, true));
     topv = two ? i2d_exact(balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, N, N, true)) : 0.0;
   }
+  {
+    const long long p_lo = j0 - halo > 0 ? j0 - halo : 0;
+    const long long p_hi = j0 + kFwdTile < N ? j0 + kFwdTile : N;
+    const DigitStage gu = stage_digits(stu, a.u, a.nlimbs, a.n, a.s0, a.b, p_lo, p_hi);
+    DigitStage gv{0, true};
+    if (two) gv = stage_digits(stv, a.v, a.nlimbs, a.n, a.s0, a.b, p_lo, p_hi);
+    __syncthreads();
+    fill_digits(du, stu, gu, a.u, a.nlimbs, a.n, a.s0, a.b, N, N, N, true, j0, halo, span);
+    if (two) fill_digits(dv, stv, gv, a.v, a.nlimbs, a.n, a.s0, a.b, N, N, N, true, j0, halo, span);
+    else
+      for (int t = threadIdx.x; t < span; t += blockDim.x) dv[t] = 0;
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < span; t += blockDim.x) {
-    long long p = j0 - halo + t;
-    if (p < 0) p += N;
-    int xu = 0, xv = 0;
-    if (p < N) {
-      xu = balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, p, N, true);
-      if (two) xv = balanced_digit(a.v, a.nlimbs, a.n, a.s0, a.b, p, N, true);
-    }
-    du[t] = xu;
-    dv[t] = xv;
-    if (head) {
-      double yu = i2d_exact(xu), yv = i2d_exact(xv);
+  if (head) {
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+      long long p = j0 - halo + t;
+      if (p < 0) p += N;
+      double yu = i2d_exact(du[t]), yv = i2d_exact(dv[t]);
       if (p < a.nkappa) {
         const double kp = __ldg(a.kappa + p);
         yu = fma(kp, topu, yu);
@@ -330,8 +456,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
       fu[t] = yu;
       fv[t] = yv;
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= N) break;
@@ -348,10 +474,18 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
       if (two) a.X[N + j] = sv;
     } else {
       long long su = (long long)du[t + halo] << Q, sv = (long long)dv[t + halo] << Q;
-      for (int r = 1; r < a.lam; ++r) {
-        const long long A = __ldg(a.tab + (long long)(r - 1) * N + (j - r));
-        su += (A * du[t + halo - r]) >> (r * a.b);
-        if (two) sv += (A * dv[t + halo - r]) >> (r * a.b);
+      const long long* tp = a.tab + (j - 1);
+      constexpr int RM = ROWS > 0 ? ROWS : kMaxLam;
+      long long A[RM + 1];
+#pragma unroll
+      for (int r = 1; r <= RM; ++r)
+        A[r] = (ROWS > 0 || r < a.lam) ? __ldg(tp + (long long)(r - 1) * (N - 1)) : 0;
+#pragma unroll
+      for (int r = 1; r <= RM; ++r) {
+        if (ROWS > 0 || r < a.lam) {
+          su += (A[r] * du[t + halo - r]) >> (r * a.b);
+          if (two) sv += (A[r] * dv[t + halo - r]) >> (r * a.b);
+        }
       }
       a.X[j] = scale2(__ll2double_rn(su), -Q);
       if (two) a.X[N + j] = scale2(__ll2double_rn(sv), -Q);
@@ -377,10 +511,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
 
 void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s) {
   const dim3 grid(unsigned((a.N + kFwdTile - 1) / kFwdTile), unsigned(batch));
-  if (kind == TM_HI)
-    k_fwd_hi<<<grid, kFwdThreads, 0, s>>>(a);
-  else
-    k_fwd_lo_full<<<grid, kFwdThreads, 0, s>>>(a, kind);
+  const int rows = a.lam - 1;                    // map rows r = 1..lam-1
+  if (kind == TM_HI) {
+    TM_ROWS_DISPATCH(rows, k_fwd_hi, (grid, kFwdThreads, 0, s), (a));
+  } else {
+    TM_ROWS_DISPATCH(rows, k_fwd_lo_full, (grid, kFwdThreads, 0, s), (a, kind));
+  }
 }
 
 // ------------------------------------------------------------ FFT pass
@@ -702,55 +838,64 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
 // product of the Convolution step); then the pre-twist of the inverse real
 // FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
 // S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
+// Real-FFT twist, pointwise product and inverse pre-twist in one step, for the
+// pair (k, M-k) of the half-length spectra Z (u) and Z' (v) (Z = DFT_M of the
+// real input packed as x_2j + i x_2j+1). With A = Z_k, B = conj(Z_(M-k)),
+// D = A - B and w = omega_N^k, the real input's spectrum is (A + B - i w D) / 2 at
+// k and conj(A + B + i w D) / 2 at M - k; multiplying the two inputs' spectra and
+// packing the product back into a half-length spectrum (scaled by 1/N for the
+// inverse transform) reduces, with |w| = 1, to
+//   Q_k     = (2/N) A A' - c_k D D',
+//   Q_(M-k) = conj((2/N) B B' - c_k D D'),   c_k = (1 + w^2) / (2N),
+// 24 FP64 instructions per pair (a square: A' = A, B' = B, D' = D).
 template <bool SQ>
 __device__ __forceinline__ void twist_pair(const double2* Zu, const double2* Zv, double2* Q,
                                            long long M, long long k,
-                                           const double2* __restrict__ twN, double scale) {
+                                           const double2* __restrict__ tc, double two_over_N) {
   const long long km = k == 0 ? 0 : M - k;
-  const double2 w = __ldg(twN + k);
-  double2 Xk[2], Xm[2];
-#pragma unroll
-  for (int o = 0; o < (SQ ? 1 : 2); ++o) {
-    const double2* Z = o == 0 ? Zu : Zv;
-    const double2 A = Z[k];
-    const double2 B = cconj(Z[km]);
-    const double2 E = cadd(A, B);
-    const double2 T = mul_si<-1>(cmul(csub(A, B), w));
-    Xk[o] = cadd(E, T);
-    Xm[o] = cconj(csub(E, T));
+  const double2 c = __ldg(tc + k);
+  const double2 A0 = Zu[k], B0 = cconj(Zu[km]);
+  const double2 D0 = csub(A0, B0);
+  double2 AA, BB, DD;
+  if (SQ) {
+    AA = cmul(A0, A0);
+    BB = cmul(B0, B0);
+    DD = cmul(D0, D0);
+  } else {
+    const double2 A1 = Zv[k], B1 = cconj(Zv[km]);
+    const double2 D1 = csub(A1, B1);
+    AA = cmul(A0, A1);
+    BB = cmul(B0, B1);
+    DD = cmul(D0, D1);
   }
-  if (SQ) { Xk[1] = Xk[0]; Xm[1] = Xm[0]; }
-  const double2 Pk = cmul(Xk[0], Xk[1]);
-  const double2 Pm = cmul(Xm[0], Xm[1]);
-  const double2 Sm = cadd(Pk, cconj(Pm));
-  const double2 Dm = csub(Pk, cconj(Pm));
-  const double2 iwD = mul_si<1>(cmulc(Dm, w));          // i conj(w) D
-  const double2 qk = cadd(Sm, iwD), qm = cconj(csub(Sm, iwD));
+  const double2 H = cmul(DD, c);
   // (reads of Z precede the writes, so Q may alias Zu)
-  Q[k] = make_double2(qk.x * scale, qk.y * scale);
-  if (k != 0 && km != k) Q[km] = make_double2(qm.x * scale, qm.y * scale);
+  Q[k] = make_double2(fma(two_over_N, AA.x, -H.x), fma(two_over_N, AA.y, -H.y));
+  if (k != 0 && km != k)
+    Q[km] = make_double2(fma(two_over_N, BB.x, -H.x), fma(-two_over_N, BB.y, H.y));
 }
 
 template <bool SQ>
 __global__ void k_twist(const double2* __restrict__ Zu, const double2* __restrict__ Zv,
                         double2* __restrict__ Q, long long M,
-                        const double2* __restrict__ twN, double scale, long long zstride,
+                        const double2* __restrict__ tc, double two_over_N, long long zstride,
                         long long qstride) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k > M / 2) return;
   twist_pair<SQ>(Zu + blockIdx.y * zstride, Zv + blockIdx.y * zstride, Q + blockIdx.y * qstride,
-                 M, k, twN, scale);
+                 M, k, tc, two_over_N);
 }
 
 void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
-                  const double2* twN, double scale, int batch, long long zstride,
+                  const double2* tc, long long N, int batch, long long zstride,
                   long long qstride, cudaStream_t s) {
   const long long n = M / 2 + 1;
   const dim3 grid(unsigned((n + 255) / 256), unsigned(batch));
+  const double two_over_N = 2.0 / double(N);
   if (Zv == Zu)
-    k_twist<true><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, twN, scale, zstride, qstride);
+    k_twist<true><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, tc, two_over_N, zstride, qstride);
   else
-    k_twist<false><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, twN, scale, zstride, qstride);
+    k_twist<false><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, tc, two_over_N, zstride, qstride);
 }
 
 // ------------------------------------------------ back maps and rounding
@@ -841,6 +986,24 @@ __device__ void back_lo_loop(const BackArgs& a, long long start, long long strid
   }
 }
 
+// Largest rounding distance of the block (every thread passes its own maximum).
+__device__ __forceinline__ void block_note_distance(unsigned long long d,
+                                                    unsigned long long* bmax) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long e = __shfl_xor_sync(~0u, d, o);
+    d = e > d ? e : d;
+  }
+  if ((threadIdx.x & 31) == 0 && d) atomicMax(bmax, d);
+}
+
+constexpr int kBackTile = 1024;
+
+// Tiles of kBackTile coefficients; every thread issues the loads of all map rows
+// and W~ values of an output before the FMAs, unrolled for ROWS = lam - 1 rows
+// (ROWS = 0: any count up to kMaxLam, predicated). Head positions i < lam (block 0)
+// take back_lo_loop's path with the wrapped terms.
+template <int ROWS>
 __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
   BackArgs a = a0;
   if (a0.items) {
@@ -849,10 +1012,36 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
   }
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
+  const long long N = a.N;
+  const long long i0 = (long long)blockIdx.x * kBackTile;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
-  back_lo_loop(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-               (long long)gridDim.x * blockDim.x, &bmax, &bflags);
+  unsigned long long dmax = 0;
+  for (int t = threadIdx.x; t < kBackTile; t += blockDim.x) {
+    const long long i = i0 + t;
+    if (i >= N) break;
+    if (i < a.lam) {
+      back_lo_loop(a, i, N, &bmax, &bflags);       // this one position
+      continue;
+    }
+    constexpr int RM = ROWS > 0 ? ROWS : kMaxLam;
+    double B[RM + 1], W[RM + 1];
+    const double* tp = a.tab + (i - 1);            // row r, index i - r
+#pragma unroll
+    for (int r = 1; r <= RM; ++r) {
+      const bool on = ROWS > 0 || r < a.lam;
+      B[r] = on ? __ldg(tp + (long long)(r - 1) * (N - 1)) : 0.0;
+      W[r] = on ? __ldg(a.w + (i - r)) : 0.0;
+    }
+    double acc = __ldg(a.w + i);
+#pragma unroll
+    for (int r = 1; r <= RM; ++r)
+      if (ROWS > 0 || r < a.lam) acc = fma(B[r], W[r], acc);
+    unsigned long long d;
+    a.c[i] = round_dist(scale2(acc, a.b), &d);
+    dmax = d > dmax ? d : dmax;
+  }
+  block_note_distance(dmax, &bmax);
   finish_block(&bmax, &bflags, a);
 }
 
@@ -933,6 +1122,9 @@ __device__ void back_hi_head(const BackArgs& a, int lane, double* P, double* Hh,
   }
 }
 
+// Tiles as in k_back_lo, ROWS = lam rows of delta'. Head positions and J_N are
+// warp 0 of block 0 (back_hi_head).
+template <int ROWS>
 __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
   BackArgs a = a0;
   if (a0.items) {
@@ -943,10 +1135,34 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
   __shared__ unsigned bflags;
   __shared__ double P[kMaxLam];
   __shared__ double Hh[kMaxLam + 64 + 1];
+  const long long N = a.N;
+  const long long i0 = (long long)blockIdx.x * kBackTile;
+  const long long head = a.lam + a.nkappa;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
-  back_hi_interior(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                   (long long)gridDim.x * blockDim.x, &bmax);
+  unsigned long long dmax = 0;
+  for (int t = threadIdx.x; t < kBackTile; t += blockDim.x) {
+    const long long i = i0 + t;
+    if (i >= N) break;
+    if (i < head) continue;
+    constexpr int RM = ROWS > 0 ? ROWS : kMaxLam;
+    double D[RM + 1], W[RM + 1];
+    const double* tp = a.tab + (i - 1);
+#pragma unroll
+    for (int r = 1; r <= RM; ++r) {
+      const bool on = ROWS > 0 || r <= a.lam;
+      D[r] = on ? __ldg(tp + (long long)(r - 1) * (N - 1)) : 0.0;
+      W[r] = on ? __ldg(a.w + (i - r)) : 0.0;
+    }
+    double acc = __ldg(a.w + i);
+#pragma unroll
+    for (int r = 1; r <= RM; ++r)
+      if (ROWS > 0 || r <= a.lam) acc = fma(D[r], W[r], acc);
+    unsigned long long d;
+    a.c[i] = round_dist(scale2(acc, a.b), &d);
+    dmax = d > dmax ? d : dmax;
+  }
+  block_note_distance(dmax, &bmax);
   if (blockIdx.x == 0 && threadIdx.x < 32) back_hi_head(a, threadIdx.x, P, Hh, &bmax, &bflags);
   finish_block(&bmax, &bflags, a);
 }
@@ -1038,10 +1254,14 @@ void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
     k_back_full<<<grid, kBackThreads, 0, s>>>(a);
   } else if (a.N <= 64 || a.N < 2 * a.lam + a.nkappa + 2) {
     k_back_small<<<dim3(1, unsigned(batch)), 32, 0, s>>>(a, kind);
-  } else if (kind == TM_LO) {
-    k_back_lo<<<grid, kBackThreads, 0, s>>>(a);
   } else {
-    k_back_hi<<<grid, kBackThreads, 0, s>>>(a);
+    const int rows = kind == TM_LO ? a.lam - 1 : a.lam;
+    const dim3 tgrid(unsigned((a.N + kBackTile - 1) / kBackTile), unsigned(batch));
+    if (kind == TM_LO) {
+      TM_ROWS_DISPATCH(rows, k_back_lo, (tgrid, kBackThreads, 0, s), (a));
+    } else {
+      TM_ROWS_DISPATCH(rows, k_back_hi, (tgrid, kBackThreads, 0, s), (a));
+    }
   }
 }
 
@@ -1371,7 +1591,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_products(SmallArgs A
     // 3.-5. forward FFTs, twist + pointwise product, inverse FFT (convolution)
     smem_fft<-1>(Z, M, 2, P, tws, tw4s);
     for (int k = tid; k <= M / 2; k += kSmallThreads)
-      twist_pair<false>(Z, Z + M, Z, M, k, P.twN, 1.0 / (4.0 * double(N)));
+      twist_pair<false>(Z, Z + M, Z, M, k, P.twc, 2.0 / double(N));
     __syncthreads();
     smem_fft<1>(Z, M, 1, P, tws, tw4s);
     // 6. back map and rounding (convert back)
@@ -1458,6 +1678,10 @@ void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ tables
+
+void launch_init_twist_coef(double2* tab, long long N, long long count, cudaStream_t s) {
+  k_init_twist_coef<<<unsigned((count + 255) / 256), 256, 0, s>>>(tab, N, count);
+}
 
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s) {
   if (count <= 0) return;

@@ -143,7 +143,7 @@ struct SmallPlan {
   int tw4_len, need_wL;
   const double2* tw_sub;         // omega_M^k, k < M
   const Tan4* tw4;
-  const double2* twN;            // omega_N^k, k <= M/2
+  const double2* twc;            // twist coefficients (1 + omega_N^(2k)) / (2N), k <= M/2
   const long long* fwd_tab;
   const double* bwd_tab;
   const double* bwd_tab2;
@@ -177,6 +177,8 @@ void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s);
 // table initialisation
 // tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
+// tab[k] = (1 + omega_N^(2k)) / (2N), k < count (coefficients of the fused twist)
+void launch_init_twist_coef(double2* tab, long long N, long long count, cudaStream_t s);
 // Tangent-form twiddles of one radix-4 Stockham stage with Ns > 1: entry k < Ns
 // holds (t1, c1, t2, c2s) with omega_(4Ns)^k = c1 (1 - i t1) and
 // omega_(4Ns)^(2k) = c2 (1 - i t2) when its angle is below pi/2, else
@@ -193,9 +195,10 @@ void set_fft_smem_attribute();
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
                      int threads, cudaStream_t s);
 // Spectra Zu + y zstride (u) and Zv + y zstride (v) -> Q + y qstride for product
-// y < batch. Zv == Zu squares u's spectrum.
+// y < batch (real transform length N, complex length M = N/2, coefficients tc from
+// launch_init_twist_coef). Zv == Zu squares u's spectrum.
 void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
-                  const double2* twN, double scale, int batch, long long zstride,
+                  const double2* tc, long long N, int batch, long long zstride,
                   long long qstride, cudaStream_t s);
 void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s);
 void launch_carry(const CarryArgs& a, int batch, cudaStream_t s);

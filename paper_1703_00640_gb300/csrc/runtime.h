@@ -17,7 +17,7 @@ struct PlanEntry {
   FftPlan fft;
   int64_t M = 0;
   double2* tw = nullptr;       // all twiddle tables
-  size_t twN_off = 0;          // omega_N^k, k <= M/2 (real-FFT twist)
+  size_t twc_off = 0;          // (1 + omega_N^(2k)) / (2N), k <= M/2 (fused twist)
   long long* fwd_tab = nullptr;   // alpha or gamma rows r = 1..lam_fwd-1, fixed point
   double* bwd_tab = nullptr;   // beta rows (low) or delta' rows (high)
   double* bwd_tab2 = nullptr;  // high: delta rows r = 1..lam_bwd-1
