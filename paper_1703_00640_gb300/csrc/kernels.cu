@@ -1333,6 +1333,42 @@ __device__ void block_compose_scan(unsigned* s, int n) {
   }
 }
 
+// Exclusive and total composition of the block's functions in thread order:
+// *ex = f_(t-1) o ... o f_0 (identity for thread 0), *tot = f_last o ... o f_0.
+// NT threads, every thread calls it.
+template <int NT>
+__device__ void block_fn_scan(unsigned f, unsigned* ex, unsigned* tot) {
+  __shared__ unsigned wsum[NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned inc = f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned g = __shfl_up_sync(~0u, inc, o);
+    if (lane >= o) inc = compose(inc, g);
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned w = lane < NT / 32 ? wsum[lane] : kIdentityFn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned g = __shfl_up_sync(~0u, w, o);
+      if (lane >= o) w = compose(w, g);
+    }
+    if (lane < NT / 32) wsum[lane] = w;
+  }
+  __syncthreads();
+  const unsigned prev = __shfl_up_sync(~0u, inc, 1);
+  const unsigned ex_lane = lane ? prev : kIdentityFn;
+  const unsigned before = wid ? wsum[wid - 1] : kIdentityFn;
+  *ex = compose(ex_lane, before);
+  *tot = wsum[NT / 32 - 1];
+  __syncthreads();
+}
+
+// r_L of every limb and the block's composed carry function. Word 2L of r holds
+// r_L mod 2^64; word 2L+1 holds floor(r_L / 2^64) (-1, 0 or 1) in its low byte and
+// the block-exclusive prefix of carry functions in bits 8..13.
 __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
   CarryArgs a = a0;
   if (a0.items) {
@@ -1343,20 +1379,22 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
   }
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   if (blockIdx.x >= my_blocks) return;     // uniform per block
-  __shared__ unsigned fs[kCarryThreads];
+  __shared__ long long hs[kCarryThreads];
   const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
-  unsigned f = kIdentityFn;
-  if (L < a.nS) {
-    const __int128 AL = limb_sum(a, L), Ap = limb_sum(a, L - 1);
-    const __int128 r = (__int128)(unsigned long long)AL + (Ap >> 64);
-    a.r[2 * L] = (unsigned long long)r;
-    a.r[2 * L + 1] = (unsigned long long)(r >> 64);
-    f = carry_fn(r);
-  }
-  fs[threadIdx.x] = f;
+  const __int128 AL = L < a.nS ? limb_sum(a, L) : (__int128)0;
+  hs[threadIdx.x] = (long long)(AL >> 64);
   __syncthreads();
-  block_compose_scan(fs, kCarryThreads);
-  if (threadIdx.x == 0) a.fblock[blockIdx.x] = (unsigned char)fs[kCarryThreads - 1];
+  const long long hp = threadIdx.x ? hs[threadIdx.x - 1] : (long long)(limb_sum(a, L - 1) >> 64);
+  const __int128 r = (__int128)(unsigned long long)AL + hp;
+  const unsigned f = L < a.nS ? carry_fn(r) : kIdentityFn;
+  unsigned ex, tot;
+  block_fn_scan<kCarryThreads>(f, &ex, &tot);
+  if (L < a.nS) {
+    a.r[2 * L] = (unsigned long long)r;
+    a.r[2 * L + 1] = (unsigned long long)((unsigned)(int)(long long)(r >> 64) & 0xFFu) |
+                     ((unsigned long long)ex << 8);
+  }
+  if (threadIdx.x == 0) a.fblock[blockIdx.x] = (unsigned char)tot;
 }
 
 // carry into every block: cin_0 = 0, cin_(B+1) = F_B(cin_B)
@@ -1368,28 +1406,24 @@ __global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
   }
-  const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
-  const long long nblocks = my_blocks;
-  __shared__ unsigned fs[1024];
+  const long long nblocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   const long long per = (nblocks + 1023) / 1024;
   const long long b0 = threadIdx.x * per;
   unsigned f = kIdentityFn;
   for (long long i = b0; i < b0 + per && i < nblocks; ++i) f = compose(a.fblock[i], f);
-  fs[threadIdx.x] = f;
-  __syncthreads();
-  block_compose_scan(fs, 1024);
-  const unsigned before = threadIdx.x ? fs[threadIdx.x - 1] : kIdentityFn;
-  int cin = apply_fn(before, 0);
+  unsigned ex, tot;
+  block_fn_scan<1024>(f, &ex, &tot);
+  int cin = apply_fn(ex, 0);
   for (long long i = b0; i < b0 + per && i < nblocks; ++i) {
     a.cin_block[i] = (unsigned char)(cin + 1);
     cin = apply_fn(a.fblock[i], cin);
   }
 }
 
-__device__ __forceinline__ unsigned long long resolved(const CarryArgs& a, long long L, int cin) {
-  if (L >= a.nS) return 0ull;
-  const __int128 r = (__int128)(((unsigned __int128)a.r[2 * L + 1] << 64) | a.r[2 * L]);
-  return (unsigned long long)(r + cin);
+// r_L + cin mod 2^64 for limb L (0 beyond the resolved limbs)
+__device__ __forceinline__ unsigned long long resolved_lo(const CarryArgs& a, long long L,
+                                                          int cin) {
+  return L < a.nS ? a.r[2 * L] + (unsigned long long)(long long)cin : 0ull;
 }
 
 __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
@@ -1402,30 +1436,21 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
   }
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   if (blockIdx.x >= my_blocks) return;     // uniform per block
-  __shared__ unsigned fs[kCarryThreads];
   const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
-  unsigned f = kIdentityFn;
-  __int128 r = 0;
-  if (L < a.nS) {
-    r = (__int128)(((unsigned __int128)a.r[2 * L + 1] << 64) | a.r[2 * L]);
-    f = carry_fn(r);
-  }
-  fs[threadIdx.x] = f;
-  __syncthreads();
-  block_compose_scan(fs, kCarryThreads);
-  const int cinB = int(a.cin_block[blockIdx.x]) - 1;
-  const unsigned before = threadIdx.x ? fs[threadIdx.x - 1] : kIdentityFn;
-  const int cin = apply_fn(before, cinB);
   if (L >= a.nS) return;
-  const unsigned long long limb = (unsigned long long)(r + cin);
   const long long sw = a.shift_bits >> 6;
   const int sb = int(a.shift_bits & 63);
   const long long j = L - sw;                // output limb whose low part comes from L
   if (j < 0 || j >= a.nout) return;
-  unsigned long long o = limb >> sb;
+  const unsigned long long lo = a.r[2 * L], w1 = a.r[2 * L + 1];
+  const int hi = (int)(signed char)(w1 & 0xFFu);
+  const unsigned pfx = unsigned(w1 >> 8) & 0x3Fu;
+  const int cin = apply_fn(pfx, int(a.cin_block[blockIdx.x]) - 1);
+  unsigned long long o = (lo + (unsigned long long)(long long)cin) >> sb;
   if (sb) {
-    const int cnext = apply_fn(f, cin);
-    o |= resolved(a, L + 1, cnext) << (64 - sb);
+    // carry out of limb L: floor((r_L + cin) / 2^64)
+    const int cnext = hi + ((cin > 0 && lo == ~0ull) ? 1 : 0) - ((cin < 0 && lo == 0ull) ? 1 : 0);
+    o |= resolved_lo(a, L + 1, cnext) << (64 - sb);
   }
   if (j == a.nout - 1) o &= a.top_mask;
   a.out[j] = o;
