@@ -224,6 +224,9 @@ int get_workspace(cudaStream_t s, size_t bytes, Workspace** out) {
   if (!w.status) {
     TM_CHECK(cudaMalloc(&w.status, sizeof(DevStatus)));
     TM_CHECK(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+    TM_CHECK(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+    TM_CHECK(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming));
+    TM_CHECK(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming));
   }
   if (bytes && w.size < bytes) {
     if (w.base) {
@@ -331,7 +334,7 @@ namespace {
 // or of u alone (one_operand), into X.
 void fwd_args(int kind, const uint64_t* u, const uint64_t* v, uint64_t n, const PlanParams& p,
               const PlanEntry& pe, double* X, double* theta, bool one_operand,
-              const double* theta_v, FwdArgs* out) {
+              const double* theta_v, bool square_theta, FwdArgs* out) {
   FwdArgs fa{};
   fa.u = reinterpret_cast<const unsigned long long*>(u);
   fa.v = reinterpret_cast<const unsigned long long*>(v);
@@ -351,6 +354,7 @@ void fwd_args(int kind, const uint64_t* u, const uint64_t* v, uint64_t n, const 
   fa.theta = theta;
   fa.one_operand = one_operand ? 1 : 0;
   fa.theta_v = theta_v;
+  fa.square_theta = square_theta ? 1 : 0;
   *out = fa;
 }
 
@@ -371,7 +375,8 @@ int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
   double2* bufs[2] = {R0, R1};
   bufs[pe.fft.npass & 1] = spec;
   FwdArgs fa;
-  fwd_args(kind, v, v, n, p, pe, reinterpret_cast<double*>(bufs[0]), theta, true, nullptr, &fa);
+  fwd_args(kind, v, v, n, p, pe, reinterpret_cast<double*>(bufs[0]), theta, true, nullptr, true,
+           &fa);
   launch_fwd(kind, fa, 1, s);
   const int cur = launch_fft(pe, bufs, 0, -1, 1, M, s);
   if (bufs[cur] != spec) return TM_ECUDA;   // (cannot happen: npass passes alternate)
@@ -394,15 +399,36 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
   const bool square = !kept && u == v;
   const bool one = square || kept;
-  // 1. digits + forward map (split and convert steps of Algorithms 1-3)
-  FwdArgs fa;
-  fwd_args(kind, u, v, n, p, pe, reinterpret_cast<double*>(R0), theta, one,
-           kept ? kept->theta : nullptr, &fa);
-  launch_fwd(kind, fa, 1, s);
-  mark(1);
-  // 2. forward FFTs of both operands (complex length M, batch 2), or of u alone
   double2* bufs[2] = {R0, R1};
-  int cur = launch_fft(pe, bufs, 0, -1, one ? 1 : 2, M, s);
+  int cur;
+  if (!one && ws.side) {
+    // 1.-2. u's digits, forward map and forward FFT on s; v's on the side stream,
+    // so that each operand's kernels fill the other's idle SMs
+    TM_CHECK(cudaEventRecord(ws.fork, s));
+    TM_CHECK(cudaStreamWaitEvent(ws.side, ws.fork, 0));
+    FwdArgs fu, fv;
+    fwd_args(kind, u, u, n, p, pe, reinterpret_cast<double*>(R0), theta, true, nullptr, false,
+             &fu);
+    fwd_args(kind, v, v, n, p, pe, reinterpret_cast<double*>(R0) + N, theta + 1, true, nullptr,
+             false, &fv);
+    launch_fwd(kind, fu, 1, s);
+    mark(1);
+    launch_fwd(kind, fv, 1, ws.side);
+    double2* bufs_v[2] = {R0 + M, R1 + M};
+    cur = launch_fft(pe, bufs, 0, -1, 1, M, s);
+    launch_fft(pe, bufs_v, 0, -1, 1, M, ws.side);
+    TM_CHECK(cudaEventRecord(ws.join, ws.side));
+    TM_CHECK(cudaStreamWaitEvent(s, ws.join, 0));
+  } else {
+    // 1. digits + forward map (split and convert steps of Algorithms 1-3)
+    FwdArgs fa;
+    fwd_args(kind, u, v, n, p, pe, reinterpret_cast<double*>(R0), theta, one,
+             kept ? kept->theta : nullptr, square, &fa);
+    launch_fwd(kind, fa, 1, s);
+    mark(1);
+    // 2. forward FFTs of both operands (complex length M, batch 2), or of u alone
+    cur = launch_fft(pe, bufs, 0, -1, one ? 1 : 2, M, s);
+  }
   mark(2);
   // 3. real-FFT twist, pointwise product, inverse pre-twist
   const double2* Zu = bufs[cur];
@@ -829,6 +855,9 @@ int tm_release(void) {
       cudaFree(it->second.base);
       cudaFree(it->second.status);
       cudaFree(it->second.io);
+      if (it->second.side) cudaStreamDestroy(it->second.side);
+      if (it->second.fork) cudaEventDestroy(it->second.fork);
+      if (it->second.join) cudaEventDestroy(it->second.join);
       it = tmul::g_ws.erase(it);
     } else {
       ++it;

@@ -492,7 +492,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     }
   }
   // theta: block 0, two threads (u and v), ntheta terms of rho^-j F_(N-j); with one
-  // operand theta_V is copied (a kept transform) or equals theta_U (a square)
+  // operand theta_V is copied (a kept transform), equals theta_U (a square) or is
+  // left to the other operand's launch
   if (head && !two && threadIdx.x == 32) {
     if (a.theta_v) a.theta[1] = *a.theta_v;
   } else if (head && (threadIdx.x == 0 || threadIdx.x == 32)) {
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
       th = fma(__ldg(a.rho_pow + j), f, th);
     }
     a.theta[threadIdx.x == 0 ? 0 : 1] = th;
-    if (!two && !a.theta_v) a.theta[1] = th;
+    if (!two && a.square_theta && threadIdx.x == 0) a.theta[1] = th;
   }
 }
 

@@ -67,8 +67,9 @@ struct FwdArgs {
   long long s0;                  // high: (N+1) b - n
   double* X;                     // out: u at X[0..N), v at X[N..2N)
   double* theta;                 // high: theta_U, theta_V
-  int one_operand;               // 1: map u only (v == u, or v's transform is kept)
-  const double* theta_v;         // one_operand: theta_V to copy (nullptr: theta_V = theta_U)
+  int one_operand;               // 1: map u only (a square, a kept v, or v on another stream)
+  const double* theta_v;         // one_operand: theta_V to copy into theta[1]
+  int square_theta;              // one_operand: theta[1] = theta_U (a square)
 };
 
 struct BackItem {

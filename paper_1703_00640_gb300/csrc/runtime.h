@@ -32,6 +32,10 @@ struct Workspace {
   DevStatus* status = nullptr;
   char* io = nullptr;          // staging for tm_mul_host
   size_t io_size = 0;
+  // second stream for the operand v's split and forward FFT, forked from and
+  // joined into the workspace's stream (nullptr: one stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 size_t align_up(size_t x);
