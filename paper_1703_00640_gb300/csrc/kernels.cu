@@ -832,13 +832,6 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
 
 // ------------------------------------------------ twist + pointwise product
 
-// Z: FFT_M of z_u = u_even + i u_odd at Z[0..M) and of z_v at Z[M..2M).
-// For each pair (k, M-k): 2X_k = E + T, 2X_(M-k) = conj(E - T) with
-// E = Z_k + conj(Z_(M-k)), T = -i omega_N^k (Z_k - conj(Z_(M-k))) (real FFT of
-// length N from the half-length complex one); P = X^u X^v (the pointwise
-// product of the Convolution step); then the pre-twist of the inverse real
-// FFT: Q_k = (S + i conj(omega) D) scale, Q_(M-k) = conj(S - i conj(omega) D) scale,
-// S = 4P_k + conj(4P_(M-k)), D = 4P_k - conj(4P_(M-k)), scale = 1/(4N).
 // Real-FFT twist, pointwise product and inverse pre-twist in one step, for the
 // pair (k, M-k) of the half-length spectra Z (u) and Z' (v) (Z = DFT_M of the
 // real input packed as x_2j + i x_2j+1). With A = Z_k, B = conj(Z_(M-k)),
