@@ -402,18 +402,16 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   double2* bufs[2] = {R0, R1};
   int cur;
   if (!one && ws.side) {
-    // 1.-2. u's digits, forward map and forward FFT on s; v's on the side stream,
-    // so that each operand's kernels fill the other's idle SMs
+    // 1. digits + forward maps of both operands in one launch (one pass over the map
+    // table); 2. u's forward FFT on s, v's on the side stream, so that each
+    // operand's passes fill the SMs the other's leave idle
+    FwdArgs fa;
+    fwd_args(kind, u, v, n, p, pe, reinterpret_cast<double*>(R0), theta, false, nullptr, false,
+             &fa);
+    launch_fwd(kind, fa, 1, s);
+    mark(1);
     TM_CHECK(cudaEventRecord(ws.fork, s));
     TM_CHECK(cudaStreamWaitEvent(ws.side, ws.fork, 0));
-    FwdArgs fu, fv;
-    fwd_args(kind, u, u, n, p, pe, reinterpret_cast<double*>(R0), theta, true, nullptr, false,
-             &fu);
-    fwd_args(kind, v, v, n, p, pe, reinterpret_cast<double*>(R0) + N, theta + 1, true, nullptr,
-             false, &fv);
-    launch_fwd(kind, fu, 1, s);
-    mark(1);
-    launch_fwd(kind, fv, 1, ws.side);
     double2* bufs_v[2] = {R0 + M, R1 + M};
     cur = launch_fft(pe, bufs, 0, -1, 1, M, s);
     launch_fft(pe, bufs_v, 0, -1, 1, M, ws.side);
