@@ -422,9 +422,10 @@ def run_cuda(args):
         fft_ms += sum(phase[k][1]) + sum(phase[k][3])
         fft_launches += args.steps * 2 * plans[k]["fft_passes"]
     achieved = fft_flops / (fft_ms * 1e-3) / 1e12
-    # per two-operand product: 2 forward maps (u and v on their streams), 2 x passes
-    # forward FFT launches, twist, passes inverse launches, back map, 3 carry kernels
-    launches = args.steps * sum(3 * plans[k]["fft_passes"] + 7 for k in kinds)
+    # per two-operand product: 1 forward map (both operands), 2 x passes forward FFT
+    # launches (u and v on two streams), twist, passes inverse launches, back map,
+    # 3 carry kernels
+    launches = args.steps * sum(3 * plans[k]["fft_passes"] + 6 for k in kinds)
 
     # end to end through tm_mul_host with page-locked host buffers
     hu = torch.from_numpy(u_np.view(np.int64)).pin_memory()
