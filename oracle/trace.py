@@ -21,9 +21,12 @@ from . import bigmul
 # ---------------------------------------------------------------- digit split
 
 def unsigned_digits(x: int, count: int, b: int) -> list:
-    """d_i = bits [ib, ib+b) of x, i = 0..count-1 (x >= 0)."""
-    mask = (1 << b) - 1
-    return [(x >> (i * b)) & mask for i in range(count)]
+    """d_i = bits [ib, ib+b) of x, i = 0..count-1 (x >= 0). The bits are read from
+    the binary string of x once (least significant first), so the cost is linear
+    in the length of x."""
+    assert x >= 0
+    bits = bin(x)[2:][::-1]
+    return [int(bits[i * b:(i + 1) * b][::-1] or "0", 2) for i in range(count)]
 
 
 def balanced_digits(x: int, count: int, b: int, balance_top: bool) -> list:
