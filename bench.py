@@ -459,8 +459,13 @@ def run_cuda(args):
     variants = None
     if not args.no_variants:
         reps = max(5, min(args.steps, 20))
-        variants = {"square_ms": {}, "kept_operand_ms": {}, "two_operand_ms": {}}
+        variants = {"square_ms": {}, "kept_operand_ms": {}, "two_operand_ms": {},
+                    "adaptive_ms": {}, "adaptive_b": {}}
         for k in kinds:
+            variants["adaptive_ms"][k] = timed(
+                lambda: pkg.mul_adaptive(k, u, v, n, out=outs[k], report=False), reps)
+            _, arep = pkg.mul_adaptive(k, u, v, n, out=outs[k])
+            variants["adaptive_b"][k] = [arep["b"], arep["N"]]
             variants["two_operand_ms"][k] = timed(
                 lambda: pkg.mul(k, u, v, n, out=outs[k], report=False), reps)
             variants["square_ms"][k] = timed(

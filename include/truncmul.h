@@ -117,6 +117,24 @@ int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64
            void* stream, tm_report* rep);
 
 /*
+ * tm_mul_adaptive: tm_mul with a data-dependent digit size. The paper picks b
+ * empirically for random inputs (Section 5); the planner's b is the largest the
+ * worst-case error bound certifies for ANY operands (all digits at their maximum).
+ * This call measures the operands instead: one kernel sums the squares of the
+ * balanced digits of u and v for b + 1 at the shortest length that b + 1 admits
+ * (the high product's top digits too), the call waits for the stream to read the
+ * sums, and the product runs with b + 1 when the same bound with the measured
+ * norms ||U||_2 ||V||_2 in place of the worst case stays within the target (and
+ * the length is shorter), else with the planner's (b, N). The margin check guards
+ * the result as in tm_mul; rep->b, rep->N and rep->e_max (the bound that applied)
+ * tell which plan ran. Random operands have norms about sqrt(3) below the worst
+ * case. Arguments, layout, errors and results as tm_mul (results are exact either
+ * way); the call blocks until the norms are read.
+ */
+int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                    uint64_t n_bits, void* stream, tm_report* rep);
+
+/*
  * tm_mul_host: one product with HOST buffers. Copies u and v to the device,
  * runs tm_mul on `stream`, copies the result back and waits for the stream.
  * Page-locked host buffers give the fastest copies; pageable ones work.

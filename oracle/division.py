@@ -6,7 +6,8 @@ here the results are their definitions, on Python integers:
 
 - ``reciprocal(m, k)``: R = floor((2^(2k) - 1) / m) for 2^(k-1) <= m < 2^k, the
   reciprocal the library's Barrett context keeps (k + 1 bits);
-- ``divrem(x, m)``: q = floor(x / m), r = x - q m.
+- ``divrem(x, m)``: q = floor(x / m), r = x - q m;
+- ``is_divrem(x, m, q, r)``: the same pair recognised by x = q m + r, 0 <= r < m.
 
 ``long_division`` is a second, independent evaluation (binary restoring division,
 one quotient bit per step) that the CPU tests compare with the definitions.
@@ -25,6 +26,12 @@ def divrem(x: int, m: int):
     if x < 0 or m < 1:
         raise ValueError("x >= 0 and m >= 1 required")
     return x // m, x % m
+
+
+def is_divrem(x: int, m: int, q: int, r: int) -> bool:
+    """Euclidean division is unique: (q, r) == divrem(x, m) exactly when x = q m + r
+    and 0 <= r < m. One product instead of a division, for very long operands."""
+    return 0 <= r < m and q * m + r == x
 
 
 def long_division(x: int, m: int):

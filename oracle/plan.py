@@ -265,3 +265,97 @@ def choose(kind: str, n: int) -> dict:
     if best is None:
         raise ValueError(f"no FP64 plan for {kind} n={n}")
     return best
+
+
+# ------------------------------------------------ measured digit norms
+
+def bound_lo_measured(b: int, N: int, nu: float, nv: float) -> float:
+    """bound_lo with the measured norms ||U||_2, ||V||_2 of the balanced digits in
+    place of the worst case 2^(b-1) sqrt(N); per-coefficient terms unchanged."""
+    la, lb = lam_alpha(b), lam_beta(b)
+    eta = eta_conv(N)
+    g = 1.0 / (1.0 - 2.0 ** -b)
+    Su, Sv = g * nu, g * nv
+    MW = Su * Sv
+    d_in = ((la + 2) * U + (16.0 / 15.0) * 2.0 ** (-la * b)) * g * 2.0 ** (b - 1)
+    E_in = math.sqrt(N) * d_in * (Su + Sv) * (1.0 + eta)
+    q = (1.0 + 2.0 ** -b) * 2.0 ** -b
+    A = 1.0 / (1.0 - q)
+    tail = q ** lb / (1.0 - q)
+    return 2.0 ** b * (A * (eta * MW + E_in) + (lb + 3) * U * A * MW + tail * MW)
+
+
+def bound_hi_measured(b: int, N: int, nu: float, nv: float, tu: float, tv: float) -> float:
+    """bound_hi with ||F_0..F_(N-1)||_2 measured and the top digits F_N measured."""
+    rho = rho_float(N, b)
+    lg, ld = lam_gamma(b, N), lam_delta(b)
+    eta = eta_conv(N)
+    g = sum(gamma_coef_bound(r, b, N) for r in range(0, 80))
+    kappa0 = 2.0 ** b / rho
+    K2 = kappa0 / math.sqrt(1.0 - rho ** -2)
+    Su, Sv = g * (nu + tu * K2), g * (nv + tv * K2)
+    MW = Su * Sv
+    m_F = 2.0 ** (b - 1) + 2.0 ** b * kappa0
+    d_in = ((lg + 4) * U + gamma_tail(lg, b, N)) * g * m_F
+    E_in = math.sqrt(N) * d_in * (Su + Sv) * (1.0 + eta)
+    T = 2.0 ** b + 2.0 ** (b - 1) / (rho - 1.0)
+    J = -(-60 // b) + 1
+    E_theta = (2 * (J + 2) + 1) * U * T * T
+    q = (1.0 + 2.0 ** (1 - b)) * 2.0 ** -b
+    A = 1.01 * (1.0 + 2.0 ** -b) / (1.0 - q)
+    tail = q ** ld / (1.0 - q)
+    return 2.0 ** b * (A * (eta * MW + E_in + E_theta) + (ld + 4) * U * A * (MW + T * T)
+                       + tail * MW)
+
+
+def bound_full_measured(L: int, nu: float, nv: float) -> float:
+    MW = nu * nv
+    return eta_conv(L) * MW + 2.0 * U * MW
+
+
+def measured_length(kind: str, n: int, b: int) -> int:
+    """The shortest admissible length for digit size b (hypotheses only)."""
+    if kind == "lo":
+        return smooth_at_least(min_len_lo(n, b))
+    if kind == "hi":
+        N = smooth_at_least(min_len_hi(n, b))
+        while not hi_ok(n, b, N):
+            N = smooth_at_least(N + 1)
+        return N
+    return smooth_at_least(2 * full_digits(n, b) - 1)
+
+
+def adaptive_choice(kind: str, n: int, u: int, v: int) -> dict:
+    """The plan of the data-dependent digit size: the worst-case plan's b plus one,
+    at its shortest admissible length, when the bound on the operands' measured
+    digit norms is <= E_TARGET and that length is shorter; else the worst-case
+    plan. Norms come from the balanced digits of the split step (trace.split)."""
+    from . import trace
+    base = choose(kind, n)
+    b = base["b"] + 1
+    if b > B_MAX:
+        return base
+    N = measured_length(kind, n, b)
+    if N >= base["N"]:
+        return base
+    count = full_digits(n, b) if kind == "full" else N
+    du = trace.split(kind, u, n, b, count)
+    dv = trace.split(kind, v, n, b, count)
+    if kind == "hi":
+        nu = math.sqrt(sum(d * d for d in du[:N]))
+        nv = math.sqrt(sum(d * d for d in dv[:N]))
+        E = bound_hi_measured(b, N, nu, nv, float(abs(du[N])), float(abs(dv[N])))
+        lf, lb, nd = lam_gamma(b, N), lam_delta(b), N + 1
+    else:
+        nu = math.sqrt(sum(d * d for d in du))
+        nv = math.sqrt(sum(d * d for d in dv))
+        if kind == "lo":
+            E = bound_lo_measured(b, N, nu, nv)
+            lf, lb, nd = lam_alpha(b), lam_beta(b), N
+        else:
+            E = bound_full_measured(N, nu, nv)
+            lf, lb, nd = 0, 0, count
+    if E > E_TARGET:
+        return base
+    return {"kind": kind, "n": n, "b": b, "N": N, "n_digits": nd, "lam_fwd": lf,
+            "lam_bwd": lb, "e_max": E}

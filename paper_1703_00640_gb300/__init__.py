@@ -51,7 +51,7 @@ class TruncMulError(RuntimeError):
 NPHASES = 6
 PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "carry"]
 STATIC_MAX_BITS = 65536
-EXPORTS = ["tm_mul", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
+EXPORTS = ["tm_mul", "tm_mul_adaptive", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
@@ -82,6 +82,8 @@ def load(path: str = None):
         getattr(lib, name).argtypes = [P, P, P, ctypes.c_uint64, P, R]
         getattr(lib, name).restype = ctypes.c_int
     lib.tm_mul.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_adaptive.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_adaptive.restype = ctypes.c_int
     lib.tm_mul_host.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_mul_static.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_coeffs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
@@ -183,6 +185,22 @@ def mul(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True, che
                        ctypes.byref(rep) if rep is not None else None)
     if check and rc:
         raise TruncMulError(rc, "tm_mul")
+    return out, (rep.as_dict() if rep is not None else None)
+
+
+def mul_adaptive(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True,
+                 check: bool = True):
+    """tm_mul_adaptive: the product with the digit size chosen from the operands'
+    measured digit norms. Returns (out, report dict or None)."""
+    import torch
+    k = _kind(kind)
+    if out is None:
+        out = torch.empty(out_limbs(k, n_bits), dtype=torch.int64, device=u.device)
+    rep = Report() if report else None
+    rc = load().tm_mul_adaptive(k, _ptr(out), _ptr(u), _ptr(v), int(n_bits),
+                                _stream_ptr(stream), ctypes.byref(rep) if rep is not None else None)
+    if check and rc:
+        raise TruncMulError(rc, "tm_mul_adaptive")
     return out, (rep.as_dict() if rep is not None else None)
 
 

@@ -224,6 +224,7 @@ int get_workspace(cudaStream_t s, size_t bytes, Workspace** out) {
   if (!w.status) {
     TM_CHECK(cudaMalloc(&w.status, sizeof(DevStatus)));
     TM_CHECK(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+    TM_CHECK(cudaMalloc(&w.norms, 4 * sizeof(unsigned long long)));
     TM_CHECK(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
     TM_CHECK(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming));
     TM_CHECK(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming));
@@ -722,6 +723,62 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   return rc;
 }
 
+int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                    uint64_t n_bits, void* stream, tm_report* rep) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0 || !u || !v || !out) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  const size_t in_bytes = size_t(tmul::limbs_of(n_bits)) * 8;
+  const size_t ob = size_t(tmul::out_limbs(kind, n_bits)) * 8;
+  if (tmul::overlaps(out, ob, u, in_bytes) || tmul::overlaps(out, ob, v, in_bytes))
+    return TM_EALIAS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tmul::PlanParams use;
+  int rc = tmul::get_params(kind, n_bits, &use);
+  if (rc) return rc;
+  tmul::Workspace* ws = nullptr;
+  rc = tmul::get_workspace(s, 0, &ws);
+  if (rc) return rc;
+  // candidate: one more bit per digit at its shortest admissible length
+  const int b1 = use.b + 1;
+  const int64_t N1 = tmul::measured_length(kind, n_bits, b1);
+  if (N1 > 0 && N1 < use.N) {
+    const int64_t count = kind == TM_FULL ? (int64_t(n_bits) + 1 + b1 - 1) / b1 : N1;
+    const int64_t shift = kind == TM_HI ? (N1 + 1) * b1 - int64_t(n_bits) : 0;
+    const int64_t top = kind == TM_HI ? N1 : count - 1;
+    unsigned long long sums[4] = {0, 0, 0, 0};
+    if (cudaMemsetAsync(ws->norms, 0, sizeof(sums), s) != cudaSuccess) return TM_ECUDA;
+    tmul::launch_digit_norms(reinterpret_cast<const unsigned long long*>(u),
+                             reinterpret_cast<const unsigned long long*>(v),
+                             tmul::limbs_of(n_bits), n_bits, shift, b1,
+                             count, top, kind == TM_HI, ws->norms, s);
+    if (cudaMemcpyAsync(sums, ws->norms, sizeof(sums), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return TM_ECUDA;
+    // upper bounds on the norms (the sums are exact integers; a few ulps of slack)
+    const double up = 1.0 + std::ldexp(1.0, -48);
+    tmul::DigitNorms dn;
+    dn.nu = std::sqrt(double(sums[0])) * up;
+    dn.nv = std::sqrt(double(sums[1])) * up;
+    dn.tu = double(sums[2]);
+    dn.tv = double(sums[3]);
+    tmul::PlanParams p1;
+    if (tmul::measured_params(kind, n_bits, b1, N1, dn, &p1) == TM_OK) use = p1;
+  }
+  std::shared_ptr<tmul::PlanEntry> pe;
+  rc = tmul::get_tables(use, false, s, &pe);
+  if (rc) return rc;
+  rc = tmul::get_workspace(s, tmul::workspace_bytes(use), &ws);
+  if (rc) return rc;
+  rc = tmul::enqueue(kind, out, u, v, n_bits, s, use, *pe, *ws, nullptr, nullptr);
+  if (rc) return rc;
+  if (!rep) return TM_OK;
+  tmul::fill_plan_report(use, pe->fft, rep);
+  rep->table_bytes = pe->table_bytes;
+  return tmul::read_status(s, ws->status, rep);
+}
+
 int tm_operand_create(int kind, uint64_t n_bits, const uint64_t* v, void* stream,
                       tm_operand** out) {
   if (!out || !v) return TM_EINVAL;
@@ -853,6 +910,7 @@ int tm_release(void) {
       cudaFree(it->second.base);
       cudaFree(it->second.status);
       cudaFree(it->second.io);
+      if (it->second.norms) cudaFree(it->second.norms);
       if (it->second.side) cudaStreamDestroy(it->second.side);
       if (it->second.fork) cudaEventDestroy(it->second.fork);
       if (it->second.join) cudaEventDestroy(it->second.join);

@@ -232,6 +232,52 @@ __device__ __forceinline__ int balanced_digit(const unsigned long long* limbs, l
   return int(d) - ((d >= half) ? (1 << b) : 0) + carry_in;
 }
 
+// ----------------------------------------------------- digit norms
+
+// sums[0] += sum of u_p^2, sums[1] += sum of v_p^2 over the balanced digits p < count
+// of u 2^shift and v 2^shift (digit size b; the digit `top` unbalanced when
+// top_unbalanced); block 0 stores |u_top|, |v_top| in sums[2], sums[3] when
+// top_unbalanced. Exact: |digit| <= 2^b, count < 2^26.
+__global__ void k_digit_norms(const unsigned long long* u, const unsigned long long* v,
+                              long long nlimbs, unsigned long long n, long long shift, int b,
+                              long long count, long long top, int top_unbalanced,
+                              unsigned long long* sums) {
+  unsigned long long su = 0, sv = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long du = balanced_digit(u, nlimbs, n, shift, b, p, top, top_unbalanced != 0);
+    const long long dv = balanced_digit(v, nlimbs, n, shift, b, p, top, top_unbalanced != 0);
+    su += (unsigned long long)(du * du);
+    sv += (unsigned long long)(dv * dv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    su += __shfl_xor_sync(~0u, su, o);
+    sv += __shfl_xor_sync(~0u, sv, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums, su);
+    atomicAdd(sums + 1, sv);
+  }
+  if (top_unbalanced && blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long tu = balanced_digit(u, nlimbs, n, shift, b, top, top, true);
+    const long long tv = balanced_digit(v, nlimbs, n, shift, b, top, top, true);
+    sums[2] = (unsigned long long)(tu < 0 ? -tu : tu);
+    sums[3] = (unsigned long long)(tv < 0 ? -tv : tv);
+  }
+}
+
+void launch_digit_norms(const unsigned long long* u, const unsigned long long* v,
+                        long long nlimbs, unsigned long long n, long long shift, int b,
+                        long long count, long long top, bool top_unbalanced,
+                        unsigned long long* sums, cudaStream_t s) {
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_digit_norms<<<unsigned(blocks), 256, 0, s>>>(u, v, nlimbs, n, shift, b, count, top,
+                                                  top_unbalanced ? 1 : 0, sums);
+}
+
 // ----------------------------------------------------- forward maps
 
 // Launches KERNEL<ROWS> with ROWS = rows for the map row counts the planner

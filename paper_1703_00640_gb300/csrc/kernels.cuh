@@ -190,6 +190,13 @@ void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cu
 void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,
                            cudaStream_t s);
 
+// Sums of squares of the balanced digits of u and v (and the top digits of the high
+// product) into sums[0..3] (zeroed by the caller).
+void launch_digit_norms(const unsigned long long* u, const unsigned long long* v,
+                        long long nlimbs, unsigned long long n, long long shift, int b,
+                        long long count, long long top, bool top_unbalanced,
+                        unsigned long long* sums, cudaStream_t s);
+
 // pipeline stages
 void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s);
 void set_fft_smem_attribute();

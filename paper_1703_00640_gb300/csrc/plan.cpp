@@ -164,6 +164,58 @@ double bound_full(uint64_t n, int b, int64_t L) {
   return eta_conv(L) * MW + 2.0 * kU * MW;
 }
 
+// The same bounds with measured digit norms in place of the worst case: nu, nv are
+// ||U||_2, ||V||_2 of the balanced digits (high product: of F_0 .. F_(N-1)), tu, tv
+// the high product's top digits F_N. Every use of the worst-case norm
+// 2^(b-1) sqrt(N) (or sqrt(N_d 2^(2b-2)) for the full product) becomes the
+// measured one; per-coefficient magnitudes (din, |theta|) keep their worst case.
+Bound bound_lo_measured(int b, int64_t N, double nu, double nv) {
+  const int la = lambda_alpha(b), lb = lambda_geometric(b, std::ldexp(1.0, -b));
+  const double eta = eta_conv(N);
+  const double g = 1.0 / (1.0 - std::ldexp(1.0, -b));
+  const double Su = g * nu, Sv = g * nv;
+  const double MW = Su * Sv;
+  const double din = ((la + 2) * kU + 16.0 / 15.0 * std::ldexp(1.0, -la * b)) * g *
+                     std::ldexp(1.0, b - 1);
+  const double Ein = std::sqrt(double(N)) * din * (Su + Sv) * (1.0 + eta);
+  const double q = (1.0 + std::ldexp(1.0, -b)) * std::ldexp(1.0, -b);
+  const double A = 1.0 / (1.0 - q);
+  const double tail = std::pow(q, lb) / (1.0 - q);
+  const double EW = eta * MW + Ein;
+  const double E = std::ldexp(A * EW + (lb + 3) * kU * A * MW + tail * MW, b);
+  return {E, la, lb};
+}
+
+Bound bound_hi_measured(int b, int64_t N, double nu, double nv, double tu, double tv) {
+  const double rho = rho_of(N, b);
+  const int lg = lambda_gamma(b, N), ld = lambda_geometric(b, std::ldexp(1.0, 1 - b));
+  const double eta = eta_conv(N);
+  double g = 0;
+  for (int r = 0; r < 80; ++r) g += gamma_bound(r, b, N);
+  const double kappa0 = std::ldexp(1.0, b) / rho;
+  const double K2 = kappa0 / std::sqrt(1.0 - 1.0 / (rho * rho));   // ||kappa||_2 / 2^b
+  const double Su = g * (nu + tu * K2), Sv = g * (nv + tv * K2);
+  const double MW = Su * Sv;
+  const double mF = std::ldexp(1.0, b - 1) + std::ldexp(kappa0, b);
+  const double din = ((lg + 4) * kU + gamma_tail(lg, b, N)) * g * mF;
+  const double Ein = std::sqrt(double(N)) * din * (Su + Sv) * (1.0 + eta);
+  const double T = std::ldexp(1.0, b) + std::ldexp(1.0, b - 1) / (rho - 1.0);
+  const int J = (60 + b - 1) / b + 1;
+  const double Etheta = (2 * (J + 2) + 1) * kU * T * T;
+  const double q = (1.0 + std::ldexp(1.0, 1 - b)) * std::ldexp(1.0, -b);
+  const double A = 1.01 * (1.0 + std::ldexp(1.0, -b)) / (1.0 - q);
+  const double tail = std::pow(q, ld) / (1.0 - q);
+  const double EW = eta * MW + Ein;
+  const double E =
+      std::ldexp(A * (EW + Etheta) + (ld + 4) * kU * A * (MW + T * T) + tail * MW, b);
+  return {E, lg, ld};
+}
+
+double bound_full_measured(int64_t L, double nu, double nv) {
+  const double MW = nu * nv;
+  return eta_conv(L) * MW + 2.0 * kU * MW;
+}
+
 std::vector<int64_t> candidate_lengths(int64_t x) {
   x = std::max<int64_t>(4, x);
   const int64_t first = smooth_at_least(x);
@@ -243,6 +295,46 @@ int choose_params(int kind, uint64_t n, PlanParams* out) {
   }
   if (!found) return TM_ERANGE;
   *out = best;
+  return TM_OK;
+}
+
+int64_t measured_length(int kind, uint64_t n, int b) {
+  if (b < kBMin || b > kBMax) return -1;
+  int64_t lmin;
+  if (kind == TM_LO) {
+    lmin = std::max<int64_t>(3, int64_t((n + b - 1) / b));
+  } else if (kind == TM_HI) {
+    lmin = std::max<int64_t>(3, int64_t((n + 2 + b - 1) / b) - 1);
+    while (!hi_hypothesis(n, b, lmin)) ++lmin;
+  } else {
+    lmin = 2 * full_digit_count(n, b) - 1;
+  }
+  int64_t N = smooth_at_least(lmin);
+  while (kind == TM_HI && !hi_hypothesis(n, b, N)) N = smooth_at_least(N + 1);
+  return N;
+}
+
+int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn,
+                    PlanParams* out) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (b < kBMin || b > kBMax || N < 4) return TM_ERANGE;
+  PlanParams p;
+  p.kind = kind; p.n = n; p.b = b; p.N = N;
+  if (kind == TM_LO) {
+    const Bound B = bound_lo_measured(b, N, dn.nu, dn.nv);
+    p.e_max = B.E; p.lam_fwd = B.lf; p.lam_bwd = B.lb; p.n_digits = N;
+  } else if (kind == TM_HI) {
+    if (!hi_hypothesis(n, b, N)) return TM_ERANGE;
+    const Bound B = bound_hi_measured(b, N, dn.nu, dn.nv, dn.tu, dn.tv);
+    p.e_max = B.E; p.lam_fwd = B.lf; p.lam_bwd = B.lb; p.n_digits = N + 1;
+    p.rho = rho_of(N, b);
+  } else {
+    p.n_digits = full_digit_count(n, b);
+    if (N < 2 * p.n_digits - 1) return TM_ERANGE;
+    p.e_max = bound_full_measured(N, dn.nu, dn.nv);
+  }
+  if (!(p.e_max <= kTarget)) return TM_ERANGE;
+  *out = p;
   return TM_OK;
 }
 

@@ -67,6 +67,20 @@ int make_fft_plan(int64_t M, FftPlan* out, bool single = false);
 int choose_params_noalloc(int kind, uint64_t n, PlanParams* out);
 int make_fft_plan_noalloc(int64_t M, FftPlan* out);
 
+// Data-dependent digit size. Measured norms of the balanced digits of u and v for
+// one (b, N): nu, nv = ||U||_2, ||V||_2 (high product: of F_0 .. F_(N-1)), tu, tv
+// = the high product's top digits F_N.
+struct DigitNorms {
+  double nu = 0, nv = 0, tu = 0, tv = 0;
+};
+// The length a plan with digit size b would take (the shortest admissible smooth
+// length for (kind, n, b)); -1 when b is outside the planner's range.
+int64_t measured_length(int kind, uint64_t n, int b);
+// The plan (b, N) with its error bound evaluated on the measured norms: TM_OK when
+// the bound is <= the target (e_max = that bound), else TM_ERANGE.
+int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn,
+                    PlanParams* out);
+
 // Exposed for tests of the planner.
 bool is_valid_length(int64_t L);
 int64_t smooth_at_least(int64_t x);

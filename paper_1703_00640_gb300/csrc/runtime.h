@@ -36,6 +36,7 @@ struct Workspace {
   // joined into the workspace's stream (nullptr: one stream)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  unsigned long long* norms = nullptr;   // 4 words for the measured digit norms
 };
 
 size_t align_up(size_t x);

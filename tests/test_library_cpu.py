@@ -78,6 +78,11 @@ def test_host_side_errors(pkg):
     # null operands are rejected before any CUDA call
     assert lib.tm_mul(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_lo(None, None, None, 0, None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_adaptive(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_adaptive(9, fake_ptr := ctypes.c_void_p(0x1000), fake_ptr, fake_ptr, 100,
+                               None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_adaptive(1, fake_ptr, fake_ptr, fake_ptr, (1 << 31) + 1, None,
+                               None) == pkg.TM_ERANGE
     # kept operands: argument checks precede any CUDA call
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(0x1000)

@@ -64,3 +64,16 @@ def test_barrett_quotient_window():
         for w in (lo, lo + 1):
             if abs(prod - (w << (k + 1))) < (1 << (k + 1)):
                 assert q - 3 <= w <= q + 1
+
+
+def test_is_divrem_characterises_divrem():
+    rng = random.Random(13)
+    for _ in range(500):
+        k = rng.randrange(1, 200)
+        m = rng.randrange(1 << (k - 1), 1 << k)
+        x = rng.randrange(0, 1 << (2 * k))
+        q, r = D.divrem(x, m)
+        assert D.is_divrem(x, m, q, r)
+        # every neighbouring pair is rejected
+        for dq, dr in ((1, 0), (-1, 0), (0, 1), (0, -1), (1, -m), (-1, m)):
+            assert not D.is_divrem(x, m, q + dq, r + dr)

@@ -60,3 +60,47 @@ def test_truncated_length_is_shorter():
     for n in (2**16, 2**20, 2**24):
         ratio = P.choose("lo", n)["N"] / P.choose("full", n)["N"]
         assert 0.6 < ratio < 0.9
+
+
+def test_measured_bounds_reduce_to_the_worst_case():
+    """With the worst-case norms (every digit at 2^(b-1), top digit 2^b) the
+    measured-norm bounds equal the planner's worst-case bounds."""
+    import math
+    for n, b, N in [(1 << 16, 11, 6144), (1 << 20, 9, 122880), (1 << 24, 8, 2097152)]:
+        w = 2.0 ** (b - 1) * math.sqrt(N)
+        assert P.bound_lo_measured(b, N, w, w) == pytest.approx(P.bound_lo(n, b, N)[0], rel=1e-12)
+    for n, b, N in [(1 << 16, 10, 6912), (1 << 24, 7, 2408448)]:
+        w = 2.0 ** (b - 1) * math.sqrt(N)
+        t = 2.0 ** b
+        assert P.bound_hi_measured(b, N, w, w, t, t) == pytest.approx(P.bound_hi(n, b, N)[0],
+                                                                      rel=1e-12)
+    for n, b, L in [(1 << 16, 17, 8192), (1 << 24, 12, 2867200)]:
+        w = 2.0 ** (b - 1) * math.sqrt(P.full_digits(n, b))
+        assert P.bound_full_measured(L, w, w) == pytest.approx(P.bound_full(n, b, L)[0],
+                                                               rel=1e-12)
+
+
+def test_adaptive_choice_bounds():
+    """The data-dependent choice: worst-case operands keep the planner's b;
+    random operands take b + 1 only where the measured bound certifies it, and
+    every accepted bound is <= the target."""
+    import random
+    rng = random.Random(3)
+    for n in (1 << 12, 1 << 16, 123457):
+        for kind in ("lo", "hi", "full"):
+            base = P.choose(kind, n)
+            # every (b+1)-bit chunk 100...0: balanced digits of magnitude ~2^b, the
+            # worst case for b + 1 (all-ones operands have balanced digits near 0)
+            b1 = base["b"] + 1
+            s0 = 0
+            if kind == "hi":               # the high product splits u 2^s0
+                s0 = (P.measured_length(kind, n, b1) + 1) * b1 - n
+            worst = sum(1 << (i * b1 + b1 - 1 - s0) for i in range((n + s0) // b1)
+                        if 0 <= i * b1 + b1 - 1 - s0 < n)
+            assert P.adaptive_choice(kind, n, worst, worst)["b"] == base["b"]
+            u, v = rng.getrandbits(n), rng.getrandbits(n)
+            c = P.adaptive_choice(kind, n, u, v)
+            assert c["b"] in (base["b"], base["b"] + 1)
+            assert c["e_max"] <= P.E_TARGET
+            if c["b"] != base["b"]:
+                assert c["N"] < base["N"]
