@@ -269,6 +269,8 @@ def choose(kind: str, n: int) -> dict:
 
 # ------------------------------------------------ measured digit norms
 
+MEASURE_SPAN = 3.5    # measure only when b + 1's worst-case bound is <= this x E_TARGET
+
 def bound_lo_measured(b: int, N: int, nu: float, nv: float) -> float:
     """bound_lo with the measured norms ||U||_2, ||V||_2 of the balanced digits in
     place of the worst case 2^(b-1) sqrt(N); per-coefficient terms unchanged."""
@@ -339,6 +341,17 @@ def adaptive_choice(kind: str, n: int, u: int, v: int) -> dict:
     if N >= base["N"]:
         return base
     count = full_digits(n, b) if kind == "full" else N
+    # the library measures only when b + 1's worst-case bound is within MEASURE_SPAN
+    # of the target
+    w = 2.0 ** (b - 1) * math.sqrt(count)
+    if kind == "lo":
+        Ew = bound_lo_measured(b, N, w, w)
+    elif kind == "hi":
+        Ew = bound_hi_measured(b, N, w, w, 2.0 ** b, 2.0 ** b)
+    else:
+        Ew = bound_full_measured(N, w, w)
+    if Ew > MEASURE_SPAN * E_TARGET:
+        return base
     du = trace.split(kind, u, n, b, count)
     dv = trace.split(kind, v, n, b, count)
     if kind == "hi":

@@ -739,10 +739,19 @@ int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* 
   tmul::Workspace* ws = nullptr;
   rc = tmul::get_workspace(s, 0, &ws);
   if (rc) return rc;
-  // candidate: one more bit per digit at its shortest admissible length
+  // candidate: one more bit per digit at its shortest admissible length, measured
+  // only when its worst-case bound is within kMeasure of the target (random digits
+  // bring the norm product down by about 3)
+  constexpr double kMeasure = 3.5;
   const int b1 = use.b + 1;
   const int64_t N1 = tmul::measured_length(kind, n_bits, b1);
-  if (N1 > 0 && N1 < use.N) {
+  tmul::PlanParams pw;
+  const bool worth =
+      N1 > 0 && N1 < use.N &&
+      tmul::measured_params(kind, n_bits, b1, N1, tmul::worst_norms(kind, n_bits, b1, N1),
+                            &pw) != TM_EINVAL &&
+      pw.N == N1 && pw.e_max <= kMeasure * tmul::bound_target();
+  if (worth) {
     const int64_t count = kind == TM_FULL ? (int64_t(n_bits) + 1 + b1 - 1) / b1 : N1;
     const int64_t shift = kind == TM_HI ? (N1 + 1) * b1 - int64_t(n_bits) : 0;
     const int64_t top = kind == TM_HI ? N1 : count - 1;

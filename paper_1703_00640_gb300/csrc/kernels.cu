@@ -243,12 +243,34 @@ __global__ void k_digit_norms(const unsigned long long* u, const unsigned long l
                               long long count, long long top, int top_unbalanced,
                               unsigned long long* sums) {
   unsigned long long su = 0, sv = 0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < count;
+  const long long pend = top_unbalanced ? (count < top ? count : top) : count;
+  const unsigned half = 1u << (b - 1);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pend;
        p += (long long)gridDim.x * blockDim.x) {
-    const long long du = balanced_digit(u, nlimbs, n, shift, b, p, top, top_unbalanced != 0);
-    const long long dv = balanced_digit(v, nlimbs, n, shift, b, p, top, top_unbalanced != 0);
-    su += (unsigned long long)(du * du);
-    sv += (unsigned long long)(dv * dv);
+    // balanced digit p (p < top when the top is unbalanced) of u and v: b bits at
+    // p b - shift and the carry bit below, from two or three cached limb reads
+    const long long pos = p * b - shift;
+    long long d[2];
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const unsigned long long* x = o ? v : u;
+      unsigned dp, c;
+      if (pos >= 1 && (unsigned long long)(pos + b) <= n) {
+        const long long w = pos >> 6;
+        const int off = int(pos & 63);
+        const unsigned long long l0 = __ldg(x + w);
+        const unsigned long long l1 = (off + b > 64) ? __ldg(x + w + 1) : 0ull;
+        dp = unsigned(((l0 >> off) | ((l1 << 1) << (63 - off))) & ((1ull << b) - 1ull));
+        const long long pc = pos - 1;
+        c = unsigned((__ldg(x + (pc >> 6)) >> (pc & 63)) & 1ull);
+      } else {
+        dp = get_bits(x, nlimbs, n, pos, b);
+        c = p > 0 ? get_bits(x, nlimbs, n, pos - 1, 1) : 0u;
+      }
+      d[o] = (long long)dp - (dp >= half ? (1ll << b) : 0) + c;
+    }
+    su += (unsigned long long)(d[0] * d[0]);
+    sv += (unsigned long long)(d[1] * d[1]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

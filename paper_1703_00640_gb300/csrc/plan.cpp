@@ -314,6 +314,16 @@ int64_t measured_length(int kind, uint64_t n, int b) {
   return N;
 }
 
+double bound_target() { return kTarget; }
+
+DigitNorms worst_norms(int kind, uint64_t n, int b, int64_t N) {
+  DigitNorms w;
+  const double count = kind == TM_FULL ? double(full_digit_count(n, b)) : double(N);
+  w.nu = w.nv = std::ldexp(std::sqrt(count), b - 1);
+  w.tu = w.tv = kind == TM_HI ? std::ldexp(1.0, b) : 0.0;
+  return w;
+}
+
 int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn,
                     PlanParams* out) {
   if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
@@ -333,9 +343,8 @@ int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn
     if (N < 2 * p.n_digits - 1) return TM_ERANGE;
     p.e_max = bound_full_measured(N, dn.nu, dn.nv);
   }
-  if (!(p.e_max <= kTarget)) return TM_ERANGE;
-  *out = p;
-  return TM_OK;
+  *out = p;                      // e_max filled even when above the target
+  return p.e_max <= kTarget ? TM_OK : TM_ERANGE;
 }
 
 // ---------------------------------------------------------------- FFT plan

@@ -76,10 +76,15 @@ struct DigitNorms {
 // The length a plan with digit size b would take (the shortest admissible smooth
 // length for (kind, n, b)); -1 when b is outside the planner's range.
 int64_t measured_length(int kind, uint64_t n, int b);
-// The plan (b, N) with its error bound evaluated on the measured norms: TM_OK when
-// the bound is <= the target (e_max = that bound), else TM_ERANGE.
+// The plan (b, N) with its error bound evaluated on the measured norms (e_max):
+// TM_OK when the bound is <= the target, TM_ERANGE when it is above (out still
+// filled) or (b, N) is not admissible.
 int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn,
                     PlanParams* out);
+// The worst-case norms for (kind, n, b, N) (every digit at its largest magnitude),
+// and the target every plan's bound must meet.
+DigitNorms worst_norms(int kind, uint64_t n, int b, int64_t N);
+double bound_target();
 
 // Exposed for tests of the planner.
 bool is_valid_length(int64_t L);
