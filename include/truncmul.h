@@ -135,8 +135,9 @@ int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* 
                     uint64_t n_bits, void* stream, tm_report* rep);
 
 /*
- * tm_mul_host: one product with HOST buffers. Copies u and v to the device,
- * runs tm_mul on `stream`, copies the result back and waits for the stream.
+ * tm_mul_host: one product with HOST buffers. Copies u and v to the device
+ * (once when u_host == v_host, which squares), runs tm_mul on `stream`, copies
+ * the result back and waits for the stream.
  * Page-locked host buffers give the fastest copies; pageable ones work.
  * Limb counts as above. Returns like tm_mul; *rep (optional) is filled.
  */

@@ -225,6 +225,7 @@ int get_workspace(cudaStream_t s, size_t bytes, Workspace** out) {
     TM_CHECK(cudaMalloc(&w.status, sizeof(DevStatus)));
     TM_CHECK(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
     TM_CHECK(cudaMalloc(&w.norms, 4 * sizeof(unsigned long long)));
+    TM_CHECK(cudaMallocHost(&w.status_host, sizeof(DevStatus)));
     TM_CHECK(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
     TM_CHECK(cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming));
     TM_CHECK(cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming));
@@ -711,15 +712,36 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   uint64_t* du = reinterpret_cast<uint64_t*>(io);
   uint64_t* dv = reinterpret_cast<uint64_t*>(io + tmul::align_up(in_bytes));
   uint64_t* dout = reinterpret_cast<uint64_t*>(io + 2 * tmul::align_up(in_bytes));
+  if (u_host == v_host) dv = du;              // a square: one copy, the squaring path
   if (cudaMemcpyAsync(du, u_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      (dv != du &&
+       cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess))
     return TM_ECUDA;
-  tm_report local{};
-  rc = tmul::run(kind, dout, du, dv, n_bits, stream, rep ? rep : &local, nullptr);
-  if (rc && rc != TM_EPRECISION) return rc;
+  tmul::PlanParams p;
+  rc = tmul::get_params(kind, n_bits, &p);
+  if (rc) return rc;
+  std::shared_ptr<tmul::PlanEntry> pe;
+  rc = tmul::get_tables(p, false, s, &pe);
+  if (rc) return rc;
+  tmul::Workspace* ws = nullptr;
+  rc = tmul::get_workspace(s, tmul::workspace_bytes(p), &ws);
+  if (rc) return rc;
+  rc = tmul::enqueue(kind, dout, du, dv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
+  if (rc) return rc;
+  // result, status word and its reset in stream order: one wait for all of it
   if (cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return TM_ECUDA;
+  rc = ws->status_host->flags ? TM_EPRECISION : TM_OK;
+  if (rep) {
+    tmul::fill_plan_report(p, pe->fft, rep);
+    rep->table_bytes = pe->table_bytes;
+    rep->margin = std::ldexp(double(ws->status_host->margin_fx), -63);
+    rep->status = rc;
+  }
   return rc;
 }
 
@@ -920,6 +942,7 @@ int tm_release(void) {
       cudaFree(it->second.status);
       cudaFree(it->second.io);
       if (it->second.norms) cudaFree(it->second.norms);
+      if (it->second.status_host) cudaFreeHost(it->second.status_host);
       if (it->second.side) cudaStreamDestroy(it->second.side);
       if (it->second.fork) cudaEventDestroy(it->second.fork);
       if (it->second.join) cudaEventDestroy(it->second.join);

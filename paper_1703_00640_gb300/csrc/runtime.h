@@ -37,6 +37,7 @@ struct Workspace {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   unsigned long long* norms = nullptr;   // 4 words for the measured digit norms
+  DevStatus* status_host = nullptr;      // page-locked copy of the status (tm_mul_host)
 };
 
 size_t align_up(size_t x);

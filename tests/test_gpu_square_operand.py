@@ -191,3 +191,13 @@ def test_operand_alias_and_stream(pkg):
         assert np.array_equal(host(got), _expect("lo", u, v, n))
     finally:
         op.close()
+
+
+def test_square_with_host_buffers(pkg):
+    n = 77777
+    u, _ = workloads.pattern_limbs("random", n, seed=19)
+    for kind in ("lo", "hi", "full"):
+        out, rep = pkg.mul_host(kind, u, u, n)
+        assert rep["status"] == 0
+        d, _ = pkg.mul(kind, dev(u), dev(u), n)
+        assert np.array_equal(out, host(d))
