@@ -29,7 +29,7 @@ UNIT = "Gbit/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs)
 FP64_DFMA_MEASURED = 1.008   # DFMA/DADD/DMUL issue ceiling measured on this GB300 pool
 # DRAM bytes per k_fft_pass launch from profiles/k_fft_pass_n2p24.md (n = 2^24 only)
-FFT_TRAFFIC_N2P24 = 32.4e6
+FFT_TRAFFIC_N2P24 = 23.5e6
 L2_FLUSH_BYTES = 256 << 20
 
 
