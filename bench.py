@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--n", "--n-bits", dest="n", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--served", action="store_true",
@@ -51,6 +51,20 @@ def parse():
     ap.add_argument("--no-division", action="store_true",
                     help="skip the division timings")
     return ap.parse_args()
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (every rank gets it)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(n, steps, world, t_lo_ms, t_hi_ms):
+    """Gbit/s of low + high products over all replicas: each of `world` ranks ran
+    `steps` low and high products of n bits; the slowest rank's times count."""
+    return 2 * n * steps * world / ((t_lo_ms + t_hi_ms) * 1e-3) / 1e9
 
 
 def dist_env():
@@ -408,10 +422,9 @@ def run_cuda(args):
     t_lo, t_hi, t_full = (sum(per[k]) for k in kinds)
     dev_total = t_lo + t_hi + t_full
     if dist:
-        tt = torch.tensor([t_lo, t_hi, t_full, dev_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_lo, t_hi, t_full, dev_total = tt.tolist()
-    value = 2 * n * args.steps * world / ((t_lo + t_hi) * 1e-3) / 1e9
+        t_lo, t_hi, t_full, dev_total = max_over_ranks([t_lo, t_hi, t_full, dev_total], dist,
+                                                       "cuda")
+    value = replica_throughput(n, args.steps, world, t_lo, t_hi)
 
     # roofline of the dominant kernel (the FFT passes): 3 complex FFTs of length
     # M = N/2 per product at the conventional 5 M log2 M flops each
