@@ -50,6 +50,8 @@ def parse():
                     help="skip the square / kept-operand timings")
     ap.add_argument("--no-division", action="store_true",
                     help="skip the division timings")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FFT layouts (no tm_autotune before timing)")
     return ap.parse_args()
 
 
@@ -370,6 +372,12 @@ def run_cuda(args):
     plans = {k: pkg.plan(k, n) for k in kinds}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    # FFT pass layouts picked by measurement for the three plans (tm_autotune)
+    tuned = None
+    if not args.no_autotune:
+        tuned = {k: pkg.autotune(k, n, stream=stream) for k in kinds}
+        plans = {k: pkg.plan(k, n) for k in kinds}
+
     # correctness gate on the bench workload (sampled against the oracle's low product)
     _, rep = pkg.mul("lo", u, v, n, out=outs["lo"])
     margin = {"lo": rep["margin"]}
@@ -570,6 +578,7 @@ def run_cuda(args):
                              "against the measured DFMA issue ceiling; traffic = ncu DRAM "
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
+        "autotune": tuned,
         "square_and_kept_operand": variants,
         "division": division,
         "cpu_baseline": cpu,

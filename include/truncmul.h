@@ -343,6 +343,30 @@ int tm_coeffs(int kind, int64_t* c_out, const uint64_t* u, const uint64_t* v, ui
               void* stream, tm_report* rep);
 
 /*
+ * tm_autotune: picks the FFT pass layout for the transform length of (kind,
+ * n_bits) by measurement. Candidates vary the points per CTA, how the odd prime
+ * factors of the length are spread over the passes, and the number of passes; each
+ * is timed on `stream` (two forward transforms and one inverse, CUDA events, median
+ * of three after a warm-up) on scratch buffers of 4 x 16 (N/2) bytes allocated for
+ * the call. The fastest becomes the layout of every later plan with that length on
+ * this device (plans built before keep theirs for their current users, e.g. a
+ * tm_batch). Results of products do not depend on the layout (they are exact);
+ * only the time does. Waits for the stream. *out: candidates timed, the chosen
+ * layout, its pass count, and the default and chosen layouts' times (ms).
+ */
+typedef struct tm_tune {
+  int32_t candidates;
+  int32_t points;      /* points per CTA the chosen layout aims for        */
+  int32_t split;       /* 0 balanced, 1 odd primes first pass, 2 last pass */
+  int32_t passes;      /* 0 default count, else 2 or 3                     */
+  int32_t npass;       /* passes of the chosen layout                      */
+  int32_t reserved;
+  double ms_default;
+  double ms_best;
+} tm_tune;
+int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out);
+
+/*
  * tm_plan_query: the plan the library uses for (kind, n_bits), without any
  * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, e_max and
  * workspace_bytes of *rep. Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.

@@ -42,6 +42,16 @@ class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("points", ctypes.c_int32),
+                ("split", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("npass", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class TruncMulError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})")
@@ -55,7 +65,8 @@ EXPORTS = ["tm_mul", "tm_mul_adaptive", "tm_mul_full", "tm_mul_lo", "tm_mul_hi",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
-           "tm_operand_create", "tm_mul_operand", "tm_operand_destroy", "tm_reciprocal",
+           "tm_autotune", "tm_operand_create", "tm_mul_operand", "tm_operand_destroy",
+           "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
            "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
@@ -110,6 +121,8 @@ def load(path: str = None):
                                       ctypes.POINTER(ctypes.c_void_p)]
     lib.tm_mul_operand.argtypes = [P, P, P, P, R]
     lib.tm_operand_destroy.argtypes = [P]
+    lib.tm_autotune.argtypes = [ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(Tune)]
+    lib.tm_autotune.restype = ctypes.c_int
     lib.tm_reciprocal.argtypes = [P, P, ctypes.c_uint64, P]
     lib.tm_barrett_create.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_void_p)]
     lib.tm_barrett_divrem.argtypes = [P, P, P, P, P, R]
@@ -327,6 +340,15 @@ class Operand:
             self.close()
         except Exception:
             pass
+
+
+def autotune(kind, n_bits: int, stream=None) -> dict:
+    """tm_autotune: time the FFT layouts for (kind, n) and keep the fastest."""
+    t = Tune()
+    rc = load().tm_autotune(_kind(kind), int(n_bits), _stream_ptr(stream), ctypes.byref(t))
+    if rc:
+        raise TruncMulError(rc, "tm_autotune")
+    return t.as_dict()
 
 
 def reciprocal(m, k_bits: int, out=None, stream=None):

@@ -23,6 +23,10 @@ std::mutex g_mu;
 std::map<std::tuple<int, int, int, int64_t, int>, std::shared_ptr<PlanEntry>> g_plans;
 std::map<std::pair<int, uint64_t>, PlanParams> g_params;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+// FFT layouts chosen by tm_autotune, per (device, complex length M), and plan
+// entries replaced after tuning (still referenced by batches; freed by tm_release)
+std::map<std::pair<int, int64_t>, FftShape> g_tuned;
+std::vector<std::shared_ptr<PlanEntry>> g_retired;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return TM_ENOMEM;
@@ -130,7 +134,14 @@ int build_tables(const PlanParams& p, bool single, cudaStream_t s, std::shared_p
   e->p = p;
   const int kind = p.kind;
   e->M = e->p.N / 2;
-  int rc = make_fft_plan(e->M, &e->fft, single);
+  const FftShape* shape = nullptr;
+  if (!single) {
+    int dev = 0;
+    TM_CHECK(cudaGetDevice(&dev));
+    auto t = g_tuned.find(std::make_pair(dev, e->M));
+    if (t != g_tuned.end()) shape = &t->second;
+  }
+  int rc = make_fft_plan(e->M, &e->fft, single, shape);
   if (rc) return rc;
   const size_t cnt = layout_twiddles(e.get());
   TM_CHECK(cudaMalloc(&e->tw, cnt * sizeof(double2)));
@@ -893,13 +904,131 @@ int tm_operand_destroy(tm_operand* op) {
   return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
+int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
+  if (!out) return TM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tmul::PlanParams p;
+  int rc = tmul::get_params(kind, n_bits, &p);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  tmul::ensure_kernel_attributes();
+  const int64_t M = p.N / 2;
+  // candidate layouts: default first, then every distinct valid variation
+  std::vector<tmul::FftShape> shapes;
+  std::vector<tmul::FftPlan> plans;
+  for (int passes : {0, 2, 3})
+    for (int split : {0, 1, 2})
+      for (int points : {1024, 512, 2048}) {
+        const tmul::FftShape sh{points, split, passes};
+        tmul::FftPlan f;
+        if (tmul::make_fft_plan(M, &f, false, &sh) != TM_OK) continue;
+        bool dup = false;
+        for (const auto& g : plans) {
+          bool same = g.npass == f.npass;
+          for (int i = 0; same && i < f.npass; ++i)
+            same = g.pass[i].L == f.pass[i].L && g.pass[i].C == f.pass[i].C &&
+                   g.pass[i].threads == f.pass[i].threads;
+          dup = dup || same;
+        }
+        if (!dup) { shapes.push_back(sh); plans.push_back(f); }
+      }
+  if (plans.empty()) return TM_ERANGE;
+  double2* buf = nullptr;
+  const size_t region = size_t(2) * M * sizeof(double2);
+  if (cudaMalloc(&buf, 2 * region) != cudaSuccess) { (void)cudaGetLastError(); return TM_ENOMEM; }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<double> ms(plans.size(), 0.0);
+  rc = TM_OK;
+  for (size_t c = 0; c < plans.size() && rc == TM_OK; ++c) {
+    tmul::PlanEntry e;
+    e.p = p;
+    e.M = M;
+    e.fft = plans[c];
+    const size_t cnt = tmul::layout_twiddles(&e);
+    if (cudaMalloc(&e.tw, cnt * sizeof(double2)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = TM_ENOMEM;
+      break;
+    }
+    tmul::init_twiddles(e, s);
+    double2* bufs[2] = {buf, reinterpret_cast<double2*>(reinterpret_cast<char*>(buf) + region)};
+    std::vector<float> t;
+    for (int rep = 0; rep < 4; ++rep) {          // one warm-up, three timed
+      cudaMemsetAsync(buf, 0x3f, 2 * region, s);  // bounded values in every repetition
+      cudaEventRecord(e0, s);
+      const int cur = tmul::launch_fft(e, bufs, 0, -1, 2, M, s);
+      tmul::launch_fft(e, bufs, cur, 1, 1, M, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = TM_ECUDA; break; }
+      float x = 0;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (rep) t.push_back(x);
+    }
+    cudaFree(e.tw);
+    if (rc) break;
+    std::sort(t.begin(), t.end());
+    ms[c] = t[t.size() / 2];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (rc == TM_OK && cudaGetLastError() != cudaSuccess) rc = TM_ECUDA;
+  if (rc) return rc;
+  size_t best = 0;
+  for (size_t c = 1; c < ms.size(); ++c)
+    if (ms[c] < ms[best]) best = c;
+  out->candidates = int32_t(plans.size());
+  out->points = shapes[best].points;
+  out->split = shapes[best].split;
+  out->passes = shapes[best].passes;
+  out->npass = plans[best].npass;
+  out->ms_default = ms[0];
+  out->ms_best = ms[best];
+  {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    const auto key = std::make_pair(dev, M);
+    if (best == 0) tmul::g_tuned.erase(key);
+    else tmul::g_tuned[key] = shapes[best];
+    // plans of this length built before now keep their layout for their holders;
+    // the cache rebuilds them with the chosen one
+    for (auto it = tmul::g_plans.begin(); it != tmul::g_plans.end();) {
+      if (std::get<0>(it->first) == dev && std::get<3>(it->first) == p.N &&
+          std::get<4>(it->first) == 0) {
+        tmul::g_retired.push_back(it->second);
+        it = tmul::g_plans.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  return TM_OK;
+}
+
 int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep) {
   if (!rep) return TM_EINVAL;
   tmul::PlanParams p;
   int rc = tmul::get_params(kind, n_bits, &p);
   if (rc) return rc;
+  // the layout a product would use: the tuned one for this device, if any
+  tmul::FftShape shape;
+  bool tuned = false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    auto t = tmul::g_tuned.find(std::make_pair(dev, p.N / 2));
+    if (t != tmul::g_tuned.end()) { shape = t->second; tuned = true; }
+  } else {
+    (void)cudaGetLastError();
+  }
   tmul::FftPlan f;
-  rc = tmul::make_fft_plan(p.N / 2, &f);
+  rc = tmul::make_fft_plan(p.N / 2, &f, false, tuned ? &shape : nullptr);
   if (rc) return rc;
   tmul::fill_plan_report(p, f, rep);
   return TM_OK;
@@ -936,6 +1065,13 @@ int tm_release(void) {
       ++it;
     }
   }
+  for (auto& r : tmul::g_retired) {
+    cudaFree(r->tw); cudaFree(r->fwd_tab); cudaFree(r->bwd_tab); cudaFree(r->bwd_tab2);
+    cudaFree(r->small);
+    r->tw = nullptr; r->fwd_tab = nullptr; r->bwd_tab = nullptr; r->bwd_tab2 = nullptr;
+    r->small = nullptr;
+  }
+  tmul::g_retired.clear();
   for (auto it = tmul::g_ws.begin(); it != tmul::g_ws.end();) {
     if (it->first.first == dev) {
       cudaFree(it->second.base);

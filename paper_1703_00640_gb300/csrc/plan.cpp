@@ -365,12 +365,11 @@ void radices_of(int L, FftPass* p) {
   if (twos) p->radix[p->nstages++] = 2;
 }
 
-void shape(FftPass* p, int64_t ctas_wanted) {
-  // sequences per CTA: fill about kPoints points (1024 measured best against 512,
-  // 2048 and 4096 at M = 2^20), keeping >= ctas_wanted CTAs; one radix-4
-  // butterfly per thread
-  constexpr int kPoints = 1024;
-  int C = std::max(1, kPoints / p->L);
+void shape(FftPass* p, int64_t ctas_wanted, int points) {
+  // sequences per CTA: fill about `points` points (default 1024, measured best
+  // against 512, 2048 and 4096 at M = 2^20; the autotuner tries others), keeping
+  // >= ctas_wanted CTAs; one radix-4 butterfly per thread
+  int C = std::max(1, points / p->L);
   while (C > 1 && (p->Q + C - 1) / C < ctas_wanted) C /= 2;
   C = int(std::min<int64_t>(C, p->Q));
   while (int64_t(C) * p->L > kMaxCL) --C;
@@ -381,7 +380,8 @@ void shape(FftPass* p, int64_t ctas_wanted) {
 
 }  // namespace
 
-int make_fft_plan(int64_t M, FftPlan* out, bool single) {
+int make_fft_plan(int64_t M, FftPlan* out, bool single, const FftShape* shape_in) {
+  const FftShape sh = shape_in ? *shape_in : FftShape{};
   FftPlan f;
   f.M = M;
   std::vector<int> primes;
@@ -390,15 +390,22 @@ int make_fft_plan(int64_t M, FftPlan* out, bool single) {
     while (rest % p == 0) { primes.push_back(p); rest /= p; }
   if (rest != 1) return TM_EINVAL;
   int np = single ? 1 : (M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3));
+  if (!single && M > 64 && (sh.passes == 2 || sh.passes == 3)) np = sh.passes;
   int64_t Ls[kMaxPasses] = {1, 1, 1};
-  for (int p : primes) {       // largest primes first, each to the smallest factor
+  for (int p : primes) {
     int best = 0;
-    for (int i = 1; i < np; ++i)
-      if (Ls[i] < Ls[best]) best = i;
+    if (p != 2 && sh.split == 1) {
+      best = 0;                             // odd primes to the first pass
+    } else if (p != 2 && sh.split == 2) {
+      best = np - 1;                        // odd primes to the last pass
+    } else {                                // largest first, each to the shortest
+      for (int i = 1; i < np; ++i)
+        if (Ls[i] < Ls[best]) best = i;
+    }
     Ls[best] *= p;
   }
   for (int i = 0; i < np; ++i)
-    if (Ls[i] > kMaxSubLen) return TM_ERANGE;
+    if (Ls[i] > kMaxSubLen || (np > 1 && Ls[i] < 2)) return TM_ERANGE;
   f.npass = np;
   const int64_t want = 2 * 152;
   if (np == 1) {
@@ -426,7 +433,7 @@ int make_fft_plan(int64_t M, FftPlan* out, bool single) {
   }
   for (int i = 0; i < np; ++i) {
     radices_of(f.pass[i].L, &f.pass[i]);
-    shape(&f.pass[i], want);
+    shape(&f.pass[i], want, std::max(32, sh.points));
   }
   *out = f;
   return TM_OK;
@@ -537,7 +544,7 @@ int make_fft_plan_noalloc(int64_t M, FftPlan* out) {
   }
   for (int i = 0; i < np; ++i) {
     radices_of(f.pass[i].L, &f.pass[i]);
-    shape(&f.pass[i], 2 * 152);
+    shape(&f.pass[i], 2 * 152, 1024);
   }
   *out = f;
   return TM_OK;

@@ -56,10 +56,22 @@ struct PlanParams {
 // Chooses (b, N, lambda) for kind and n; returns 0 or a TM_E* code.
 int choose_params(int kind, uint64_t n, PlanParams* out);
 
+// Layout choices of the FFT passes that the autotuner varies: points a CTA aims to
+// hold (sequences per CTA = points / L), how the odd primes of M are distributed
+// over the passes (0: each prime to the currently shortest pass, largest primes
+// first; 1: all odd primes to the first pass; 2: all to the last pass), and the
+// number of passes (0: 1 up to M = 64, 2 up to M = 2^22, else 3).
+struct FftShape {
+  int points = 1024;
+  int split = 0;
+  int passes = 0;
+};
+
 // Splits the complex length M into at most kMaxPasses sub-FFT passes and picks
 // their radices and launch shapes. Twiddle offsets are left for the caller.
 // single = true: one sub-FFT of length M (M <= kMaxSubLen), for CTA-resident products.
-int make_fft_plan(int64_t M, FftPlan* out, bool single = false);
+// Returns TM_ERANGE / TM_EINVAL when `shape` cannot lay out M.
+int make_fft_plan(int64_t M, FftPlan* out, bool single = false, const FftShape* shape = nullptr);
 
 // The same two plans computed without any heap allocation (for the entry point
 // whose callers cannot allocate): identical choice of (b, N, lambda); the FFT

@@ -201,3 +201,20 @@ def test_square_with_host_buffers(pkg):
         assert rep["status"] == 0
         d, _ = pkg.mul(kind, dev(u), dev(u), n)
         assert np.array_equal(out, host(d))
+
+
+@pytest.mark.parametrize("n", [100003, 1 << 20])
+def test_autotuned_layout_keeps_results(pkg, n):
+    """tm_autotune only changes the FFT pass layout: products after it equal the
+    oracle and the products before it, limb for limb."""
+    u, v = workloads.pattern_limbs("random", n, seed=57)
+    du, dv = dev(u), dev(v)
+    before = {k: host(pkg.mul(k, du, dv, n)[0]) for k in ("lo", "hi", "full")}
+    for k in ("lo", "hi", "full"):
+        t = pkg.autotune(k, n)
+        assert t["candidates"] >= 1 and 0 < t["ms_best"] <= t["ms_default"]
+    for k in ("lo", "hi", "full"):
+        out, rep = pkg.mul(k, du, dv, n)
+        assert rep["status"] == 0
+        assert np.array_equal(host(out), before[k])
+        _check(k, out, _expect(k, u, v, n), u, v, n)

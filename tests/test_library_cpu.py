@@ -52,6 +52,18 @@ def test_report_layout_matches_header(tmp_path, pkg):
                                   R.table_bytes.offset)
 
 
+def test_tune_layout_matches_header(tmp_path, pkg):
+    src = tmp_path / "tune.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "truncmul.h"\n'
+                   'int main(void){printf("%zu %zu %zu\\n", sizeof(tm_tune),'
+                   ' offsetof(tm_tune, ms_default), offsetof(tm_tune, ms_best)); return 0;}\n')
+    exe = tmp_path / "tune"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    size, od, ob = map(int, subprocess.check_output([str(exe)], text=True).split())
+    T = pkg.Tune
+    assert (size, od, ob) == (ctypes.sizeof(T), T.ms_default.offset, T.ms_best.offset)
+
+
 NS = [1, 2, 7, 63, 64, 65, 100, 999, 1000, 4096, 5000, 65536, 100003, 2**20, 10**6, 2**24,
       21544346, 2**28]
 
@@ -78,6 +90,9 @@ def test_host_side_errors(pkg):
     # null operands are rejected before any CUDA call
     assert lib.tm_mul(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_lo(None, None, None, 0, None, None) == pkg.TM_EINVAL
+    assert lib.tm_autotune(1, 100, None, None) == pkg.TM_EINVAL
+    assert lib.tm_autotune(5, 100, None, ctypes.byref(pkg.Tune())) == pkg.TM_EINVAL
+    assert lib.tm_autotune(1, (1 << 31) + 1, None, ctypes.byref(pkg.Tune())) == pkg.TM_ERANGE
     assert lib.tm_mul_adaptive(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_adaptive(9, fake_ptr := ctypes.c_void_p(0x1000), fake_ptr, fake_ptr, 100,
                                None, None) == pkg.TM_EINVAL
