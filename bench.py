@@ -46,6 +46,8 @@ def parse():
                     help="run the served-stream configuration instead of the default")
     ap.add_argument("--served-count", type=int, default=20000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run the batched configuration alone (graph launches)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the square / kept-operand timings")
     ap.add_argument("--no-division", action="store_true",
@@ -194,10 +196,11 @@ def run_reference(args):
 
 # ------------------------------------------------------------ batched configuration
 
-def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
+def run_batched(pkg, torch, np, count, steps, warmup, stream, seed, compare=True):
     """count products, n log-uniform in [2^12, 2^20] bits, half low / half high,
     uniform random operands: one graph launch (tm_batch_launch) per step against
-    `count` individual tm_mul launches per step, both timed with CUDA events."""
+    `count` individual tm_mul launches per step, both timed with CUDA events
+    (compare=False: the graph launches alone)."""
     import workloads
     sizes = workloads.log_uniform_sizes(count, 12, 20, seed=seed)
     items = []
@@ -213,18 +216,20 @@ def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
     ref = [torch.empty_like(it[2]) for it in items]
     for _ in range(max(1, warmup)):
         batch.launch(stream)
-        for it, r in zip(items, ref):
-            pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
+        if compare:
+            for it, r in zip(items, ref):
+                pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
     torch.cuda.synchronize()
-    same = all(torch.equal(it[2], r) for it, r in zip(items, ref))
+    same = all(torch.equal(it[2], r) for it, r in zip(items, ref)) if compare else None
     g_ms, p_ms = [], []
     for _ in range(steps):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         batch.launch(stream)
         e1.record(stream)
-        for it, r in zip(items, ref):
-            pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
+        if compare:
+            for it, r in zip(items, ref):
+                pkg.mul(it[0], it[3], it[4], it[1], out=r, stream=stream, report=False)
         e2.record(stream)
         e2.synchronize()
         g_ms.append(e0.elapsed_time(e1))
@@ -234,6 +239,8 @@ def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
     batch.close()
     bits = float(sum(int(n) for n in sizes))
     med_g, med_p = float(np.median(g_ms)), float(np.median(p_ms))
+    if not compare:
+        med_p = float("nan")
     return {
         "products": count, "n_bits": "log-uniform in [2^12, 2^20]", "kinds": "50/50 low/high",
         "graph_launch_ms": {"p50": med_g, "p99": float(np.percentile(g_ms, 99))},
@@ -241,7 +248,8 @@ def run_batched(pkg, torch, np, count, steps, warmup, stream, seed):
         "products_per_s": count / (med_g * 1e-3),
         "gbit_s": bits / (med_g * 1e-3) / 1e9,
         "speedup_vs_per_product_launches": med_p / med_g,
-        "bit_exact_vs_single": bool(same), "status": st["rc"], "margin": st["margin"],
+        "bit_exact_vs_single": bool(same) if compare else None, "status": st["rc"],
+        "margin": st["margin"],
     }
 
 
@@ -594,12 +602,30 @@ def run_cuda(args):
         dist.destroy_process_group()
 
 
+def run_batched_only(args):
+    """The batched configuration alone (graph launches, no per-product comparison):
+    one JSON line, for profiling the batch."""
+    import numpy as np
+    import torch
+    import paper_1703_00640_gb300 as pkg
+    pkg.build()
+    pkg.load()
+    stream = torch.cuda.current_stream()
+    res = run_batched(pkg, torch, np, args.batch_count, args.steps, args.warmup, stream, seed=4,
+                      compare=False)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": res["gbit_s"],
+                      "batched": res, "n_gpus": 1, "dtype": "f64", "data": "synthetic"}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.served:
         run_served(args)
+    elif args.batched_only:
+        run_batched_only(args)
     else:
         run_cuda(args)
 

@@ -16,7 +16,7 @@
 namespace tmul {
 namespace {
 
-constexpr int kBranches = 4;   // concurrent graph branches
+constexpr int kBranches = 12;  // concurrent graph branches
 
 #define TB_CHECK(x)                                    \
   do {                                                 \
@@ -370,16 +370,26 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
       cudaMemsetAsync(sa.counter, 0, sizeof(int), cs[0]);
       launch_small(sa, std::min(sa.count, 152), B->small_smem, cs[0]);
     }
-    // largest groups first, round robin over the branches
+    // largest groups first, each to the branch with the least estimated work so far
+    // (longest-processing-time order); work ~ products x N (log2 N + 8)
+    auto work = [](double N, double count) { return count * N * (std::log2(N) + 8.0); };
+    double load[kBranches] = {};
+    if (sa.count > 0)
+      for (const SmallItem& it : small_items) load[0] += work(double(B->small_plans[it.plan].N), 1.0);
     std::vector<size_t> order(B->groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-      return B->groups[x].members.size() * B->groups[x].p.N >
-             B->groups[y].members.size() * B->groups[y].p.N;
+      return work(double(B->groups[x].p.N), double(B->groups[x].members.size())) >
+             work(double(B->groups[y].p.N), double(B->groups[y].members.size()));
     });
-    for (size_t i = 0; i < order.size() && rc == TM_OK; ++i)
-      rc = enqueue_group(B.get(), B->groups[order[i]],
-                         cs[sa.count > 0 ? 1 + i % (kBranches - 1) : i % kBranches]);
+    for (size_t i = 0; i < order.size() && rc == TM_OK; ++i) {
+      int br = 0;
+      for (int j = 1; j < kBranches; ++j)
+        if (load[j] < load[br]) br = j;
+      const Group& g = B->groups[order[i]];
+      load[br] += work(double(g.p.N), double(g.members.size()));
+      rc = enqueue_group(B.get(), g, cs[br]);
+    }
     for (int i = 1; i < kBranches; ++i) {
       cudaEventRecord(join[i], cs[i]);
       cudaStreamWaitEvent(cs[0], join[i], 0);
