@@ -467,9 +467,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
 // F' = F mod C: F'_i = F_i + kappa_i F_N (eq. 4.5), then
 // U~_j = sum_{r<lam} gamma_{(j-r) mod N, r} F'_{(j-r) mod N}, and
 // theta = rho^-N F(rho) = sum_j rho^-j F_(N-j).
-// Outputs that read a kappa-corrected F'_i (j < nkappa + lam - 1, all in the
-// first tile) are evaluated in FP64; the others read integer digits only and use
-// the fixed-point form of the low product's map.
+// Outputs that read a kappa-corrected F'_i or wrap around (j < nkappa + lam - 1,
+// all in the first tile) are evaluated in FP64; the others read integer digits
+// only and use the fixed-point form of the low product's map.
 __device__ __forceinline__ double fx_coef(const long long* tab, long long N, int r, long long k,
                                           int Q, int b) {
   return scale2(__ll2double_rn(__ldg(tab + (long long)(r - 1) * N + k)), -(Q + r * b));
@@ -526,10 +526,11 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     }
     __syncthreads();
   }
+  const long long head_end = head ? (long long)a.nkappa + a.lam - 1 : 0;
   for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= N) break;
-    if (head) {
+    if (j < head_end) {             // reads a kappa-corrected F'_i or wraps: FP64
       double su = fu[t + halo], sv = fv[t + halo];
       for (int r = 1; r < a.lam; ++r) {
         long long k = j - r;
