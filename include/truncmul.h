@@ -137,7 +137,12 @@ int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* 
 /*
  * tm_mul_host: one product with HOST buffers. Copies u and v to the device
  * (once when u_host == v_host, which squares), runs tm_mul on `stream`, copies
- * the result back and waits for the stream.
+ * the result back and waits for the stream. On a created stream (not NULL, the
+ * legacy or the per-thread default stream) the whole sequence is recorded once
+ * per (stream, kind, n_bits) as a CUDA graph, and later calls re-point its three
+ * host copies at the new buffers and launch it (one launch instead of about
+ * twenty calls); the recording is redone when the library's buffers for that
+ * stream change, and skipped when it cannot be made (pageable host buffers).
  * Page-locked host buffers give the fastest copies; pageable ones work.
  * Limb counts as above. Returns like tm_mul; *rep (optional) is filled.
  */

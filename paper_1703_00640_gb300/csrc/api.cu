@@ -28,6 +28,26 @@ std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 std::map<std::pair<int, int64_t>, FftShape> g_tuned;
 std::vector<std::shared_ptr<PlanEntry>> g_retired;
 
+// tm_mul_host's whole sequence (copies in, product, copies out, status) recorded once
+// per (device, stream, kind, n, square) as a CUDA graph; later calls only point the
+// three host copies at the new buffers and launch it. Valid while the io buffer,
+// workspace and plan tables it was recorded with are the current ones.
+struct HostGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t in_u = nullptr, in_v = nullptr, out = nullptr;
+  char* io = nullptr;
+  char* ws_base = nullptr;
+  const PlanEntry* pe = nullptr;
+};
+std::map<std::tuple<int, cudaStream_t, int, uint64_t, bool>, HostGraph> g_host_graphs;
+
+void drop_host_graph(HostGraph& h) {
+  if (h.exec) cudaGraphExecDestroy(h.exec);
+  if (h.graph) cudaGraphDestroy(h.graph);
+  h = HostGraph{};
+}
+
 int cuda_fail(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return TM_ENOMEM;
   return e == cudaSuccess ? TM_OK : TM_ECUDA;
@@ -724,10 +744,6 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   uint64_t* dv = reinterpret_cast<uint64_t*>(io + tmul::align_up(in_bytes));
   uint64_t* dout = reinterpret_cast<uint64_t*>(io + 2 * tmul::align_up(in_bytes));
   if (u_host == v_host) dv = du;              // a square: one copy, the squaring path
-  if (cudaMemcpyAsync(du, u_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      (dv != du &&
-       cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess))
-    return TM_ECUDA;
   tmul::PlanParams p;
   rc = tmul::get_params(kind, n_bits, &p);
   if (rc) return rc;
@@ -737,15 +753,92 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   tmul::Workspace* ws = nullptr;
   rc = tmul::get_workspace(s, tmul::workspace_bytes(p), &ws);
   if (rc) return rc;
-  rc = tmul::enqueue(kind, dout, du, dv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
-  if (rc) return rc;
-  // result, status word and its reset in stream order: one wait for all of it
-  if (cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
-                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return TM_ECUDA;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
+  const bool square = dv == du;
+  // the recorded sequence, if this stream has one for (kind, n) that is still valid
+  bool done = false;
+  if (s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    tmul::HostGraph& h = tmul::g_host_graphs[std::make_tuple(dev, s, kind, n_bits, square)];
+    if (h.exec && (h.io != io || h.ws_base != ws->base || h.pe != pe.get()))
+      tmul::drop_host_graph(h);
+    if (!h.exec) {
+      tmul::ensure_kernel_attributes();
+      bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool rec =
+            cudaMemcpyAsync(du, u_host, in_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            (square ||
+             cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) == cudaSuccess) &&
+            tmul::enqueue(kind, dout, du, dv, n_bits, s, p, *pe, *ws, nullptr, nullptr) ==
+                TM_OK &&
+            cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, s) ==
+                cudaSuccess &&
+            cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
+                            cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) == cudaSuccess;
+        cudaGraph_t g = nullptr;
+        ok = cudaStreamEndCapture(s, &g) == cudaSuccess && rec && g;
+        size_t count = 0;
+        if (ok) ok = cudaGraphGetNodes(g, nullptr, &count) == cudaSuccess;
+        std::vector<cudaGraphNode_t> nodes(count);
+        if (ok && count) ok = cudaGraphGetNodes(g, nodes.data(), &count) == cudaSuccess;
+        for (size_t i = 0; ok && i < count; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeMemcpy)
+            continue;
+          cudaMemcpy3DParms m{};
+          if (cudaGraphMemcpyNodeGetParams(nodes[i], &m) != cudaSuccess) { ok = false; break; }
+          if (m.dstPtr.ptr == du) h.in_u = nodes[i];
+          else if (m.dstPtr.ptr == dv) h.in_v = nodes[i];
+          else if (m.srcPtr.ptr == dout) h.out = nodes[i];
+        }
+        ok = ok && h.in_u && h.out && (square || h.in_v);
+        if (ok) ok = cudaGraphInstantiate(&h.exec, g, 0) == cudaSuccess;
+        if (ok) {
+          h.graph = g;
+          h.io = io;
+          h.ws_base = ws->base;
+          h.pe = pe.get();
+          // the recording did not run: run it now
+          done = cudaGraphLaunch(h.exec, s) == cudaSuccess;
+        } else {                       // e.g. pageable host buffers: no recording
+          if (g) cudaGraphDestroy(g);
+          h = tmul::HostGraph{};
+        }
+      }
+      (void)cudaGetLastError();
+    } else if (h.exec) {
+      done = cudaGraphExecMemcpyNodeSetParams1D(h.exec, h.in_u, du, u_host, in_bytes,
+                                                cudaMemcpyHostToDevice) == cudaSuccess &&
+             (square || cudaGraphExecMemcpyNodeSetParams1D(h.exec, h.in_v, dv, v_host, in_bytes,
+                                                           cudaMemcpyHostToDevice) ==
+                            cudaSuccess) &&
+             cudaGraphExecMemcpyNodeSetParams1D(h.exec, h.out, out_host, dout, out_bytes,
+                                                cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaGraphLaunch(h.exec, s) == cudaSuccess;
+      if (!done) {
+        (void)cudaGetLastError();
+        tmul::drop_host_graph(h);
+      }
+    }
+  }
+  if (!done) {
+    if (cudaMemcpyAsync(du, u_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (!square &&
+         cudaMemcpyAsync(dv, v_host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess))
+      return TM_ECUDA;
+    rc = tmul::enqueue(kind, dout, du, dv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
+    if (rc) return rc;
+    // result, status word and its reset in stream order: one wait for all of it
+    if (cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess)
+      return TM_ECUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TM_ECUDA;
   rc = ws->status_host->flags ? TM_EPRECISION : TM_OK;
   if (rep) {
     tmul::fill_plan_report(p, pe->fft, rep);
@@ -1065,6 +1158,8 @@ int tm_release(void) {
       ++it;
     }
   }
+  for (auto& kv : tmul::g_host_graphs) tmul::drop_host_graph(kv.second);
+  tmul::g_host_graphs.clear();
   for (auto& r : tmul::g_retired) {
     cudaFree(r->tw); cudaFree(r->fwd_tab); cudaFree(r->bwd_tab); cudaFree(r->bwd_tab2);
     cudaFree(r->small);

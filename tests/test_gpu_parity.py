@@ -154,3 +154,36 @@ def test_config_2_28(pkg):
     n = 2**28
     u, v = workloads.pattern_limbs("random", n, seed=28)
     _check_all(pkg, n, u, v, exact_hi=False)
+
+
+def test_host_buffers_on_a_stream_repeated(pkg):
+    """tm_mul_host on a created stream records its sequence once and then only points
+    the copies at new buffers: repeated calls with other (page-locked and pageable)
+    buffers, other kinds and sizes in between, all give the device path's limbs."""
+    import torch
+    s = torch.cuda.Stream()
+    n = 40000
+    for kind in ("lo", "hi", "full"):
+        for rep in range(3):
+            u, v = workloads.pattern_limbs("random", n, seed=300 + rep)
+            if rep == 1:      # page-locked host tensors
+                hu = torch.from_numpy(u.view(np.int64)).pin_memory()
+                hv = torch.from_numpy(v.view(np.int64)).pin_memory()
+                out = torch.empty(pkg.out_limbs(kind, n), dtype=torch.int64).pin_memory()
+                got, rep_d = pkg.mul_host(kind, hu, hv, n, out=out, stream=s)
+                got = got.numpy().view(np.uint64)
+            else:
+                got, rep_d = pkg.mul_host(kind, u, v, n, stream=s)
+            assert rep_d["status"] == 0
+            d, _ = pkg.mul(kind, dev(u), dev(v), n)
+            assert np.array_equal(got, host(d)), (kind, rep)
+            # another size on the same stream between the calls
+            a, b = workloads.pattern_limbs("random", 999, seed=rep)
+            pkg.mul_host("lo", a, b, 999, stream=s)
+    # squares through the same stream
+    u, _ = workloads.pattern_limbs("random", n, seed=310)
+    hu = torch.from_numpy(u.view(np.int64)).pin_memory()
+    for _ in range(2):
+        got, _ = pkg.mul_host("lo", hu, hu, n, stream=s)
+        d, _ = pkg.mul("lo", dev(u), dev(u), n)
+        assert np.array_equal(np.asarray(got).view(np.uint64), host(d))
