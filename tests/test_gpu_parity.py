@@ -187,3 +187,34 @@ def test_host_buffers_on_a_stream_repeated(pkg):
         got, _ = pkg.mul_host("lo", hu, hu, n, stream=s)
         d, _ = pkg.mul("lo", dev(u), dev(u), n)
         assert np.array_equal(np.asarray(got).view(np.uint64), host(d))
+
+
+def test_concurrent_streams(pkg):
+    """Products enqueued on three streams without waits between them (each stream has
+    its own workspace and side stream) equal the oracle."""
+    import torch
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    jobs = []
+    for i, s in enumerate(streams):
+        for j, kind in enumerate(("lo", "hi", "full")):
+            n = [30001, 65536, 200003][(i + j) % 3]
+            u, v = workloads.pattern_limbs("random", n, seed=400 + 3 * i + j)
+            with torch.cuda.stream(s):
+                du, dv = dev(u), dev(v)
+                out, _ = pkg.mul(kind, du, dv, n, stream=s, report=False)
+            jobs.append((kind, n, u, v, out, du, dv))
+    torch.cuda.synchronize()
+    for s in streams:
+        assert pkg.stream_status(s)["rc"] == 0
+    for kind, n, u, v, out, _, _ in jobs:
+        full = bigmul.mul_full(u, v, par_depth=3)
+        nl = (n + 63) // 64
+        if kind == "full":
+            assert np.array_equal(host(out), full)
+        elif kind == "lo":
+            lo = full[:nl].copy()
+            if n % 64:
+                lo[-1] &= np.uint64((1 << (n % 64)) - 1)
+            assert np.array_equal(host(out), lo)
+        else:
+            assert hi_ok(bigmul.to_int(host(out)), u, v, n, full=full)
