@@ -13,6 +13,34 @@
 
 namespace tmul {
 
+// Programmatic dependent launch (sm_90+): every kernel of the product pipeline lets
+// the next launch proceed as soon as all of its own CTAs have started
+// (griddepcontrol.launch_dependents), and waits for the previous kernel to complete
+// and its writes to be visible (griddepcontrol.wait) before it touches data that
+// kernel produced; only static tables are read before the wait. Kernels launched
+// without the attribute see both as no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// <<<grid, block, smem, s>>> with the programmatic-serialization attribute.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------ constants
 
 constexpr double kC5_1 = 0.30901699437494745;   // cos(2 pi/5)
@@ -305,7 +333,7 @@ void launch_digit_norms(const unsigned long long* u, const unsigned long long* v
 // Launches KERNEL<ROWS> with ROWS = rows for the map row counts the planner
 // produces (3..12 for b = 5..14), else KERNEL<0> (any count up to kMaxLam).
 #define TM_LAUNCH_ROWS(R, KERNEL, CFG, ARGS) \
-  case R: KERNEL<R><<<TM_UNPAREN CFG>>>(TM_UNPAREN ARGS); break;
+  case R: launch_pdl(KERNEL<R>, TM_UNPAREN CFG, TM_UNPAREN ARGS); break;
 #define TM_UNPAREN(...) __VA_ARGS__
 #define TM_ROWS_DISPATCH(rows, KERNEL, CFG, ARGS)                                     \
   switch (rows) {                                                                    \
@@ -314,7 +342,7 @@ void launch_digit_norms(const unsigned long long* u, const unsigned long long* v
     TM_LAUNCH_ROWS(7, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(8, KERNEL, CFG, ARGS)        \
     TM_LAUNCH_ROWS(9, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(10, KERNEL, CFG, ARGS)       \
     TM_LAUNCH_ROWS(11, KERNEL, CFG, ARGS) TM_LAUNCH_ROWS(12, KERNEL, CFG, ARGS)      \
-    default: KERNEL<0><<<TM_UNPAREN CFG>>>(TM_UNPAREN ARGS); break;                  \
+    default: launch_pdl(KERNEL<0>, TM_UNPAREN CFG, TM_UNPAREN ARGS); break;          \
   }
 
 constexpr int kFwdTile = 1024;
@@ -404,6 +432,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
     a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
     a.X = it.X; a.theta = it.theta;
   }
+  pdl_trigger();
+  pdl_wait();
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
   const bool two = !a.one_operand;
@@ -483,6 +513,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
     a.X = it.X; a.theta = it.theta;
   }
+  pdl_trigger();
+  pdl_wait();
   __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
   __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
   __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
@@ -819,9 +851,11 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   const int off4 = (C * L + 1) & ~1;    // 32-byte aligned
   Tan4* tw4s = reinterpret_cast<Tan4*>(smem + off4);
   double2* tws = smem + off4 + 2 * p.tw4_len;   // omega_L^k, k < L (when needed)
+  pdl_trigger();
   for (int t = threadIdx.x; t < p.tw4_len; t += blockDim.x) tw4s[t] = p.tw4[t];
   if (p.need_wL)
     for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = __ldg(p.tw_sub + t);
+  pdl_wait();                       // the plan's tables above; the data below
   const long long q0 = (long long)blockIdx.x * C;
   const long long boff = (long long)blockIdx.y * p.batch_stride;
   in += boff;
@@ -894,9 +928,9 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
                       (p.need_wL ? size_t(p.L) : 0)) * sizeof(double2);
   dim3 grid(blocks, batch);
   if (dir < 0)
-    k_fft_pass<-1><<<grid, threads, smem, s>>>(in, out, p);
+    launch_pdl(k_fft_pass<-1>, grid, dim3(threads), smem, s, in, out, p);
   else
-    k_fft_pass<1><<<grid, threads, smem, s>>>(in, out, p);
+    launch_pdl(k_fft_pass<1>, grid, dim3(threads), smem, s, in, out, p);
 }
 
 // ------------------------------------------------ twist + pointwise product
@@ -943,6 +977,8 @@ __global__ void k_twist(const double2* __restrict__ Zu, const double2* __restric
                         double2* __restrict__ Q, long long M,
                         const double2* __restrict__ tc, double two_over_N, long long zstride,
                         long long qstride) {
+  pdl_trigger();
+  pdl_wait();
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k > M / 2) return;
   twist_pair<SQ>(Zu + blockIdx.y * zstride, Zv + blockIdx.y * zstride, Q + blockIdx.y * qstride,
@@ -956,9 +992,11 @@ void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
   const dim3 grid(unsigned((n + 255) / 256), unsigned(batch));
   const double two_over_N = 2.0 / double(N);
   if (Zv == Zu)
-    k_twist<true><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, tc, two_over_N, zstride, qstride);
+    launch_pdl(k_twist<true>, grid, dim3(256), 0, s, Zu, Zv, Q, M, tc, two_over_N, zstride,
+               qstride);
   else
-    k_twist<false><<<grid, 256, 0, s>>>(Zu, Zv, Q, M, tc, two_over_N, zstride, qstride);
+    launch_pdl(k_twist<false>, grid, dim3(256), 0, s, Zu, Zv, Q, M, tc, two_over_N, zstride,
+               qstride);
 }
 
 // ------------------------------------------------ back maps and rounding
@@ -1001,6 +1039,8 @@ __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
     const BackItem it = a0.items[blockIdx.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
@@ -1073,6 +1113,8 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
     const BackItem it = a0.items[blockIdx.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   const long long N = a.N;
@@ -1194,6 +1236,8 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
     const BackItem it = a0.items[blockIdx.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
+  pdl_trigger();
+  pdl_wait();
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   __shared__ double P[kMaxLam];
@@ -1298,6 +1342,8 @@ __device__ void back_small_body(const BackArgs& a, int kind) {
 
 
 __global__ void k_back_small(BackArgs a0, int kind) {
+  pdl_trigger();
+  pdl_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   BackArgs a = a0;
   if (a0.items) {
@@ -1314,9 +1360,9 @@ void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
   if (blocks == 0) blocks = 1;
   const dim3 grid(blocks, unsigned(batch));
   if (kind == TM_FULL) {
-    k_back_full<<<grid, kBackThreads, 0, s>>>(a);
+    launch_pdl(k_back_full, grid, dim3(kBackThreads), 0, s, a);
   } else if (a.N <= 64 || a.N < 2 * a.lam + a.nkappa + 2) {
-    k_back_small<<<dim3(1, unsigned(batch)), 32, 0, s>>>(a, kind);
+    launch_pdl(k_back_small, dim3(1, unsigned(batch)), dim3(32), 0, s, a, kind);
   } else {
     const int rows = kind == TM_LO ? a.lam - 1 : a.lam;
     const dim3 tgrid(unsigned((a.N + kBackTile - 1) / kBackTile), unsigned(batch));
@@ -1440,6 +1486,8 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
   }
+  pdl_trigger();
+  pdl_wait();
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   if (blockIdx.x >= my_blocks) return;     // uniform per block
   __shared__ long long hs[kCarryThreads];
@@ -1469,6 +1517,8 @@ __global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
   }
+  pdl_trigger();
+  pdl_wait();
   const long long nblocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   const long long per = (nblocks + 1023) / 1024;
   const long long b0 = threadIdx.x * per;
@@ -1497,6 +1547,8 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
   }
+  pdl_trigger();
+  pdl_wait();
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
   if (blockIdx.x >= my_blocks) return;     // uniform per block
   const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
@@ -1523,9 +1575,9 @@ void launch_carry(const CarryArgs& a, int batch, cudaStream_t s) {
   const long long nblocks =
       a.items ? a.nblocks_max : (a.nS + kCarryThreads - 1) / kCarryThreads;
   const dim3 grid(static_cast<unsigned>(nblocks), static_cast<unsigned>(batch));
-  k_carry_local<<<grid, kCarryThreads, 0, s>>>(a);
-  k_carry_blocks<<<dim3(1, unsigned(batch)), 1024, 0, s>>>(a);
-  k_carry_apply<<<grid, kCarryThreads, 0, s>>>(a);
+  launch_pdl(k_carry_local, grid, dim3(kCarryThreads), 0, s, a);
+  launch_pdl(k_carry_blocks, dim3(1, unsigned(batch)), dim3(1024), 0, s, a);
+  launch_pdl(k_carry_apply, grid, dim3(kCarryThreads), 0, s, a);
 }
 
 
