@@ -119,6 +119,8 @@ __device__ __forceinline__ GP limb_gp(u64 x, u64 y) {
 
 // 1. carry behaviour of each block's limbs
 __global__ void __launch_bounds__(kLopThreads) k_lop_local(LopArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const bool neg = neg_of(a);
   const long long base = blockIdx.x * kLopTile + (long long)threadIdx.x * kLopPer;
   GP t{0u, 1u};
@@ -134,6 +136,8 @@ __global__ void __launch_bounds__(kLopThreads) k_lop_local(LopArgs a) {
 
 // 2. carry into every block (one CTA), the top limb's value and the condition
 __global__ void __launch_bounds__(kScanThreads) k_lop_scan(LopArgs a, long long nblk) {
+  pdl_trigger();
+  pdl_wait();
   const bool neg = neg_of(a);
   const unsigned cin0 = neg ? 1u : 0u;
   const long long per = (nblk + kScanThreads - 1) / kScanThreads;
@@ -181,6 +185,8 @@ __global__ void __launch_bounds__(kScanThreads) k_lop_scan(LopArgs a, long long 
 
 // 3. the limbs of the sum (or of keep)
 __global__ void __launch_bounds__(kLopThreads) k_lop_apply(LopArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const bool neg = neg_of(a);
   const bool ap = *a.applied != 0;
   const long long base = blockIdx.x * kLopTile + (long long)threadIdx.x * kLopPer;
@@ -236,6 +242,8 @@ __device__ __forceinline__ u64 field64(const u64* src, long long ns, long long s
 // to dst_bits bits; i < nd. dst must not overlap src.
 __global__ void k_bits(u64* dst, long long nd, long long dst_bits, const u64* src, long long ns,
                        long long src_bits, long long off, int invert) {
+  pdl_trigger();
+  pdl_wait();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= nd) return;
   u64 x = field64(src, ns, src_bits, 64 * i + off);
@@ -248,6 +256,8 @@ __global__ void k_bits(u64* dst, long long nd, long long dst_bits, const u64* sr
 
 // v (W limbs) := the p-bit two's complement value in its low p bits, sign-extended.
 __global__ void k_sext(u64* v, long long W, long long p) {
+  pdl_trigger();
+  pdl_wait();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= W) return;
   const bool sign = (v[(p - 1) / 64] >> ((p - 1) % 64)) & 1ull;   // bit p-1 is never rewritten
@@ -266,6 +276,8 @@ __global__ void k_sext(u64* v, long long W, long long p) {
 // division on one thread (every bit of the dividend is one).
 __global__ void k_recip_base(u64* X, long long nX, const u64* m, long long nm, long long k,
                              int h) {
+  pdl_trigger();
+  pdl_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const u64 mh = field64(m, nm, k, k - h) & ((1ull << h) - 1ull);
   u64 rem = 0, q = 0;
@@ -330,19 +342,20 @@ struct Limbs {
   void bits(u64* dst, long long nd, long long dst_bits, const u64* src, long long ns,
             long long src_bits, long long off, bool invert = false) const {
     const unsigned grid = unsigned((nd + 255) / 256);
-    k_bits<<<grid, 256, 0, s>>>(dst, nd, dst_bits, src, ns, src_bits, off, invert ? 1 : 0);
+    launch_pdl(k_bits, dim3(grid), dim3(256), 0, s, dst, nd, dst_bits, src, ns, src_bits, off,
+               invert ? 1 : 0);
   }
   void sext(u64* v, long long W, long long p) const {
-    k_sext<<<unsigned((W + 255) / 256), 256, 0, s>>>(v, W, p);
+    launch_pdl(k_sext, dim3(unsigned((W + 255) / 256)), dim3(256), 0, s, v, W, p);
   }
   void lop(LopArgs a) const {
     const long long nblk = (a.W + kLopTile - 1) / kLopTile;
     a.blk = blk;
     a.bcin = bcin;
     a.applied = applied;
-    k_lop_local<<<unsigned(nblk), kLopThreads, 0, s>>>(a);
-    k_lop_scan<<<1, kScanThreads, 0, s>>>(a, nblk);
-    k_lop_apply<<<unsigned(nblk), kLopThreads, 0, s>>>(a);
+    launch_pdl(k_lop_local, dim3(unsigned(nblk)), dim3(kLopThreads), 0, s, a);
+    launch_pdl(k_lop_scan, dim3(1), dim3(kScanThreads), 0, s, a, nblk);
+    launch_pdl(k_lop_apply, dim3(unsigned(nblk)), dim3(kLopThreads), 0, s, a);
   }
 };
 

@@ -13,34 +13,6 @@
 
 namespace tmul {
 
-// Programmatic dependent launch (sm_90+): every kernel of the product pipeline lets
-// the next launch proceed as soon as all of its own CTAs have started
-// (griddepcontrol.launch_dependents), and waits for the previous kernel to complete
-// and its writes to be visible (griddepcontrol.wait) before it touches data that
-// kernel produced; only static tables are read before the wait. Kernels launched
-// without the attribute see both as no-ops.
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// <<<grid, block, smem, s>>> with the programmatic-serialization attribute.
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 // ------------------------------------------------------------ constants
 
 constexpr double kC5_1 = 0.30901699437494745;   // cos(2 pi/5)
