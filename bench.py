@@ -54,6 +54,14 @@ def parse():
                     help="skip the division timings")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT layouts (no tm_autotune before timing)")
+    ap.add_argument("--large-bits", type=int, default=1 << 28,
+                    help="operand size of the large single-product section")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large single-product section")
+    ap.add_argument("--large-only", action="store_true",
+                    help="run the large single-product section alone")
+    ap.add_argument("--large-kinds", default="lo,hi,full",
+                    help="products of the large section (comma list of lo, hi, full)")
     return ap.parse_args()
 
 
@@ -562,6 +570,12 @@ def run_cuda(args):
                             "corrections; reciprocal by Newton iteration, host-timed "
                             "(it waits for the stream)"}
 
+    large = None
+    if not args.no_large:
+        large = run_large(pkg, torch, np, workloads, args.large_bits,
+                          max(3, min(args.steps, 10)), args.warmup, stream, flush,
+                          seed=28 + rank)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(pkg, torch, np, args.batch_count, max(3, min(args.steps, 10)),
@@ -608,6 +622,7 @@ def run_cuda(args):
                              "against the measured DFMA issue ceiling; traffic = ncu DRAM "
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
+        "large": large,
         "autotune": tuned,
         "square_and_kept_operand": variants,
         "division": division,
@@ -622,6 +637,114 @@ def run_cuda(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _as_int(t) -> int:
+    """A device or host tensor of little-endian uint64 limbs (stored as int64) as an int."""
+    return int.from_bytes(t.cpu().numpy().tobytes(), "little")
+
+
+def run_large(pkg, torch, np, workloads, n, reps, warmup, stream, flush, seed,
+              kinds=("lo", "hi", "full")):
+    """Single low, high and full products at a large n (2^28 bits by default: 32 MiB
+    operands, transforms of 2-3 x 10^7 complex points, far above L2, so the FFT
+    passes stream through HBM). Per kind: device time (CUDA events, L2 flushed),
+    Gbit/s, the FFT phases' algorithmic HBM bytes (passes x read + write x 16 B per
+    complex point, three transforms) over their time, their FP64 rate in the
+    conventional 5 M log2 M count, the largest rounding distance (margin) against
+    the bound e_max, and the data-dependent digit size's time. The low product is
+    checked against the full product's low n bits and the high product against the
+    two admissible values floor(uv / 2^n) and floor(uv / 2^n) + 1."""
+    u_np, v_np = workloads.pattern_limbs("random", n, seed=seed)
+    u = torch.from_numpy(u_np.view(np.int64)).cuda()
+    v = torch.from_numpy(v_np.view(np.int64)).cuda()
+    kinds = list(kinds)
+    outs = {k: torch.empty(pkg.out_limbs(k, n), dtype=torch.int64, device="cuda") for k in kinds}
+    reps_margin = {}
+    for k in kinds:
+        _, rep = pkg.mul(k, u, v, n, out=outs[k], stream=stream)
+        assert rep["status"] == 0, rep
+        reps_margin[k] = rep
+    checks = {}
+    if "full" in kinds:
+        full = _as_int(outs["full"])
+        if "lo" in kinds:      # a mask, not %: Python's division is quadratic in the size
+            checks["lo_equals_full_low_bits"] = _as_int(outs["lo"]) == full & ((1 << n) - 1)
+        if "hi" in kinds:
+            w = _as_int(outs["hi"])
+            checks["hi_admissible"] = w in (full >> n, (full >> n) + 1)
+
+    def timed(fn):
+        ev = []
+        for i in range(warmup + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            if i >= warmup:
+                ev.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    res = {}
+    for k in kinds:
+        ms = timed(lambda: pkg.mul(k, u, v, n, out=outs[k], stream=stream, report=False))
+        ph = [[] for _ in range(pkg.NPHASES)]
+        for _ in range(reps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(pkg.NPHASES + 1)]
+            for x in e:
+                x.record(stream)
+            pkg.mul_events(k, u, v, n, e, out=outs[k], stream=stream)
+            torch.cuda.synchronize()
+            for i in range(pkg.NPHASES):
+                ph[i].append(e[i].elapsed_time(e[i + 1]))
+        phases = {pkg.PHASES[i]: round(statistics.median(ph[i]), 4) for i in range(pkg.NPHASES)}
+        rep = reps_margin[k]
+        M = rep["N"] // 2
+        fft_ms = phases["fwd_fft"] + phases["inv_fft"]
+        fft_bytes = 3 * rep["fft_passes"] * 2 * 16 * M
+        ams = timed(lambda: pkg.mul_adaptive(k, u, v, n, out=outs[k], stream=stream,
+                                             report=False))
+        _, arep = pkg.mul_adaptive(k, u, v, n, out=outs[k], stream=stream)
+        assert arep["status"] == 0, arep
+        res[k] = {"ms": ms, "gbit_s": n / (ms * 1e-3) / 1e9,
+                  "plan": {x: rep[x] for x in ("b", "N", "lam_fwd", "lam_bwd", "fft_passes")},
+                  "margin": rep["margin"], "e_max": rep["e_max"],
+                  "phases_ms": phases,
+                  "fft_hbm_gb_s": fft_bytes / (fft_ms * 1e-3) / 1e9,
+                  "fft_fp64_tflops": 3 * 5.0 * M * np.log2(M) / (fft_ms * 1e-3) / 1e12,
+                  "adaptive": {"ms": ams, "b": arep["b"], "N": arep["N"],
+                               "margin": arep["margin"], "e_max": arep["e_max"]}}
+    for k in ("lo", "hi"):
+        if k in kinds and "full" in kinds:
+            res[k]["t_over_full"] = res[k]["ms"] / res["full"]["ms"]
+            res[k]["adaptive"]["t_over_full"] = (res[k]["adaptive"]["ms"] /
+                                                 res["full"]["adaptive"]["ms"])
+    return {"n_bits": n, "operands": "uniform random uint64 limbs (seeded PCG64)",
+            "l2": "flushed (256 MB write) before every product", "reps": reps,
+            **checks, "fp64_peak_tflops": FP64_PEAK_TFLOPS, **res}
+
+
+def run_large_only(args):
+    """The large single-product section alone: one JSON line."""
+    import numpy as np
+    import torch
+    import paper_1703_00640_gb300 as pkg
+    import workloads
+    pkg.build()
+    pkg.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    kinds = [k for k in args.large_kinds.split(",") if k]
+    res = run_large(pkg, torch, np, workloads, args.large_bits, max(3, min(args.steps, 10)),
+                    args.warmup, stream, flush, seed=28, kinds=kinds)
+    trunc = [res[k]["ms"] for k in ("lo", "hi") if k in kinds]
+    value = len(trunc) * args.large_bits / (sum(trunc) * 1e-3) / 1e9 if trunc else None
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": value,
+                      "large": res, "n_gpus": 1, "dtype": "f64", "data": "synthetic"}),
+          flush=True)
 
 
 def run_batched_only(args):
@@ -648,6 +771,8 @@ def main():
         run_served(args)
     elif args.batched_only:
         run_batched_only(args)
+    elif args.large_only:
+        run_large_only(args)
     else:
         run_cuda(args)
 
