@@ -372,6 +372,19 @@ typedef struct tm_tune {
 int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out);
 
 /*
+ * tm_set_layout: makes a layout (points, split and passes of *layout, as
+ * tm_autotune reports them; the other fields are ignored) the FFT pass layout of
+ * every later plan with the transform length of (kind, n_bits) on the current
+ * device, without timing anything: a layout chosen by tm_autotune in an earlier
+ * process can be reapplied. points, split and passes as in tm_tune (points
+ * 32..4096); points 1024, split 0, passes 0 is the default layout.
+ * Results do not depend on the layout. Errors: TM_EINVAL (bad kind, n_bits = 0,
+ * null layout or a field out of range), TM_ERANGE (n_bits too large, or no valid
+ * pass split of the length with that many passes), TM_ECUDA (no device).
+ */
+int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
+
+/*
  * tm_plan_query: the plan the library uses for (kind, n_bits), without any
  * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, e_max and
  * workspace_bytes of *rep. Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.

@@ -65,7 +65,7 @@ EXPORTS = ["tm_mul", "tm_mul_adaptive", "tm_mul_full", "tm_mul_lo", "tm_mul_hi",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
-           "tm_autotune", "tm_operand_create", "tm_mul_operand", "tm_operand_destroy",
+           "tm_autotune", "tm_set_layout", "tm_operand_create", "tm_mul_operand", "tm_operand_destroy",
            "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
@@ -123,6 +123,8 @@ def load(path: str = None):
     lib.tm_operand_destroy.argtypes = [P]
     lib.tm_autotune.argtypes = [ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(Tune)]
     lib.tm_autotune.restype = ctypes.c_int
+    lib.tm_set_layout.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Tune)]
+    lib.tm_set_layout.restype = ctypes.c_int
     lib.tm_reciprocal.argtypes = [P, P, ctypes.c_uint64, P]
     lib.tm_barrett_create.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_void_p)]
     lib.tm_barrett_divrem.argtypes = [P, P, P, P, P, R]
@@ -349,6 +351,16 @@ def autotune(kind, n_bits: int, stream=None) -> dict:
     if rc:
         raise TruncMulError(rc, "tm_autotune")
     return t.as_dict()
+
+
+def set_layout(kind, n_bits: int, points: int = 1024, split: int = 0, passes: int = 0):
+    """tm_set_layout: make a layout (as autotune reports it) the FFT pass layout of
+    later plans with the transform length of (kind, n); the defaults restore the
+    default layout."""
+    t = Tune(points=points, split=split, passes=passes)
+    rc = load().tm_set_layout(_kind(kind), int(n_bits), ctypes.byref(t))
+    if rc:
+        raise TruncMulError(rc, "tm_set_layout")
 
 
 def reciprocal(m, k_bits: int, out=None, stream=None):

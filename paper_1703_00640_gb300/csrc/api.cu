@@ -28,6 +28,25 @@ std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 std::map<std::pair<int, int64_t>, FftShape> g_tuned;
 std::vector<std::shared_ptr<PlanEntry>> g_retired;
 
+// Makes `shape` (nullptr: the default) the layout of every later plan of
+// transform length N on device `dev`. Plans of that length built before keep
+// their layout for their holders (batches); the cache rebuilds them.
+void apply_layout(int dev, int64_t N, const FftShape* shape) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const auto key = std::make_pair(dev, N / 2);
+  if (!shape) g_tuned.erase(key);
+  else g_tuned[key] = *shape;
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    if (std::get<0>(it->first) == dev && std::get<3>(it->first) == N &&
+        std::get<4>(it->first) == 0) {
+      g_retired.push_back(it->second);
+      it = g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 // tm_mul_host's whole sequence (copies in, product, copies out, status) recorded once
 // per (device, stream, kind, n, square) as a CUDA graph; later calls only point the
 // three host copies at the new buffers and launch it. Valid while the io buffer,
@@ -1084,23 +1103,34 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
   out->npass = plans[best].npass;
   out->ms_default = ms[0];
   out->ms_best = ms[best];
-  {
-    std::lock_guard<std::mutex> lk(tmul::g_mu);
-    const auto key = std::make_pair(dev, M);
-    if (best == 0) tmul::g_tuned.erase(key);
-    else tmul::g_tuned[key] = shapes[best];
-    // plans of this length built before now keep their layout for their holders;
-    // the cache rebuilds them with the chosen one
-    for (auto it = tmul::g_plans.begin(); it != tmul::g_plans.end();) {
-      if (std::get<0>(it->first) == dev && std::get<3>(it->first) == p.N &&
-          std::get<4>(it->first) == 0) {
-        tmul::g_retired.push_back(it->second);
-        it = tmul::g_plans.erase(it);
-      } else {
-        ++it;
-      }
-    }
+  tmul::apply_layout(dev, p.N, best == 0 ? nullptr : &shapes[best]);
+  return TM_OK;
+}
+
+int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout) {
+  if (!layout) return TM_EINVAL;
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  const tmul::FftShape sh{layout->points, layout->split, layout->passes};
+  if (sh.points < 32 || sh.points > 4096 || sh.split < 0 || sh.split > 2 ||
+      (sh.passes != 0 && sh.passes != 2 && sh.passes != 3))
+    return TM_EINVAL;
+  tmul::PlanParams p;
+  int rc = tmul::get_params(kind, n_bits, &p);
+  if (rc) return rc;
+  tmul::FftPlan f;
+  rc = tmul::make_fft_plan(p.N / 2, &f, false, &sh);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TM_ECUDA;
   }
+  const tmul::FftShape def{};
+  const bool is_default = sh.points == def.points && sh.split == def.split &&
+                          sh.passes == def.passes;
+  tmul::apply_layout(dev, p.N, is_default ? nullptr : &sh);
   return TM_OK;
 }
 

@@ -93,6 +93,16 @@ def test_host_side_errors(pkg):
     assert lib.tm_autotune(1, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_autotune(5, 100, None, ctypes.byref(pkg.Tune())) == pkg.TM_EINVAL
     assert lib.tm_autotune(1, (1 << 31) + 1, None, ctypes.byref(pkg.Tune())) == pkg.TM_ERANGE
+    # layouts: checked before any CUDA call
+    good = pkg.Tune(points=512, split=0, passes=3)
+    assert lib.tm_set_layout(1, 100, None) == pkg.TM_EINVAL
+    assert lib.tm_set_layout(4, 100, ctypes.byref(good)) == pkg.TM_EINVAL
+    assert lib.tm_set_layout(1, 0, ctypes.byref(good)) == pkg.TM_EINVAL
+    assert lib.tm_set_layout(1, (1 << 31) + 1, ctypes.byref(good)) == pkg.TM_ERANGE
+    for bad in (dict(points=16), dict(points=8192), dict(split=3), dict(split=-1),
+                dict(passes=1), dict(passes=4)):
+        t = pkg.Tune(**{**dict(points=1024, split=0, passes=0), **bad})
+        assert lib.tm_set_layout(1, 1 << 20, ctypes.byref(t)) == pkg.TM_EINVAL, bad
     assert lib.tm_mul_adaptive(1, None, None, None, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_mul_adaptive(9, fake_ptr := ctypes.c_void_p(0x1000), fake_ptr, fake_ptr, 100,
                                None, None) == pkg.TM_EINVAL
