@@ -135,15 +135,20 @@ int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* 
                     uint64_t n_bits, void* stream, tm_report* rep);
 
 /*
- * tm_mul_host: one product with HOST buffers. Copies u and v to the device
- * (once when u_host == v_host, which squares), runs tm_mul on `stream`, copies
- * the result back and waits for the stream. On a created stream (not NULL, the
- * legacy or the per-thread default stream) the whole sequence is recorded once
- * per (stream, kind, n_bits) as a CUDA graph, and later calls re-point its three
- * host copies at the new buffers and launch it (one launch instead of about
- * twenty calls); the recording is redone when the library's buffers for that
- * stream change, and skipped when it cannot be made (pageable host buffers).
- * Page-locked host buffers give the fastest copies; pageable ones work.
+ * tm_mul_host: one product with HOST buffers; waits for `stream` before it
+ * returns. u_host == v_host squares.
+ * When u_host, v_host and out_host are all page-locked memory mapped into the
+ * device's address space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister
+ * with mapping, on a 64-bit system) and out_host overlaps neither input, the
+ * kernels read the operands and write the product in host memory directly (over
+ * NVLink-C2C on a GB300): no staging copies.
+ * Otherwise it copies u and v to the device, runs tm_mul on `stream` and copies
+ * the result back. On a created stream (not NULL, the legacy or the per-thread
+ * default stream) that sequence is recorded once per (stream, kind, n_bits) as a
+ * CUDA graph, and later calls re-point its three host copies at the new buffers
+ * and launch it (one launch instead of about twenty calls); the recording is
+ * redone when the library's buffers for that stream change, and skipped when it
+ * cannot be made (pageable host buffers).
  * Limb counts as above. Returns like tm_mul; *rep (optional) is filled.
  */
 int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint64_t* v_host,

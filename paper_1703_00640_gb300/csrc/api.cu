@@ -319,6 +319,17 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
+// The device address of page-locked host memory mapped into the device's address
+// space, or nullptr (pageable memory, device memory, an unknown pointer).
+const uint64_t* mapped_host(const void* h) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<const uint64_t*>(a.devicePointer) : nullptr;
+}
+
 }  // namespace
 
 void ensure_kernel_attributes() {
@@ -775,9 +786,28 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TM_ECUDA;
   const bool square = dv == du;
-  // the recorded sequence, if this stream has one for (kind, n) that is still valid
+  // Page-locked host buffers that the device addresses directly (mapped pinned
+  // memory; a GB300's Grace memory is reached over NVLink-C2C): the forward map
+  // reads the operands and the carry kernel writes the product where they are,
+  // with no staging copies. The operands are read before the product is written,
+  // but overlapping buffers still take the staged path.
+  const uint64_t* mu = tmul::mapped_host(u_host);
+  const uint64_t* mv = square ? mu : tmul::mapped_host(v_host);
+  uint64_t* mo = const_cast<uint64_t*>(tmul::mapped_host(out_host));
+  const bool direct = mu && mv && mo && !tmul::overlaps(out_host, out_bytes, u_host, in_bytes) &&
+                      !tmul::overlaps(out_host, out_bytes, v_host, in_bytes);
   bool done = false;
-  if (s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+  if (direct) {
+    rc = tmul::enqueue(kind, mo, mu, mv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess)
+      return TM_ECUDA;
+    done = true;
+  }
+  // the recorded sequence, if this stream has one for (kind, n) that is still valid
+  if (!done && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
     std::lock_guard<std::mutex> lk(tmul::g_mu);
     tmul::HostGraph& h = tmul::g_host_graphs[std::make_tuple(dev, s, kind, n_bits, square)];
     if (h.exec && (h.io != io || h.ws_base != ws->base || h.pe != pe.get()))

@@ -189,6 +189,43 @@ def test_host_buffers_on_a_stream_repeated(pkg):
         assert np.array_equal(np.asarray(got).view(np.uint64), host(d))
 
 
+@pytest.mark.parametrize("n", [1, 64, 65, 4097, 100003, 1 << 20])
+def test_host_buffers_mapped(pkg, n):
+    """Page-locked operands and output: the kernels read and write the host buffers
+    in place (no staging copies). Interior pointers of one page-locked block, squares,
+    a page-locked input with a pageable output, and an output that overlaps an input
+    (which takes the staged path) all give the device path's limbs."""
+    import torch
+    nl = (n + 63) // 64
+    u, v = workloads.pattern_limbs("random", n, seed=n % 1000 + 400)
+    for kind in ("lo", "hi", "full"):
+        no = pkg.out_limbs(kind, n)
+        ref = {k: host(pkg.mul(kind, dev(a), dev(b), n)[0])
+               for k, (a, b) in (("uv", (u, v)), ("uu", (u, u)))}
+        block = torch.zeros(1 + 2 * nl + no + 3, dtype=torch.int64).pin_memory()
+        bu = block[1:1 + nl]                             # odd-limb offset
+        bv = block[1 + nl:1 + 2 * nl]
+        bo = block[1 + 2 * nl:1 + 2 * nl + no]
+        bu.copy_(torch.from_numpy(u.view(np.int64)))
+        bv.copy_(torch.from_numpy(v.view(np.int64)))
+        for stream in (None, torch.cuda.Stream()):
+            bo.fill_(-1)
+            got, rep = pkg.mul_host(kind, bu, bv, n, out=bo, stream=stream)
+            assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
+            assert np.array_equal(bo.numpy().view(np.uint64), ref["uv"]), (kind, n)
+            assert block[0].item() == 0 and bool((block[1 + 2 * nl + no:] == 0).all())
+            got, _ = pkg.mul_host(kind, bu, bu, n, out=bo, stream=stream)
+            assert np.array_equal(bo.numpy().view(np.uint64), ref["uu"]), (kind, n)
+        pageable = np.zeros(no, dtype=np.uint64)
+        got, _ = pkg.mul_host(kind, bu, bv, n, out=pageable)
+        assert np.array_equal(got, ref["uv"])
+        if no <= 2 * nl:                                  # out over u and v: staged
+            both = torch.cat([torch.from_numpy(u.view(np.int64)),
+                              torch.from_numpy(v.view(np.int64))]).pin_memory()
+            got, _ = pkg.mul_host(kind, both[:nl], both[nl:], n, out=both[:no])
+            assert np.array_equal(both[:no].numpy().view(np.uint64), ref["uv"])
+
+
 def test_concurrent_streams(pkg):
     """Products enqueued on three streams without waits between them (each stream has
     its own workspace and side stream) equal the oracle."""
