@@ -485,12 +485,14 @@ def run_cuda(args):
     # 3 carry kernels
     launches = args.steps * sum(3 * plans[k]["fft_passes"] + 6 for k in kinds)
 
-    # end to end through tm_mul_host with page-locked host buffers
+    # end to end through tm_mul_host with page-locked host buffers: every call moves
+    # the operands host -> device and the product device -> host (the kernels read and
+    # write the mapped host buffers over NVLink-C2C), then waits for the stream
     hu = torch.from_numpy(u_np.view(np.int64)).pin_memory()
     hv = torch.from_numpy(v_np.view(np.int64)).pin_memory()
     hout = {k: torch.empty(pkg.out_limbs(k, n), dtype=torch.int64).pin_memory() for k in kinds}
     e2e_t = []
-    e2e_stream = torch.cuda.Stream()      # a created stream: tm_mul_host records its calls
+    e2e_stream = torch.cuda.Stream()
     for it in range(args.warmup + args.steps):
         t1 = time.perf_counter()
         for k in ("lo", "hi"):
