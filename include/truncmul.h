@@ -59,10 +59,18 @@ extern "C" {
 #define TM_ENOMEM     -2   /* device or host allocation failed                   */
 #define TM_EPRECISION -3   /* margin above the a-priori bound, or 2^b not
                               dividing c_0: the output must not be trusted       */
-#define TM_ETIMEOUT   -4   /* a bounded device-side wait gave up                 */
+#define TM_ETIMEOUT   -4   /* reserved: no call of this version waits on the
+                              device                                             */
 #define TM_ECUDA      -5   /* a CUDA runtime call failed                         */
 #define TM_ERANGE     -6   /* n too large for any FP64 plan of this library      */
 #define TM_EALIAS     -7   /* out overlaps u or v                                */
+
+/* Fault injection for callers' tests. With the environment variable
+ * TRUNCMUL_FAULT_EMAX_SCALE set to a number in (0, 1] (read once, when the
+ * library first enqueues a product), every bound the device checks the margin
+ * against is multiplied by it: a small value such as 1e-12 makes every product
+ * report TM_EPRECISION through every entry point while computing the same limbs.
+ * Other values are ignored. */
 
 /* ---- product kinds ---- */
 #define TM_FULL 0          /* Algorithm 1 */

@@ -2,6 +2,7 @@
 // workspaces and the launch sequence of one product.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -84,6 +85,17 @@ int cuda_fail(cudaError_t e) {
 }  // namespace
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+unsigned long long emax_fixed(double e_max) {
+  static const double scale = [] {
+    const char* v = std::getenv("TRUNCMUL_FAULT_EMAX_SCALE");
+    if (!v) return 1.0;
+    char* end = nullptr;
+    const double x = std::strtod(v, &end);
+    return (end != v && x > 0.0 && x <= 1.0) ? x : 1.0;
+  }();
+  return (unsigned long long)std::ldexp(e_max * scale, 63);
+}
 
 int64_t limbs_of(uint64_t n) { return int64_t((n + 63) / 64); }
 int64_t out_limbs(int kind, uint64_t n) {
@@ -516,7 +528,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   ba.rho = p.rho;
   ba.c = cbuf;
   ba.count = kind == TM_HI ? N + 1 : N;
-  ba.emax_fx = (unsigned long long)std::ldexp(p.e_max, 63);
+  ba.emax_fx = emax_fixed(p.e_max);
   ba.status = ws.status;
   launch_back(kind, ba, 1, s);
   mark(5);
@@ -1251,7 +1263,7 @@ const char* tm_strerror(int code) {
     case TM_EINVAL: return "invalid argument";
     case TM_ENOMEM: return "out of memory";
     case TM_EPRECISION: return "rounding margin above the error bound: result not trusted";
-    case TM_ETIMEOUT: return "device-side wait timed out";
+    case TM_ETIMEOUT: return "device-side wait timed out (reserved)";
     case TM_ECUDA: return "CUDA runtime error";
     case TM_ERANGE: return "operand size outside the supported range";
     case TM_EALIAS: return "output overlaps an input";

@@ -160,7 +160,7 @@ void build_items(tm_batch* B, const Group& g, std::vector<char>* host) {
     bi[i].w = reinterpret_cast<const double*>(R1 + size_t(i) * 2 * M * sizeof(double2));
     bi[i].c = reinterpret_cast<long long*>(X);
     bi[i].theta = theta + 2 * i;
-    bi[i].emax_fx = (unsigned long long)std::ldexp(q.e_max, 63);
+    bi[i].emax_fx = emax_fixed(q.e_max);
     int64_t nS, shift, rbit;
     carry_shape(q, &nS, &shift, &rbit);
     char* scratch = carry + size_t(i) * g.carry_bytes;
@@ -248,7 +248,7 @@ SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
   it.shift_bits = shift;
   it.nout = out_limbs(q.kind, n);
   it.top_mask = (q.kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
-  it.emax_fx = (unsigned long long)std::ldexp(q.e_max, 63);
+  it.emax_fx = emax_fixed(q.e_max);
   it.plan = plan;
   return it;
 }

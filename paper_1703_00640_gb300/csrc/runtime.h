@@ -41,6 +41,11 @@ struct Workspace {
 };
 
 size_t align_up(size_t x);
+// The margin bound the device checks, e_max in units of 2^-63. Fault injection on
+// the host: the environment variable TRUNCMUL_FAULT_EMAX_SCALE (a number in (0, 1],
+// read once per process) scales every bound down, so that the device-side margin
+// check fails and the TM_EPRECISION path can be exercised without a GPU fault.
+unsigned long long emax_fixed(double e_max);
 int64_t limbs_of(uint64_t n);
 int64_t out_limbs(int kind, uint64_t n);
 void carry_shape(const PlanParams& p, int64_t* nS, int64_t* shift, int64_t* round_bit);

@@ -117,7 +117,7 @@ SmallItem small_item(const Request& r, int plan) {
   it.shift_bits = shift;
   it.nout = out_limbs(q.kind, r.n);
   it.top_mask = (q.kind == TM_LO && r.n % 64) ? ((1ull << (r.n % 64)) - 1ull) : ~0ull;
-  it.emax_fx = (unsigned long long)std::ldexp(q.e_max, 63);
+  it.emax_fx = emax_fixed(q.e_max);
   it.plan = plan;
   return it;
 }

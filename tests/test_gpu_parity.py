@@ -226,6 +226,58 @@ def test_host_buffers_mapped(pkg, n):
             assert np.array_equal(both[:no].numpy().view(np.uint64), ref["uv"])
 
 
+@pytest.mark.parametrize("n", [1, 65, 127, 1000, 4097, 100003, (1 << 20) + 5])
+def test_bits_above_n_are_ignored(pkg, n):
+    """Bits at positions >= n of the operands' top limb are ignored: set at random,
+    every entry point (tm_mul, tm_mul_adaptive, squares, host buffers, kept operands,
+    a batch) gives the product of the masked operands."""
+    import torch
+    if n % 64 == 0:
+        return
+    u, v = workloads.pattern_limbs("random", n, seed=n % 991)
+    rng = np.random.default_rng(n)
+    junk = np.uint64(~((1 << (n % 64)) - 1) & (2**64 - 1))
+    ud, vd = u.copy(), v.copy()
+    ud[-1] |= rng.integers(0, 2**63, dtype=np.uint64) * np.uint64(2) & junk
+    vd[-1] |= junk                                         # every bit above n set
+    assert (ud[-1] & junk) != 0 or n % 64 > 60
+    for kind in ("lo", "hi", "full"):
+        clean, rep = pkg.mul(kind, dev(u), dev(v), n)
+        want = host(clean)
+        dirty, rep_d = pkg.mul(kind, dev(ud), dev(vd), n)
+        assert np.array_equal(host(dirty), want), kind
+        assert rep_d["margin"] == rep["margin"]
+        a_c, ra = pkg.mul_adaptive(kind, dev(u), dev(v), n)
+        a_d, rd = pkg.mul_adaptive(kind, dev(ud), dev(vd), n)
+        assert (ra["b"], ra["N"]) == (rd["b"], rd["N"]) and np.array_equal(host(a_c), host(a_d))
+        sq_c, _ = pkg.mul(kind, dev(v), dev(v), n)
+        sq_d, _ = pkg.mul(kind, dev(vd), dev(vd), n)
+        assert np.array_equal(host(sq_c), host(sq_d))
+        pu = torch.from_numpy(ud.view(np.int64)).pin_memory()
+        pv = torch.from_numpy(vd.view(np.int64)).pin_memory()
+        po = torch.empty(pkg.out_limbs(kind, n), dtype=torch.int64).pin_memory()
+        pkg.mul_host(kind, pu, pv, n, out=po)
+        assert np.array_equal(po.numpy().view(np.uint64), want)
+        got, _ = pkg.mul_host(kind, ud, vd, n)
+        assert np.array_equal(got, want)
+        op = pkg.Operand(kind, dev(vd), n)
+        try:
+            got, _ = op.mul(dev(ud))
+            assert np.array_equal(host(got), want)
+        finally:
+            op.close()
+        o = torch.empty(pkg.out_limbs(kind, n), dtype=torch.int64, device="cuda")
+        b = pkg.Batch([(kind, n, o, dev(ud), dev(vd))])
+        try:
+            b.launch()
+            torch.cuda.synchronize()
+            assert np.array_equal(host(o), want)
+        finally:
+            b.close()
+    # and the oracle agrees with the masked operands
+    assert np.array_equal(host(pkg.mul("lo", dev(ud), dev(vd), n)[0]), bigmul.mul_lo(u, v, n))
+
+
 def test_concurrent_streams(pkg):
     """Products enqueued on three streams without waits between them (each stream has
     its own workspace and side stream) equal the oracle."""
