@@ -11,6 +11,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/truncmul.h"
 #include "kernels.cuh"
@@ -459,12 +460,35 @@ int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
   return TM_OK;
 }
 
+namespace {
+// NVTX ranges (header-only NVTX 3: inert unless a profiler injects its library):
+// one per product, named by kind, with one nested range per phase, so that a
+// timeline tool groups each product's kernel launches by the paper's steps.
+const char* const kPhaseNames[TM_NPHASES] = {"split+convert", "forward FFT",
+                                             "twist+pointwise", "inverse FFT",
+                                             "convert back+round", "overlap-add+carry"};
+const char* const kKindNames[3] = {"tm_mul full", "tm_mul lo", "tm_mul hi"};
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
             cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
             int64_t* coeff_out, void* const* events, const KeptOperand* kept) {
+  NvtxRange product(kKindNames[kind]);
+  bool phase_open = false;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
+    if (phase_open) nvtxRangePop();
+    phase_open = i < TM_NPHASES;
+    if (phase_open) nvtxRangePushA(kPhaseNames[i]);
   };
+  struct ClosePhase {                   // an early return leaves no phase range open
+    bool* open;
+    ~ClosePhase() { if (*open) nvtxRangePop(); }
+  } close_phase{&phase_open};
   ensure_kernel_attributes();
   mark(0);
   const int64_t N = p.N, M = pe.M;
