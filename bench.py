@@ -62,6 +62,8 @@ def parse():
                     help="run the large single-product section alone")
     ap.add_argument("--large-kinds", default="lo,hi,full",
                     help="products of the large section (comma list of lo, hi, full)")
+    ap.add_argument("--no-paper-params", action="store_true",
+                    help="skip the products with the paper's Table 2 parameters")
     return ap.parse_args()
 
 
@@ -572,6 +574,12 @@ def run_cuda(args):
                             "corrections; reciprocal by Newton iteration, host-timed "
                             "(it waits for the stream)"}
 
+    paper_params = None
+    if not args.no_paper_params:
+        paper_params = run_paper_params(pkg, torch, np, workloads, max(3, min(args.steps, 7)),
+                                        args.warmup, stream, flush, seed=2017 + rank)
+        pkg.release()                   # the rows' plan tables (about 20 GB)
+
     large = None
     if not args.no_large:
         large = run_large(pkg, torch, np, workloads, args.large_bits,
@@ -625,6 +633,7 @@ def run_cuda(args):
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
         "large": large,
+        "paper_parameters": paper_params,
         "autotune": tuned,
         "square_and_kept_operand": variants,
         "division": division,
@@ -727,6 +736,86 @@ def run_large(pkg, torch, np, workloads, n, reps, warmup, stream, flush, seed,
     return {"n_bits": n, "operands": "uniform random uint64 limbs (seeded PCG64)",
             "l2": "flushed (256 MB write) before every product", "reps": reps,
             **checks, "fp64_peak_tflops": FP64_PEAK_TFLOPS, **res}
+
+
+def table2_rows():
+    """The paper's Table 2 (Section 5): n, N and b of the truncated products, lambda,
+    the full product's cyclic length 2N and b (rows with n < 2^31)."""
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "table2_params.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(tuple(int(x) for x in line.split()))
+    return rows
+
+
+def run_paper_params(pkg, torch, np, workloads, reps, warmup, stream, flush, seed,
+                     max_bits=1 << 28):
+    """Every Table 2 row with n <= max_bits (the certified plans of the two larger rows
+    hold 50-80 GB of map tables): low and high products with the paper's (N, b) and the full
+    product with its (2N, b) through tm_mul_params (b chosen by experiment, not
+    certified: the acceptance limit is 3/8), next to the certified plans of tm_mul
+    at the same n. Per row: device times (CUDA events, L2 flushed, median), the
+    ratios t_lo / t_full and t_hi / t_full in both settings, margins and statuses;
+    the low product is checked against the full product's low bits and the high
+    product against the admissible values."""
+    out_rows = []
+    for n, N, b, lam, L, bf in table2_rows():
+        if n > max_bits:
+            continue
+        u_np, v_np = workloads.pattern_limbs("random", n, seed=seed)
+        u = torch.from_numpy(u_np.view(np.int64)).cuda()
+        v = torch.from_numpy(v_np.view(np.int64)).cuda()
+        outs = {k: torch.empty(pkg.out_limbs(k, n), dtype=torch.int64, device="cuda")
+                for k in ("lo", "hi", "full")}
+        row = {"n_bits": n, "paper": {}, "certified": {}}
+        prm = {"lo": (b, N), "hi": (b, N), "full": (bf, L)}
+        for k in ("lo", "hi", "full"):
+            _, rep = pkg.mul_params(k, u, v, n, b=prm[k][0], N=prm[k][1], out=outs[k],
+                                    stream=stream, check=False)
+            res = {"b": rep["b"], "N": rep["N"], "lam": rep["lam_fwd"], "status": rep["status"],
+                   "margin": rep["margin"], "e_max": rep["e_max"]}
+            ev = []
+            for i in range(warmup + reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.mul_params(k, u, v, n, b=prm[k][0], N=prm[k][1], out=outs[k],
+                               stream=stream, report=False, check=False)
+                e1.record(stream)
+                if i >= warmup:
+                    ev.append((e0, e1))
+            torch.cuda.synchronize()
+            res["ms"] = statistics.median(a.elapsed_time(c) for a, c in ev)
+            row["paper"][k] = res
+        full = _as_int(outs["full"])
+        row["lo_equals_full_low_bits"] = _as_int(outs["lo"]) == full & ((1 << n) - 1)
+        row["hi_admissible"] = _as_int(outs["hi"]) in (full >> n, (full >> n) + 1)
+        for k in ("lo", "hi", "full"):
+            o = torch.empty_like(outs[k])
+            _, rep = pkg.mul(k, u, v, n, out=o, stream=stream)
+            ev = []
+            for i in range(warmup + reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.mul(k, u, v, n, out=o, stream=stream, report=False)
+                e1.record(stream)
+                if i >= warmup:
+                    ev.append((e0, e1))
+            torch.cuda.synchronize()
+            row["certified"][k] = {"b": rep["b"], "N": rep["N"], "margin": rep["margin"],
+                                   "ms": statistics.median(a.elapsed_time(c) for a, c in ev)}
+        for setting in ("paper", "certified"):
+            r = row[setting]
+            r["t_lo_over_full"] = r["lo"]["ms"] / r["full"]["ms"]
+            r["t_hi_over_full"] = r["hi"]["ms"] / r["full"]["ms"]
+            r["trunc_gbit_s"] = 2 * n / ((r["lo"]["ms"] + r["hi"]["ms"]) * 1e-3) / 1e9
+        out_rows.append(row)
+    return {"source": "Table 2 of the paper (Section 5)", "acceptance_limit": 0.375,
+            "operands": "uniform random uint64 limbs (seeded PCG64)", "reps": reps,
+            "rows": out_rows}
 
 
 def run_large_only(args):

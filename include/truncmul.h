@@ -125,6 +125,36 @@ int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64
            void* stream, tm_report* rep);
 
 /*
+ * tm_mul_params: tm_mul with the caller's digit size b and transform length N,
+ * as in the paper's Section 5, where b, N and lambda are chosen by experiment
+ * for random operands (its Table 2 lists them).
+ *   prm->b      digit size, 4..24.
+ *   prm->N      transform length: N of Algorithms 2 and 3, the cyclic length of
+ *               Algorithm 1 for the full product; even, 2^a m with m one of
+ *               1, 3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49, 63, 75, 81, 105, 125,
+ *               135, 147, 175, 189, at most 2^31; (b, N) must satisfy the
+ *               hypotheses of Theorem 2.2 (N b >= n), Theorem 2.3
+ *               ((N + 1) b >= n + lg N + 2) or Theorem 2.1 (N >= 2 ceil((n+1)/b) - 1).
+ *   prm->limit  the largest rounding distance the call accepts, in [0, 1/2];
+ *               0 = e_max when e_max < 1/2, else 3/8.
+ * lambda comes from the library's tail budgets for b. rep->e_max is the
+ * worst-case bound for (b, N): at or above 1/2 the result is NOT certified (the
+ * paper's own setting) and the limit is a heuristic: a product whose errors
+ * reach 1/2 almost surely also has distances near 1/2, so operands too large for
+ * b show up as TM_EPRECISION. With the paper's Table 2 parameters the largest
+ * distance on random operands is about 1/4 (n = 10^6, b = 14). Other arguments,
+ * layout and errors as tm_mul; TM_EINVAL also for a NULL prm or parameters
+ * outside the ranges above.
+ */
+typedef struct tm_params {
+  uint32_t b;
+  uint32_t N;
+  double limit;
+} tm_params;
+int tm_mul_params(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, const tm_params* prm, void* stream, tm_report* rep);
+
+/*
  * tm_mul_adaptive: tm_mul with a data-dependent digit size. The paper picks b
  * empirically for random inputs (Section 5); the planner's b is the largest the
  * worst-case error bound certifies for ANY operands (all digits at their maximum).

@@ -42,6 +42,10 @@ class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Params(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_uint32), ("N", ctypes.c_uint32), ("limit", ctypes.c_double)]
+
+
 class Tune(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("points", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("passes", ctypes.c_int32),
@@ -61,7 +65,7 @@ class TruncMulError(RuntimeError):
 NPHASES = 6
 PHASES = ["fwd_map", "fwd_fft", "twist_pointwise", "inv_fft", "back_round", "carry"]
 STATIC_MAX_BITS = 65536
-EXPORTS = ["tm_mul", "tm_mul_adaptive", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
+EXPORTS = ["tm_mul", "tm_mul_params", "tm_mul_adaptive", "tm_mul_full", "tm_mul_lo", "tm_mul_hi", "tm_mul_host", "tm_mul_events",
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
@@ -93,6 +97,9 @@ def load(path: str = None):
         getattr(lib, name).argtypes = [P, P, P, ctypes.c_uint64, P, R]
         getattr(lib, name).restype = ctypes.c_int
     lib.tm_mul.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
+    lib.tm_mul_params.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64,
+                                  ctypes.POINTER(Params), P, R]
+    lib.tm_mul_params.restype = ctypes.c_int
     lib.tm_mul_adaptive.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
     lib.tm_mul_adaptive.restype = ctypes.c_int
     lib.tm_mul_host.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P, R]
@@ -200,6 +207,24 @@ def mul(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True, che
                        ctypes.byref(rep) if rep is not None else None)
     if check and rc:
         raise TruncMulError(rc, "tm_mul")
+    return out, (rep.as_dict() if rep is not None else None)
+
+
+def mul_params(kind, u, v, n_bits: int, b: int, N: int, limit: float = 0.0, out=None,
+               stream=None, report: bool = True, check: bool = True):
+    """tm_mul_params: the product with the caller's digit size b and transform
+    length N (the paper's empirical parameters). Returns (out, report dict or None)."""
+    import torch
+    k = _kind(kind)
+    if out is None:
+        out = torch.empty(out_limbs(k, n_bits), dtype=torch.int64, device=u.device)
+    prm = Params(b=int(b), N=int(N), limit=float(limit))
+    rep = Report() if report else None
+    rc = load().tm_mul_params(k, _ptr(out), _ptr(u), _ptr(v), int(n_bits), ctypes.byref(prm),
+                              _stream_ptr(stream),
+                              ctypes.byref(rep) if rep is not None else None)
+    if check and rc:
+        raise TruncMulError(rc, "tm_mul_params")
     return out, (rep.as_dict() if rep is not None else None)
 
 

@@ -552,7 +552,7 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   ba.rho = p.rho;
   ba.c = cbuf;
   ba.count = kind == TM_HI ? N + 1 : N;
-  ba.emax_fx = emax_fixed(p.e_max);
+  ba.emax_fx = emax_fixed(p.limit > 0.0 ? p.limit : p.e_max);
   ba.status = ws.status;
   launch_back(kind, ba, 1, s);
   mark(5);
@@ -588,7 +588,8 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
 namespace {
 
 int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n, void* stream,
-        tm_report* rep, int64_t* coeff_out, void* const* events = nullptr) {
+        tm_report* rep, int64_t* coeff_out, void* const* events = nullptr,
+        const tm_params* explicit_prm = nullptr) {
   if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
   if (n == 0 || !u || !v || (!out && !coeff_out)) return TM_EINVAL;
   if (n > TM_MAX_BITS) return TM_ERANGE;
@@ -599,7 +600,16 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PlanParams p;
-  int rc = get_params(kind, n, &p);
+  int rc;
+  if (explicit_prm) {
+    const double lim = explicit_prm->limit;
+    if (!(lim >= 0.0 && lim <= 0.5)) return TM_EINVAL;
+    rc = explicit_params(kind, n, int(explicit_prm->b), int64_t(explicit_prm->N), &p);
+    if (rc) return rc;
+    p.limit = lim > 0.0 ? lim : (p.e_max < 0.5 ? p.e_max : 0.375);
+  } else {
+    rc = get_params(kind, n, &p);
+  }
   if (rc) return rc;
   std::shared_ptr<PlanEntry> pe;
   rc = get_tables(p, false, s, &pe);
@@ -764,6 +774,12 @@ int tm_mul_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
 int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
            void* stream, tm_report* rep) {
   return tmul::run(kind, out, u, v, n_bits, stream, rep, nullptr);
+}
+
+int tm_mul_params(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
+                  uint64_t n_bits, const tm_params* prm, void* stream, tm_report* rep) {
+  if (!prm) return TM_EINVAL;
+  return tmul::run(kind, out, u, v, n_bits, stream, rep, nullptr, nullptr, prm);
 }
 
 int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,

@@ -298,6 +298,32 @@ int choose_params(int kind, uint64_t n, PlanParams* out) {
   return TM_OK;
 }
 
+int explicit_params(int kind, uint64_t n, int b, int64_t N, PlanParams* out) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n == 0) return TM_EINVAL;
+  if (n > TM_MAX_BITS) return TM_ERANGE;
+  if (b < kBMin || b > kBMax || !is_valid_length(N) || N > (int64_t(1) << 31))
+    return TM_EINVAL;
+  PlanParams p;
+  p.kind = kind; p.n = n; p.b = b; p.N = N;
+  if (kind == TM_LO) {
+    if (N < 3 || uint64_t(N) * uint64_t(b) < n) return TM_EINVAL;     // Theorem 2.2
+    const Bound B = bound_lo(b, N);
+    p.e_max = B.E; p.lam_fwd = B.lf; p.lam_bwd = B.lb; p.n_digits = N;
+  } else if (kind == TM_HI) {
+    if (!hi_hypothesis(n, b, N)) return TM_EINVAL;                     // Theorem 2.3
+    const Bound B = bound_hi(b, N);
+    p.e_max = B.E; p.lam_fwd = B.lf; p.lam_bwd = B.lb; p.n_digits = N + 1;
+    p.rho = rho_of(N, b);
+  } else {
+    p.n_digits = full_digit_count(n, b);
+    if (N < 2 * p.n_digits - 1) return TM_EINVAL;                      // Theorem 2.1
+    p.e_max = bound_full(n, b, N);
+  }
+  *out = p;
+  return TM_OK;
+}
+
 int64_t measured_length(int kind, uint64_t n, int b) {
   if (b < kBMin || b > kBMax) return -1;
   int64_t lmin;

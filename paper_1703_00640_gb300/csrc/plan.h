@@ -51,10 +51,18 @@ struct PlanParams {
   int lam_fwd = 0, lam_bwd = 0;
   double e_max = 0.0;    // bound on the rounding distance
   double rho = 0.0;      // auxiliary real root (high product only)
+  double limit = 0.0;    // largest distance the device accepts (0: e_max)
 };
 
 // Chooses (b, N, lambda) for kind and n; returns 0 or a TM_E* code.
 int choose_params(int kind, uint64_t n, PlanParams* out);
+
+// The plan for a caller's digit size b and transform length N (the cyclic length
+// of Algorithm 1 for the full product): lambda from the same tail budgets as the
+// planner, e_max the worst-case bound for (b, N), which may exceed 1/2. TM_EINVAL
+// when b is outside [4, 24], N is not a supported length, or (b, N) violates the
+// hypotheses of Theorems 2.1-2.3 for n.
+int explicit_params(int kind, uint64_t n, int b, int64_t N, PlanParams* out);
 
 // Layout choices of the FFT passes that the autotuner varies: points a CTA aims to
 // hold (sequences per CTA = points / L), how the odd primes of M are distributed

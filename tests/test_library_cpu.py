@@ -93,6 +93,28 @@ def test_host_side_errors(pkg):
     assert lib.tm_autotune(1, 100, None, None) == pkg.TM_EINVAL
     assert lib.tm_autotune(5, 100, None, ctypes.byref(pkg.Tune())) == pkg.TM_EINVAL
     assert lib.tm_autotune(1, (1 << 31) + 1, None, ctypes.byref(pkg.Tune())) == pkg.TM_ERANGE
+    # explicit parameters: checked before any CUDA call
+    fp = ctypes.c_void_p(0x1000)
+    fq = ctypes.c_void_p(0x100000)
+    n = 1000000
+    ok = dict(b=14, N=71680, limit=0.0)               # a Table 2 row (low product)
+    assert lib.tm_mul_params(1, fq, fp, fp, n, None, None, None) == pkg.TM_EINVAL
+    for bad in (dict(b=3), dict(b=25), dict(N=71681), dict(N=71680 * 11), dict(N=2),
+                dict(b=13, N=71680),                  # N b < n: Theorem 2.2 fails
+                dict(limit=-0.1), dict(limit=0.6), dict(limit=float("nan"))):
+        prm = pkg.Params(**{**ok, **bad})
+        assert lib.tm_mul_params(1, fq, fp, fp, n, ctypes.byref(prm), None, None) == \
+            pkg.TM_EINVAL, bad
+    hi_bad = pkg.Params(b=14, N=65536, limit=0.0)    # (N + 1) b < n + lg N + 2
+    assert lib.tm_mul_params(2, fq, fp, fp, n, ctypes.byref(hi_bad), None, None) == pkg.TM_EINVAL
+    full_bad = pkg.Params(b=21, N=65536, limit=0.0)   # below 2 ceil((n+1)/b) - 1
+    assert lib.tm_mul_params(0, fq, fp, fp, n, ctypes.byref(full_bad), None, None) == \
+        pkg.TM_EINVAL
+    prm = pkg.Params(**ok)
+    assert lib.tm_mul_params(1, fq, fp, fp, 0, ctypes.byref(prm), None, None) == pkg.TM_EINVAL
+    assert lib.tm_mul_params(1, fq, fp, fp, (1 << 31) + 1, ctypes.byref(prm), None,
+                             None) == pkg.TM_ERANGE
+    assert lib.tm_mul_params(1, fp, fp, fp, n, ctypes.byref(prm), None, None) == pkg.TM_EALIAS
     # layouts: checked before any CUDA call
     good = pkg.Tune(points=512, split=0, passes=3)
     assert lib.tm_set_layout(1, 100, None) == pkg.TM_EINVAL
