@@ -372,12 +372,43 @@ int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int 
   return cur;
 }
 
+namespace {
+// One page-locked status word per host thread (mapped: the device writes it).
+DevStatus* thread_status_host() {
+  thread_local struct Holder {
+    DevStatus* p = nullptr;
+    ~Holder() { if (p) cudaFreeHost(p); }
+  } h;
+  if (!h.p && cudaHostAlloc(&h.p, sizeof(DevStatus),
+                            cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
+    (void)cudaGetLastError();
+    h.p = nullptr;
+  }
+  return h.p;
+}
+}  // namespace
+
 int read_status(cudaStream_t s, DevStatus* status, tm_report* rep) {
-  TM_CHECK(cudaStreamSynchronize(s));
   DevStatus st{};
-  TM_CHECK(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
-  TM_CHECK(cudaMemsetAsync(status, 0, sizeof(DevStatus), s));
-  TM_CHECK(cudaStreamSynchronize(s));
+  DevStatus* h = thread_status_host();
+  DevStatus* hd = nullptr;
+  if (h && cudaHostGetDevicePointer(reinterpret_cast<void**>(&hd), h, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    hd = nullptr;
+  }
+  if (hd) {                      // one kernel and one wait
+    launch_status_publish(status, hd, s);
+    TM_CHECK(cudaGetLastError());
+    TM_CHECK(cudaStreamSynchronize(s));
+    const volatile DevStatus* vh = h;
+    st.margin_fx = vh->margin_fx;
+    st.flags = vh->flags;
+  } else {
+    TM_CHECK(cudaStreamSynchronize(s));
+    TM_CHECK(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    TM_CHECK(cudaMemsetAsync(status, 0, sizeof(DevStatus), s));
+    TM_CHECK(cudaStreamSynchronize(s));
+  }
   const int code = st.flags ? TM_EPRECISION : TM_OK;
   if (rep) {
     rep->margin = std::ldexp(double(st.margin_fx), -63);
@@ -852,10 +883,16 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
   if (direct) {
     rc = tmul::enqueue(kind, mo, mu, mv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
     if (rc) return rc;
-    if (cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess)
+    tmul::DevStatus* sh = nullptr;        // the status word, published by one kernel
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&sh), ws->status_host, 0) ==
+        cudaSuccess) {
+      tmul::launch_status_publish(ws->status, sh, s);
+      if (cudaGetLastError() != cudaSuccess) return TM_ECUDA;
+    } else if (cudaMemcpyAsync(ws->status_host, ws->status, sizeof(tmul::DevStatus),
+                               cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaMemsetAsync(ws->status, 0, sizeof(tmul::DevStatus), s) != cudaSuccess) {
       return TM_ECUDA;
+    }
     done = true;
   }
   // the recorded sequence, if this stream has one for (kind, n) that is still valid

@@ -1543,6 +1543,21 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
   a.out[j] = o;
 }
 
+__global__ void k_status_publish(DevStatus* status, DevStatus* host) {
+  pdl_trigger();
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    const DevStatus v = *status;
+    *host = v;
+    status->margin_fx = 0ull;
+    status->flags = 0u;
+  }
+}
+
+void launch_status_publish(DevStatus* status, DevStatus* host, cudaStream_t s) {
+  launch_pdl(k_status_publish, dim3(1), dim3(32), 0, s, status, host);
+}
+
 void launch_carry(const CarryArgs& a, int batch, cudaStream_t s) {
   const long long nblocks =
       a.items ? a.nblocks_max : (a.nS + kCarryThreads - 1) / kCarryThreads;

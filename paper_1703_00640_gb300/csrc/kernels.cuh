@@ -238,6 +238,9 @@ void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
                   long long qstride, cudaStream_t s);
 void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s);
 void launch_carry(const CarryArgs& a, int batch, cudaStream_t s);
+// Copies the status word to page-locked host memory mapped into the device's
+// address space and resets it, in stream order after the work before it.
+void launch_status_publish(DevStatus* status, DevStatus* host, cudaStream_t s);
 
 // map table selectors for launch_init_maptab
 constexpr int kTabAlpha = 0, kTabBeta = 1, kTabGamma = 2, kTabDelta = 3, kTabDeltaPrime = 4;
