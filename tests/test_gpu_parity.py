@@ -64,6 +64,18 @@ def test_random(pkg, n):
     _check_all(pkg, n, u, v)
 
 
+SWEEP_N = sorted({int(x) for x in workloads.log_uniform_sizes(160, 0, 21, seed=1703)} | {1})
+
+
+@pytest.mark.parametrize("chunk", range(8))
+def test_random_size_sweep(pkg, chunk):
+    """Seeded sizes, log-uniform in [1, 2^21] (132 distinct: ragged, every pass layout class):
+    low and full bit for bit, high admissible and (n <= 2^18) the exact round(t)."""
+    for n in SWEEP_N[chunk::8]:
+        u, v = workloads.pattern_limbs("random", n, seed=50000 + n)
+        _check_all(pkg, n, u, v, exact_hi=n <= 1 << 18)
+
+
 @pytest.mark.parametrize("pattern", ["ones", "balanced_worst", "alternating", "zero", "one", "top"])
 @pytest.mark.parametrize("n", [64, 1000, 4097, 65536, 200000])
 def test_adversarial(pkg, n, pattern):
