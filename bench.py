@@ -390,10 +390,12 @@ def run_cuda(args):
     plans = {k: pkg.plan(k, n) for k in kinds}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    # FFT pass layouts picked by measurement for the three plans (tm_autotune)
+    # the plan (b, N) among the certified candidates, then the FFT pass layout of
+    # its length, picked by measurement (tm_autotune_plan, tm_autotune)
     tuned = None
     if not args.no_autotune:
-        tuned = {k: pkg.autotune(k, n, stream=stream) for k in kinds}
+        tuned = {"plans": {k: pkg.autotune_plan(k, n, stream=stream) for k in kinds}}
+        tuned["layouts"] = {k: pkg.autotune(k, n, stream=stream) for k in kinds}
         plans = {k: pkg.plan(k, n) for k in kinds}
 
     # correctness gate on the bench workload (sampled against the oracle's low product)

@@ -428,6 +428,39 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out);
 int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
 
 /*
+ * tm_autotune_plan: picks the plan (b, N) of (kind, n_bits) by measurement, as
+ * the paper's Section 5 picks N among its candidate lengths by their timings.
+ * Candidates: every certified plan (worst-case bound within the target, so every
+ * result stays exact) whose transform length is at most 1.15x the planner's, the
+ * planner's first, at most 8. Each runs whole products on scratch operands on
+ * `stream` (one warm-up, median of three, CUDA events); the fastest becomes the
+ * plan of (kind, n_bits) for later calls in this process (tm_mul and the calls
+ * built on it; tm_mul_static keeps the planner's). Low and full products do not
+ * change; a high product may become the other admissible value. Tables of the
+ * losing candidates are freed. Waits for the stream. *out: the chosen b and N,
+ * the number of candidates, and the planner's and the chosen plan's times (ms).
+ * Errors: TM_EINVAL, TM_ERANGE as tm_mul; TM_ENOMEM for the scratch operands.
+ */
+typedef struct tm_plan_tune {
+  uint32_t b;
+  uint32_t N;
+  uint32_t candidates;
+  uint32_t reserved;
+  double ms_default;
+  double ms_best;
+} tm_plan_tune;
+int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out);
+
+/*
+ * tm_plan_set: makes the certified plan (b, N) the plan of (kind, n_bits) for later
+ * calls in this process (for example one chosen by tm_autotune_plan earlier);
+ * b = N = 0 restores the planner's choice. TM_EINVAL for parameters outside the
+ * ranges of tm_mul_params, TM_ERANGE when the worst-case bound for (b, N) is above
+ * the target (use tm_mul_params for uncertified parameters).
+ */
+int tm_plan_set(int kind, uint64_t n_bits, uint32_t b, uint32_t N);
+
+/*
  * tm_plan_query: the plan the library uses for (kind, n_bits), without any
  * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, e_max and
  * workspace_bytes of *rep. Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.

@@ -46,6 +46,15 @@ class Params(ctypes.Structure):
     _fields_ = [("b", ctypes.c_uint32), ("N", ctypes.c_uint32), ("limit", ctypes.c_double)]
 
 
+class PlanTune(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_uint32), ("N", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("ms_default", ctypes.c_double),
+                ("ms_best", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class Tune(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("points", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("passes", ctypes.c_int32),
@@ -69,7 +78,7 @@ EXPORTS = ["tm_mul", "tm_mul_params", "tm_mul_adaptive", "tm_mul_full", "tm_mul_
            "tm_mul_static", "tm_batch_create", "tm_batch_launch", "tm_batch_status",
            "tm_batch_destroy", "tm_mul_batch", "tm_server_create", "tm_server_submit",
            "tm_server_progress", "tm_server_pending", "tm_server_destroy",
-           "tm_autotune", "tm_set_layout", "tm_operand_create", "tm_mul_operand", "tm_operand_destroy",
+           "tm_autotune", "tm_set_layout", "tm_autotune_plan", "tm_plan_set", "tm_operand_create", "tm_mul_operand", "tm_operand_destroy",
            "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
@@ -132,6 +141,10 @@ def load(path: str = None):
     lib.tm_autotune.restype = ctypes.c_int
     lib.tm_set_layout.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Tune)]
     lib.tm_set_layout.restype = ctypes.c_int
+    lib.tm_autotune_plan.argtypes = [ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(PlanTune)]
+    lib.tm_autotune_plan.restype = ctypes.c_int
+    lib.tm_plan_set.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+    lib.tm_plan_set.restype = ctypes.c_int
     lib.tm_reciprocal.argtypes = [P, P, ctypes.c_uint64, P]
     lib.tm_barrett_create.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_void_p)]
     lib.tm_barrett_divrem.argtypes = [P, P, P, P, P, R]
@@ -376,6 +389,24 @@ def autotune(kind, n_bits: int, stream=None) -> dict:
     if rc:
         raise TruncMulError(rc, "tm_autotune")
     return t.as_dict()
+
+
+def autotune_plan(kind, n_bits: int, stream=None) -> dict:
+    """tm_autotune_plan: time the certified plans (b, N) of (kind, n) near the
+    planner's and keep the fastest for later calls."""
+    t = PlanTune()
+    rc = load().tm_autotune_plan(_kind(kind), int(n_bits), _stream_ptr(stream), ctypes.byref(t))
+    if rc:
+        raise TruncMulError(rc, "tm_autotune_plan")
+    return t.as_dict()
+
+
+def plan_set(kind, n_bits: int, b: int = 0, N: int = 0):
+    """tm_plan_set: make the certified (b, N) the plan of (kind, n); b = N = 0
+    restores the planner's choice."""
+    rc = load().tm_plan_set(_kind(kind), int(n_bits), int(b), int(N))
+    if rc:
+        raise TruncMulError(rc, "tm_plan_set")
 
 
 def set_layout(kind, n_bits: int, points: int = 1024, split: int = 0, passes: int = 0):

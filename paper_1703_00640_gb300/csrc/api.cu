@@ -1226,6 +1226,113 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
   return TM_OK;
 }
 
+int tm_plan_set(int kind, uint64_t n_bits, uint32_t b, uint32_t N) {
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  const auto key = std::make_pair(kind, n_bits);
+  if (b == 0 && N == 0) {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    tmul::g_params.erase(key);             // the planner's choice again
+    return TM_OK;
+  }
+  tmul::PlanParams p;
+  const int rc = tmul::explicit_params(kind, n_bits, int(b), int64_t(N), &p);
+  if (rc) return rc;
+  if (p.e_max > tmul::bound_target()) return TM_ERANGE;   // not certified
+  std::lock_guard<std::mutex> lk(tmul::g_mu);
+  tmul::g_params[key] = p;
+  return TM_OK;
+}
+
+int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out) {
+  if (!out) return TM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;
+  if (n_bits == 0) return TM_EINVAL;
+  if (n_bits > TM_MAX_BITS) return TM_ERANGE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<tmul::PlanParams> cands;
+  int rc = tmul::certified_candidates(kind, n_bits, 1.15, 8, &cands);
+  if (rc) return rc;
+  // operands: any bits do (the work does not depend on the values)
+  const size_t in_bytes = size_t(tmul::limbs_of(n_bits)) * 8;
+  const size_t out_bytes = size_t(tmul::out_limbs(kind, n_bits)) * 8;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * tmul::align_up(in_bytes) + out_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TM_ENOMEM;
+  }
+  uint64_t* du = reinterpret_cast<uint64_t*>(buf);
+  uint64_t* dv = reinterpret_cast<uint64_t*>(buf + tmul::align_up(in_bytes));
+  uint64_t* dout = reinterpret_cast<uint64_t*>(buf + 2 * tmul::align_up(in_bytes));
+  cudaMemsetAsync(du, 0x5a, in_bytes, s);
+  cudaMemsetAsync(dv, 0xa7, in_bytes, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const auto key = std::make_pair(kind, n_bits);
+  std::vector<double> ms(cands.size(), 0.0);
+  for (size_t c = 0; c < cands.size() && rc == TM_OK; ++c) {
+    {
+      std::lock_guard<std::mutex> lk(tmul::g_mu);
+      tmul::g_params[key] = cands[c];
+    }
+    std::vector<float> t;
+    for (int rep = 0; rep < 4 && rc == TM_OK; ++rep) {      // one warm-up, three timed
+      cudaEventRecord(e0, s);
+      rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
+      cudaEventRecord(e1, s);
+      if (rc == TM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TM_ECUDA;
+      float x = 0;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (rep) t.push_back(x);
+    }
+    if (rc) break;
+    std::sort(t.begin(), t.end());
+    ms[c] = t[t.size() / 2];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  tmul::PlanParams chosen = cands[0];
+  size_t best = 0;
+  if (rc == TM_OK) {
+    for (size_t c = 1; c < ms.size(); ++c)
+      if (ms[c] < ms[best]) best = c;
+    chosen = cands[best];
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(tmul::g_mu);
+    if (best == 0) tmul::g_params.erase(key);
+    else tmul::g_params[key] = chosen;
+    // tables of the candidates that lost and that nothing else holds
+    for (size_t c = 1; c < cands.size(); ++c) {
+      if (c == best) continue;
+      auto it = tmul::g_plans.find(std::make_tuple(dev, kind, cands[c].b, cands[c].N, 0));
+      if (it == tmul::g_plans.end()) continue;
+      if (it->second.use_count() == 1) {
+        tmul::PlanEntry& e = *it->second;
+        cudaFree(e.tw); cudaFree(e.fwd_tab); cudaFree(e.bwd_tab); cudaFree(e.bwd_tab2);
+        cudaFree(e.small);
+      } else {
+        tmul::g_retired.push_back(it->second);
+      }
+      tmul::g_plans.erase(it);
+    }
+  }
+  if (rc) return rc;
+  if (cudaGetLastError() != cudaSuccess) return TM_ECUDA;
+  out->b = uint32_t(chosen.b);
+  out->N = uint32_t(chosen.N);
+  out->candidates = uint32_t(cands.size());
+  out->ms_default = ms[0];
+  out->ms_best = ms[best];
+  return TM_OK;
+}
+
 int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout) {
   if (!layout) return TM_EINVAL;
   if (kind != TM_FULL && kind != TM_LO && kind != TM_HI) return TM_EINVAL;

@@ -324,6 +324,37 @@ int explicit_params(int kind, uint64_t n, int b, int64_t N, PlanParams* out) {
   return TM_OK;
 }
 
+int certified_candidates(int kind, uint64_t n, double span, int max_count,
+                         std::vector<PlanParams>* out) {
+  out->clear();
+  PlanParams best;
+  int rc = choose_params(kind, n, &best);
+  if (rc) return rc;
+  out->push_back(best);
+  const double top = span * double(best.N);
+  std::vector<PlanParams> rest;
+  for (int b = kBMin; b <= kBMax; ++b) {
+    int64_t lmin;
+    if (kind == TM_LO) lmin = std::max<int64_t>(3, int64_t((n + b - 1) / b));
+    else if (kind == TM_HI) lmin = std::max<int64_t>(3, int64_t((n + 2 + b - 1) / b) - 1);
+    else lmin = 2 * full_digit_count(n, b) - 1;
+    if (double(lmin) > top) continue;
+    for (int64_t N : candidate_lengths(lmin)) {
+      if (double(N) > top || (b == best.b && N == best.N)) continue;
+      PlanParams p;
+      if (explicit_params(kind, n, b, N, &p) == TM_OK && p.e_max <= kTarget) rest.push_back(p);
+    }
+  }
+  std::sort(rest.begin(), rest.end(), [](const PlanParams& x, const PlanParams& y) {
+    return x.N != y.N ? x.N < y.N : x.b > y.b;
+  });
+  for (const PlanParams& p : rest) {
+    if (int(out->size()) >= max_count) break;
+    out->push_back(p);
+  }
+  return TM_OK;
+}
+
 int64_t measured_length(int kind, uint64_t n, int b) {
   if (b < kBMin || b > kBMax) return -1;
   int64_t lmin;

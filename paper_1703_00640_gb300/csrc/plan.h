@@ -3,6 +3,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace tmul {
 
@@ -63,6 +64,12 @@ int choose_params(int kind, uint64_t n, PlanParams* out);
 // when b is outside [4, 24], N is not a supported length, or (b, N) violates the
 // hypotheses of Theorems 2.1-2.3 for n.
 int explicit_params(int kind, uint64_t n, int b, int64_t N, PlanParams* out);
+
+// Every certified plan (worst-case bound within the target) of (kind, n) whose
+// transform length is at most `span` times the planner's, the planner's own plan
+// first, the others by increasing N; at most max_count.
+int certified_candidates(int kind, uint64_t n, double span, int max_count,
+                         std::vector<PlanParams>* out);
 
 // Layout choices of the FFT passes that the autotuner varies: points a CTA aims to
 // hold (sequences per CTA = points / L), how the odd primes of M are distributed

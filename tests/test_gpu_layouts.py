@@ -110,3 +110,38 @@ def test_batch_with_forced_layout(pkg):
             b.close()
     finally:
         pkg.set_layout("lo", n)
+
+
+def _bound(kind, n, b, N):
+    E = {"lo": P.bound_lo, "hi": P.bound_hi, "full": P.bound_full}[kind](n, b, N)
+    return E[0] if isinstance(E, tuple) else (E["E"] if isinstance(E, dict) else E)
+
+
+@pytest.mark.parametrize("n", [100003, 1 << 20, 1 << 22])
+@pytest.mark.parametrize("kind", ["lo", "hi", "full"])
+def test_autotuned_plan_stays_exact(pkg, kind, n):
+    """tm_autotune_plan picks a plan the oracle planner's own bound certifies; products
+    with it are exact (high: the round(t) of Algorithm 3 for the chosen (b, N)), and
+    tm_plan_set(0, 0) restores the planner's choice."""
+    u, v = workloads.pattern_limbs("random", n, seed=n % 613)
+    du, dv = dev(u), dev(v)
+    try:
+        t = pkg.autotune_plan(kind, n)
+        assert 1 <= t["candidates"] <= 8 and 0 < t["ms_best"] <= t["ms_default"]
+        q = pkg.plan(kind, n)
+        assert (q["b"], q["N"]) == (t["b"], t["N"])
+        assert _bound(kind, n, t["b"], t["N"]) <= P.E_TARGET
+        out, rep = pkg.mul(kind, du, dv, n)
+        assert (rep["b"], rep["N"]) == (t["b"], t["N"])
+        assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
+        got = bigmul.to_int(host(out))
+        if kind == "hi":
+            want = T.trace("hi", bigmul.to_int(u), bigmul.to_int(v), n, t["b"], t["N"])["out"]
+        else:
+            want = _expect(kind, u, v, n)
+        assert got == want
+    finally:
+        pkg.plan_set(kind, n)
+    base = P.choose(kind, n)
+    q = pkg.plan(kind, n)
+    assert (q["b"], q["N"]) == (base["b"], base["N"])

@@ -9,6 +9,8 @@ import subprocess
 
 import pytest
 
+from oracle import plan as P
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "truncmul.h")
 
@@ -115,6 +117,17 @@ def test_host_side_errors(pkg):
     assert lib.tm_mul_params(1, fq, fp, fp, (1 << 31) + 1, ctypes.byref(prm), None,
                              None) == pkg.TM_ERANGE
     assert lib.tm_mul_params(1, fp, fp, fp, n, ctypes.byref(prm), None, None) == pkg.TM_EALIAS
+    # plan choice: checked (and, for tm_plan_set, applied) without a GPU
+    T = pkg.PlanTune()
+    assert lib.tm_autotune_plan(1, 1000, None, None) == pkg.TM_EINVAL
+    assert lib.tm_autotune_plan(5, 1000, None, ctypes.byref(T)) == pkg.TM_EINVAL
+    assert lib.tm_autotune_plan(1, 0, None, ctypes.byref(T)) == pkg.TM_EINVAL
+    assert lib.tm_autotune_plan(1, (1 << 31) + 1, None, ctypes.byref(T)) == pkg.TM_ERANGE
+    assert lib.tm_plan_set(7, 1000000, 9, 122880) == pkg.TM_EINVAL
+    assert lib.tm_plan_set(1, 0, 9, 122880) == pkg.TM_EINVAL
+    assert lib.tm_plan_set(1, 1000000, 9, 122881) == pkg.TM_EINVAL        # not a length
+    assert lib.tm_plan_set(1, 1000000, 14, 71680) == pkg.TM_ERANGE        # not certified
+    assert lib.tm_plan_set(1, 1000000, 0, 0) == pkg.TM_OK
     # layouts: checked before any CUDA call
     good = pkg.Tune(points=512, split=0, passes=3)
     assert lib.tm_set_layout(1, 100, None) == pkg.TM_EINVAL
@@ -156,3 +169,31 @@ def test_host_side_errors(pkg):
     assert lib.tm_barrett_destroy(None) == pkg.TM_OK
     for code in (0, -1, -2, -3, -4, -5, -6, -7, 99):
         assert pkg.strerror(code)
+
+
+def test_plan_set_changes_the_plan(pkg):
+    """tm_plan_set makes a certified (b, N) the plan of (kind, n) (tm_plan_query shows
+    it) and b = N = 0 restores the planner's choice; certification comes from the
+    oracle planner's independent bound."""
+    n = 1000000
+    for kind in ("lo", "hi", "full"):
+        base = P.choose(kind, n)
+        cand = None
+        for N in P.smooth_lengths_from(base["N"] + 1):
+            if kind == "hi" and not P.hi_ok(n, base["b"], N):
+                continue
+            E = {"lo": P.bound_lo, "hi": P.bound_hi, "full": P.bound_full}[kind](n, base["b"], N)
+            E = E[0] if isinstance(E, tuple) else (E["E"] if isinstance(E, dict) else E)
+            if E <= P.E_TARGET:
+                cand = N
+                break
+        assert cand is not None
+        pkg.plan_set(kind, n, base["b"], cand)
+        try:
+            q = pkg.plan(kind, n)
+            assert (q["b"], q["N"]) == (base["b"], cand)
+        finally:
+            pkg.plan_set(kind, n)
+        q = pkg.plan(kind, n)
+        assert (q["b"], q["N"]) == (base["b"], base["N"])
+
