@@ -53,7 +53,11 @@ def parse():
     ap.add_argument("--no-division", action="store_true",
                     help="skip the division timings")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default FFT layouts (no tm_autotune before timing)")
+                    help="keep the planner's plans and the default FFT layouts (no "
+                         "tm_autotune_plan / tm_autotune before timing)")
+    ap.add_argument("--plan", action="append", default=[], metavar="KIND:B:N",
+                    help="fix the plan of a product kind at the bench size with "
+                         "tm_plan_set (e.g. hi:7:2621440), instead of tuning it")
     ap.add_argument("--large-bits", type=int, default=1 << 28,
                     help="operand size of the large single-product section")
     ap.add_argument("--no-large", action="store_true",
@@ -393,10 +397,18 @@ def run_cuda(args):
     # the plan (b, N) among the certified candidates, then the FFT pass layout of
     # its length, picked by measurement (tm_autotune_plan, tm_autotune)
     tuned = None
+    fixed = {}
+    for spec in args.plan:
+        k, b, N = spec.split(":")
+        pkg.plan_set(k, n, int(b), int(N))
+        fixed[k] = {"b": int(b), "N": int(N)}
     if not args.no_autotune:
-        tuned = {"plans": {k: pkg.autotune_plan(k, n, stream=stream) for k in kinds}}
+        tuned = {"plans": {k: pkg.autotune_plan(k, n, stream=stream)
+                           for k in kinds if k not in fixed}}
         tuned["layouts"] = {k: pkg.autotune(k, n, stream=stream) for k in kinds}
-        plans = {k: pkg.plan(k, n) for k in kinds}
+    if fixed:
+        tuned = dict(tuned or {}, fixed_plans=fixed)
+    plans = {k: pkg.plan(k, n) for k in kinds}
 
     # correctness gate on the bench workload (sampled against the oracle's low product)
     _, rep = pkg.mul("lo", u, v, n, out=outs["lo"])

@@ -396,7 +396,8 @@ int tm_coeffs(int kind, int64_t* c_out, const uint64_t* u, const uint64_t* v, ui
  * factors of the length are spread over the passes, and the number of passes; each
  * is timed on `stream` (two forward transforms and one inverse, CUDA events, median
  * of three after a warm-up) on scratch buffers of 4 x 16 (N/2) bytes allocated for
- * the call. The fastest becomes the layout of every later plan with that length on
+ * the call. The fastest, if at least 1% faster than the default layout (else the
+ * default), becomes the layout of every later plan with that length on
  * this device (plans built before keep theirs for their current users, e.g. a
  * tm_batch). Results of products do not depend on the layout (they are exact);
  * only the time does. Waits for the stream. *out: candidates timed, the chosen
@@ -433,8 +434,9 @@ int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
  * Candidates: every certified plan (worst-case bound within the target, so every
  * result stays exact) whose transform length is at most 1.15x the planner's, the
  * planner's first, at most 8. Each runs whole products on scratch operands on
- * `stream` (one warm-up, median of three, CUDA events); the fastest becomes the
- * plan of (kind, n_bits) for later calls in this process (tm_mul and the calls
+ * `stream` (one warm-up, median of three, CUDA events); the fastest, if at least 1%
+ * faster than the planner's (else the planner's), becomes the plan of (kind, n_bits)
+ * for later calls in this process (tm_mul and the calls
  * built on it; tm_mul_static keeps the planner's). Low and full products do not
  * change; a high product may become the other admissible value. Tables of the
  * losing candidates are freed. Waits for the stream. *out: the chosen b and N,

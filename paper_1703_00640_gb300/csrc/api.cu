@@ -1135,6 +1135,9 @@ int tm_operand_destroy(tm_operand* op) {
   return e == cudaSuccess ? TM_OK : TM_ECUDA;
 }
 
+// An autotuner replaces the default only for a candidate at least 1% faster.
+constexpr double kTuneGain = 0.99;
+
 int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
   if (!out) return TM_EINVAL;
   std::memset(out, 0, sizeof(*out));
@@ -1215,6 +1218,7 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
   size_t best = 0;
   for (size_t c = 1; c < ms.size(); ++c)
     if (ms[c] < ms[best]) best = c;
+  if (ms[best] > kTuneGain * ms[0]) best = 0;     // within the noise: keep the default
   out->candidates = int32_t(plans.size());
   out->points = shapes[best].points;
   out->split = shapes[best].split;
@@ -1300,6 +1304,7 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
   if (rc == TM_OK) {
     for (size_t c = 1; c < ms.size(); ++c)
       if (ms[c] < ms[best]) best = c;
+    if (ms[best] > kTuneGain * ms[0]) best = 0;   // within the noise: keep the planner's
     chosen = cands[best];
   }
   int dev = 0;
