@@ -388,6 +388,27 @@ DevStatus* thread_status_host() {
 }
 }  // namespace
 
+int stream_status_word(cudaStream_t s, DevStatus* word, bool save) {
+  int dev = 0;
+  TM_CHECK(cudaGetDevice(&dev));
+  DevStatus* st = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, s));
+    if (it != g_ws.end()) st = it->second.status;
+  }
+  if (!st) {                     // no workspace yet: nothing pending, nothing to restore
+    if (save) *word = DevStatus{};
+    return TM_OK;
+  }
+  TM_CHECK(cudaStreamSynchronize(s));
+  if (save)
+    TM_CHECK(cudaMemcpy(word, st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+  else
+    TM_CHECK(cudaMemcpy(st, word, sizeof(DevStatus), cudaMemcpyHostToDevice));
+  return TM_OK;
+}
+
 int read_status(cudaStream_t s, DevStatus* status, tm_report* rep) {
   DevStatus st{};
   DevStatus* h = thread_status_host();
@@ -1272,6 +1293,11 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
   uint64_t* dout = reinterpret_cast<uint64_t*>(buf + 2 * tmul::align_up(in_bytes));
   cudaMemsetAsync(du, 0x5a, in_bytes, s);
   cudaMemsetAsync(dv, 0xa7, in_bytes, s);
+  tmul::DevStatus saved{};
+  if (tmul::stream_status_word(s, &saved, true) != TM_OK) {
+    cudaFree(buf);
+    return TM_ECUDA;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1299,6 +1325,9 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
+  // the stream's status word as the caller left it: the trial products' margins must
+  // not reach the next reported call
+  if (rc == TM_OK && tmul::stream_status_word(s, &saved, false) != TM_OK) rc = TM_ECUDA;
   tmul::PlanParams chosen = cands[0];
   size_t best = 0;
   if (rc == TM_OK) {

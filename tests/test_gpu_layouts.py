@@ -145,3 +145,27 @@ def test_autotuned_plan_stays_exact(pkg, kind, n):
     base = P.choose(kind, n)
     q = pkg.plan(kind, n)
     assert (q["b"], q["N"]) == (base["b"], base["N"])
+
+
+def test_autotune_plan_keeps_the_streams_status(pkg):
+    """tm_autotune_plan runs trial products on the caller's stream: a status pending
+    there before (here a flagged product) is still reported after, and the trials'
+    own margins are not."""
+    import torch
+    n = 100003
+    s = torch.cuda.Stream()
+    u, v = workloads.pattern_limbs("random", n, seed=2)
+    du, dv = dev(u), dev(v)
+    pl = P.choose("lo", n)
+    try:
+        pkg.mul_params("lo", du, dv, n, b=pl["b"], N=pl["N"], limit=1e-15, stream=s,
+                       report=False, check=False)
+        pkg.autotune_plan("hi", n, stream=s)
+        st = pkg.stream_status(s)
+        assert st["rc"] == pkg.TM_EPRECISION
+        pkg.autotune_plan("full", n, stream=s)          # nothing pending now
+        assert pkg.stream_status(s)["rc"] == 0
+        assert pkg.stream_status(s)["margin"] == 0.0
+    finally:
+        pkg.plan_set("hi", n)
+        pkg.plan_set("full", n)
