@@ -26,7 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50/p99 ms"
 UNIT = "Gbit/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs)
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 FP64_DFMA_MEASURED = 1.008   # DFMA/DADD/DMUL issue ceiling measured on this GB300 pool
 # DRAM bytes per k_fft_pass launch from profiles/k_fft_pass_n2p24.md (n = 2^24 only)
 FFT_TRAFFIC_N2P24 = 23.5e6
