@@ -592,7 +592,7 @@ def run_cuda(args):
     if not args.no_paper_params:
         paper_params = run_paper_params(pkg, torch, np, workloads, max(3, min(args.steps, 7)),
                                         args.warmup, stream, flush, seed=2017 + rank)
-        pkg.release()                   # the rows' plan tables (about 20 GB)
+        pkg.release()                   # the rows' plan tables (about 50 GB)
 
     large = None
     if not args.no_large:
@@ -765,19 +765,17 @@ def table2_rows():
 
 
 def run_paper_params(pkg, torch, np, workloads, reps, warmup, stream, flush, seed,
-                     max_bits=1 << 28):
-    """Every Table 2 row with n <= max_bits (the certified plans of the two larger rows
-    hold 50-80 GB of map tables): low and high products with the paper's (N, b) and the full
-    product with its (2N, b) through tm_mul_params (b chosen by experiment, not
-    certified: the acceptance limit is 3/8), next to the certified plans of tm_mul
-    at the same n. Per row: device times (CUDA events, L2 flushed, median), the
+                     certified_max_bits=1 << 28):
+    """Every Table 2 row (n < 2^31): low and high products with the paper's (N, b) and
+    the full product with its (2N, b) through tm_mul_params (b chosen by experiment, not
+    certified: the acceptance limit is 3/8), next to the certified plans of tm_mul at
+    the same n for n <= certified_max_bits (above, their map tables alone take 50-80
+    GB). Per row: device times (CUDA events, L2 flushed, median), the
     ratios t_lo / t_full and t_hi / t_full in both settings, margins and statuses;
     the low product is checked against the full product's low bits and the high
     product against the admissible values."""
     out_rows = []
     for n, N, b, lam, L, bf in table2_rows():
-        if n > max_bits:
-            continue
         u_np, v_np = workloads.pattern_limbs("random", n, seed=seed)
         u = torch.from_numpy(u_np.view(np.int64)).cuda()
         v = torch.from_numpy(v_np.view(np.int64)).cuda()
@@ -806,7 +804,8 @@ def run_paper_params(pkg, torch, np, workloads, reps, warmup, stream, flush, see
         full = _as_int(outs["full"])
         row["lo_equals_full_low_bits"] = _as_int(outs["lo"]) == full & ((1 << n) - 1)
         row["hi_admissible"] = _as_int(outs["hi"]) in (full >> n, (full >> n) + 1)
-        for k in ("lo", "hi", "full"):
+        del full
+        for k in (("lo", "hi", "full") if n <= certified_max_bits else ()):
             o = torch.empty_like(outs[k])
             _, rep = pkg.mul(k, u, v, n, out=o, stream=stream)
             ev = []
@@ -821,8 +820,12 @@ def run_paper_params(pkg, torch, np, workloads, reps, warmup, stream, flush, see
             torch.cuda.synchronize()
             row["certified"][k] = {"b": rep["b"], "N": rep["N"], "margin": rep["margin"],
                                    "ms": statistics.median(a.elapsed_time(c) for a, c in ev)}
+        if not row["certified"]:
+            row["certified"] = None
         for setting in ("paper", "certified"):
             r = row[setting]
+            if r is None:
+                continue
             r["t_lo_over_full"] = r["lo"]["ms"] / r["full"]["ms"]
             r["t_hi_over_full"] = r["hi"]["ms"] / r["full"]["ms"]
             r["trunc_gbit_s"] = 2 * n / ((r["lo"]["ms"] + r["hi"]["ms"]) * 1e-3) / 1e9
