@@ -68,6 +68,8 @@ def parse():
                     help="products of the large section (comma list of lo, hi, full)")
     ap.add_argument("--no-paper-params", action="store_true",
                     help="skip the products with the paper's Table 2 parameters")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the single products at n = 2^16 and 2^20")
     return ap.parse_args()
 
 
@@ -588,6 +590,12 @@ def run_cuda(args):
                             "corrections; reciprocal by Newton iteration, host-timed "
                             "(it waits for the stream)"}
 
+    sizes = None
+    if not args.no_sizes:
+        sizes = run_sizes(pkg, torch, np, workloads, (1 << 16, 1 << 20),
+                          max(5, min(args.steps, 50)), args.warmup, stream, flush, seed=16 + rank,
+                          tune=not args.no_autotune)
+
     paper_params = None
     if not args.no_paper_params:
         paper_params = run_paper_params(pkg, torch, np, workloads, max(3, min(args.steps, 7)),
@@ -646,6 +654,7 @@ def run_cuda(args):
                              "against the measured DFMA issue ceiling; traffic = ncu DRAM "
                              "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
         "batched": batched,
+        "sizes": sizes,
         "large": large,
         "paper_parameters": paper_params,
         "autotune": tuned,
@@ -750,6 +759,49 @@ def run_large(pkg, torch, np, workloads, n, reps, warmup, stream, flush, seed,
     return {"n_bits": n, "operands": "uniform random uint64 limbs (seeded PCG64)",
             "l2": "flushed (256 MB write) before every product", "reps": reps,
             **checks, "fp64_peak_tflops": FP64_PEAK_TFLOPS, **res}
+
+
+def run_sizes(pkg, torch, np, workloads, sizes, reps, warmup, stream, flush, seed,
+              tune=True):
+    """Single products at the smaller configuration sizes (n = 2^16 and 2^20): per kind
+    the device time (CUDA events, L2 flushed, median), Gbit/s, the t_lo / t_full and
+    t_hi / t_full ratios, the plan (tuned with tm_autotune_plan unless tune is off),
+    and the margin on uniformly random operands and on all-ones operands (the largest
+    coefficients the digit size admits)."""
+    out = {}
+    for n in sizes:
+        if tune:
+            for k in ("lo", "hi", "full"):
+                pkg.autotune_plan(k, n, stream=stream)
+        u_np, v_np = workloads.pattern_limbs("random", n, seed=seed)
+        one_np, _ = workloads.pattern_limbs("ones", n)
+        u = torch.from_numpy(u_np.view(np.int64)).cuda()
+        v = torch.from_numpy(v_np.view(np.int64)).cuda()
+        ones = torch.from_numpy(one_np.view(np.int64)).cuda()
+        row = {}
+        for k in ("lo", "hi", "full"):
+            o = torch.empty(pkg.out_limbs(k, n), dtype=torch.int64, device="cuda")
+            _, rep = pkg.mul(k, u, v, n, out=o, stream=stream)
+            _, rep1 = pkg.mul(k, ones, ones, n, out=o, stream=stream)
+            ev = []
+            for i in range(warmup + reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.mul(k, u, v, n, out=o, stream=stream, report=False)
+                e1.record(stream)
+                if i >= warmup:
+                    ev.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(c) for a, c in ev)
+            row[k] = {"ms": ms, "gbit_s": n / (ms * 1e-3) / 1e9, "b": rep["b"], "N": rep["N"],
+                      "margin_random": rep["margin"], "margin_all_ones": rep1["margin"],
+                      "e_max": rep["e_max"], "status": max(rep["status"], rep1["status"],
+                                                           key=abs)}
+        row["t_lo_over_full"] = row["lo"]["ms"] / row["full"]["ms"]
+        row["t_hi_over_full"] = row["hi"]["ms"] / row["full"]["ms"]
+        out[str(n)] = row
+    return out
 
 
 def table2_rows():
