@@ -6,7 +6,14 @@ default: the single-product configuration at n = 2^24 bits. The headline value
 is the truncated-product throughput, operand bits per second over the low and
 high products (2 n bits / (t_lo + t_hi)); the full product gives the
 t_trunc / t_full ratios. Each product is timed with CUDA events on its stream,
-with the L2 flushed (256 MB written) between products.
+with the L2 flushed (256 MB written) between products. Before timing, the plans
+(b, N) and the FFT layouts are tuned (tm_autotune_plan, tm_autotune).
+
+Further sections of the JSON line: end to end from page-locked host memory
+(e2e), squares / kept operands / data-dependent digit size, Barrett division,
+single products at n = 2^16 and 2^20 (sizes), the paper's Table 2 parameters
+(paper_parameters), n = 2^28 (large), the 4096-product batch (batched), and the
+CPU oracle on the host cores (cpu_baseline). --served runs the served stream.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 Multi-GPU (torchrun, one rank per GPU): replicas, each rank multiplies its own
