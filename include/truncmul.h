@@ -455,8 +455,8 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
 
 /*
  * tm_plan_set: makes the certified plan (b, N) the plan of (kind, n_bits) for later
- * calls in this process (for example one chosen by tm_autotune_plan earlier);
- * b = N = 0 restores the planner's choice. TM_EINVAL for parameters outside the
+ * calls in this process (for example one chosen by tm_autotune_plan earlier; as
+ * there, tm_mul_static keeps the planner's); b = N = 0 restores the planner's choice. TM_EINVAL for parameters outside the
  * ranges of tm_mul_params, TM_ERANGE when the worst-case bound for (b, N) is above
  * the target (use tm_mul_params for uncertified parameters).
  */
