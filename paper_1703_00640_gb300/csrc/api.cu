@@ -409,9 +409,9 @@ int stream_status_word(cudaStream_t s, DevStatus* word, bool save) {
   return TM_OK;
 }
 
-int read_status(cudaStream_t s, DevStatus* status, tm_report* rep) {
+int read_status(cudaStream_t s, DevStatus* status, tm_report* rep, bool may_allocate) {
   DevStatus st{};
-  DevStatus* h = thread_status_host();
+  DevStatus* h = may_allocate ? thread_status_host() : nullptr;
   DevStatus* hd = nullptr;
   if (h && cudaHostGetDevicePointer(reinterpret_cast<void**>(&hd), h, 0) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -797,7 +797,7 @@ int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, ui
   if (!rep) return TM_OK;
   fill_plan_report(pe.p, pe.fft, rep);
   rep->table_bytes = 0;
-  return read_status(s, ws.status, rep);
+  return read_status(s, ws.status, rep, false);
 }
 
 }  // namespace

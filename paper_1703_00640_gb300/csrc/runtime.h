@@ -80,7 +80,9 @@ int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
                       double* theta);
 // Single-pass plan tables of a CTA-resident product, and its per-product item.
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe);
-int read_status(cudaStream_t s, DevStatus* status, tm_report* rep);
+// Waits for s, reads the status word into *rep and resets it. may_allocate = false
+// keeps to calls that allocate nothing (no page-locked status buffer).
+int read_status(cudaStream_t s, DevStatus* status, tm_report* rep, bool may_allocate = true);
 // Waits for s and copies the status word of its workspace out (save) or back in.
 int stream_status_word(cudaStream_t s, DevStatus* word, bool save);
 void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep);
