@@ -197,3 +197,35 @@ def test_plan_set_changes_the_plan(pkg):
         q = pkg.plan(kind, n)
         assert (q["b"], q["N"]) == (base["b"], base["N"])
 
+
+
+@pytest.mark.parametrize("n", [1000, 65536, 1000003, 1 << 24])
+def test_plan_set_certification_matches_oracle_bound(pkg, n):
+    """tm_plan_set accepts (b, N) exactly when the oracle planner's independent
+    worst-case bound for (b, N) is within the target (and rejects lengths that
+    break the hypotheses of Theorems 2.1-2.3 as invalid)."""
+    lib = pkg.load()
+    bound = {"lo": P.bound_lo, "hi": P.bound_hi, "full": P.bound_full}
+    kinds = {"lo": 1, "hi": 2, "full": 0}
+    checked = 0
+    for kind in ("lo", "hi", "full"):
+        base = P.choose(kind, n)
+        for b in (base["b"] - 1, base["b"], base["b"] + 1):
+            if kind == "lo":
+                x = P.min_len_lo(n, b)
+            elif kind == "hi":
+                x = P.min_len_hi(n, b)
+            else:
+                x = 2 * P.full_digits(n, b) - 1
+            for N in list(P.smooth_lengths_from(x))[:4]:
+                if kind == "hi" and not P.hi_ok(n, b, N):
+                    continue
+                E = bound[kind](n, b, N)
+                E = E[0] if isinstance(E, tuple) else (E["E"] if isinstance(E, dict) else E)
+                if abs(E - P.E_TARGET) < 1e-9 * P.E_TARGET:
+                    continue                      # too close to call across two codes
+                rc = lib.tm_plan_set(kinds[kind], n, b, N)
+                assert rc == (pkg.TM_OK if E <= P.E_TARGET else pkg.TM_ERANGE), (kind, b, N, E)
+                checked += 1
+        lib.tm_plan_set(kinds[kind], n, 0, 0)
+    assert checked >= 12
