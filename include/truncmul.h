@@ -179,7 +179,8 @@ int tm_mul_adaptive(int kind, uint64_t* out, const uint64_t* u, const uint64_t* 
  * device's address space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister
  * with mapping, on a 64-bit system) and out_host overlaps neither input, the
  * kernels read the operands and write the product in host memory directly (over
- * NVLink-C2C on a GB300): no staging copies.
+ * NVLink-C2C on a GB300): no staging copies. A page-locked out_host must then be
+ * writable from the device (not registered with cudaHostRegisterReadOnly).
  * Otherwise it copies u and v to the device, runs tm_mul on `stream` and copies
  * the result back. On a created stream (not NULL, the legacy or the per-thread
  * default stream) that sequence is recorded once per (stream, kind, n_bits) as a
