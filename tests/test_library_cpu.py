@@ -229,3 +229,19 @@ def test_plan_set_certification_matches_oracle_bound(pkg, n):
                 checked += 1
         lib.tm_plan_set(kinds[kind], n, 0, 0)
     assert checked >= 12
+
+
+def test_plan_matches_oracle_plan_random_sizes(pkg):
+    """The C++ planner and the oracle's planner agree on (b, N, lambda, e_max) for 200
+    seeded sizes, log-uniform over [1, 2^31]."""
+    import random
+    rnd = random.Random(1703)
+    for _ in range(200):
+        n = int(2 ** rnd.uniform(0, 31))
+        kind = rnd.choice(("lo", "hi", "full"))
+        mine = pkg.plan(kind, n)
+        ref = P.choose(kind, n)
+        assert (mine["b"], mine["N"], mine["n_digits"]) == \
+            (ref["b"], ref["N"], ref["n_digits"]), (kind, n)
+        assert (mine["lam_fwd"], mine["lam_bwd"]) == (ref["lam_fwd"], ref["lam_bwd"]), (kind, n)
+        assert mine["e_max"] == pytest.approx(ref["e_max"], rel=1e-9), (kind, n)
