@@ -51,10 +51,10 @@ def test_fp64_reference_matches_exact_trace(n, pattern):
         assert r["margin"] <= p["e_max"]
 
 
-@pytest.mark.parametrize("row", golden("table2_params.txt")[:1])
+@pytest.mark.parametrize("row", golden("table2_params.txt")[:3])
 def test_table2_replay(row):
-    """Table 2, n = 10^6: N = 71680 = 2^11 * 35, b = 14, lambda = 4 for both
-    truncated products; 2N = 98304, b = 21 for the full product."""
+    """Table 2, n = 10^6 (N = 71680 = 2^11 * 35, b = 14, lambda = 4 for both truncated
+    products; 2N = 98304, b = 21 for the full product), 2154434 and 4641588."""
     n, N, b, lam, L, bf = map(int, row)
     rnd = random.Random(2017)
     nl = (n + 63) // 64
