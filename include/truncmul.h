@@ -55,6 +55,10 @@ extern "C" {
 
 /* ---- status codes (0 = success) ---- */
 #define TM_OK          0
+#define TM_UNCERTIFIED 1   /* success of tm_mul_params with a (b, N) whose
+                              worst-case bound is at or above 1/2: every rounding
+                              distance stayed within the caller's limit, but the
+                              result is not certified                            */
 #define TM_EINVAL     -1   /* bad argument: n = 0, NULL pointer, unknown kind    */
 #define TM_ENOMEM     -2   /* device or host allocation failed                   */
 #define TM_EPRECISION -3   /* margin above the a-priori bound, or 2^b not
@@ -83,7 +87,8 @@ extern "C" {
 /* Plan and outcome of one call. */
 typedef struct tm_report {
   int32_t  kind;      /* TM_FULL, TM_LO or TM_HI                                  */
-  int32_t  status;    /* device-side status of the call (TM_OK or TM_EPRECISION)  */
+  int32_t  status;    /* device-side status of the call (TM_OK, TM_EPRECISION, or
+                         TM_UNCERTIFIED from tm_mul_params)                       */
   uint32_t b;         /* digit size in bits                                       */
   uint32_t N;         /* real transform length (N of Algorithms 2/3; the cyclic
                          length >= 2 n_digits - 1 of Algorithm 1)                 */
@@ -138,10 +143,12 @@ int tm_mul(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64
  *   prm->limit  the largest rounding distance the call accepts, in [0, 1/2];
  *               0 = e_max when e_max < 1/2, else 3/8.
  * lambda comes from the library's tail budgets for b. rep->e_max is the
- * worst-case bound for (b, N): at or above 1/2 the result is NOT certified (the
- * paper's own setting) and the limit is a heuristic: a product whose errors
- * reach 1/2 almost surely also has distances near 1/2, so operands too large for
- * b show up as TM_EPRECISION. With the paper's Table 2 parameters the largest
+ * worst-case bound for (b, N). Below 1/2 the result is certified and the call
+ * returns TM_OK. At or above 1/2 (the paper's own setting) the result is NOT
+ * certified: the call then returns TM_UNCERTIFIED (a positive code, also in
+ * rep->status) in place of TM_OK, and the limit is only a heuristic - a product
+ * whose errors reach 1/2 usually also has distances near 1/2, so operands too
+ * large for b usually show up as TM_EPRECISION, but nothing guarantees it. With the paper's Table 2 parameters the largest
  * distance on random operands is about 1/4 (n = 10^6, b = 14). Other arguments,
  * layout and errors as tm_mul; TM_EINVAL also for a NULL prm or parameters
  * outside the ranges above.
@@ -226,6 +233,11 @@ int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
  *   the next call (each call rebuilds its tables and clears its status word), so
  *   calls that overlap on the GPU - on different streams, threads or in flight
  *   at once - race and must be serialised by the caller.
+ *   Cost of the rebuild: before the product, every call enqueues one memset and
+ *   four to six small table kernels (twiddles, tangent-form and twist tables, map
+ *   rows, and for the high product kappa and rho^-j, all computed on the
+ *   device; no host-to-device copy), a few microseconds next to the product's
+ *   own kernels at n = 65536.
  *   rep as for tm_mul (NULL = asynchronous; a non-NULL rep waits and reports).
  */
 #define TM_STATIC_MAX_BITS 65536

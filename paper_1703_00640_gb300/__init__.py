@@ -12,10 +12,11 @@ import os
 from . import build as _build
 
 KIND = {"full": 0, "lo": 1, "hi": 2}
-STATUS = {0: "TM_OK", -1: "TM_EINVAL", -2: "TM_ENOMEM", -3: "TM_EPRECISION", -4: "TM_ETIMEOUT",
+STATUS = {0: "TM_OK", 1: "TM_UNCERTIFIED", -1: "TM_EINVAL", -2: "TM_ENOMEM", -3: "TM_EPRECISION", -4: "TM_ETIMEOUT",
           -5: "TM_ECUDA", -6: "TM_ERANGE", -7: "TM_EALIAS"}
 TM_OK, TM_EINVAL, TM_ENOMEM, TM_EPRECISION, TM_ETIMEOUT, TM_ECUDA, TM_ERANGE, TM_EALIAS = (
     0, -1, -2, -3, -4, -5, -6, -7)
+TM_UNCERTIFIED = 1
 
 
 class Report(ctypes.Structure):
@@ -226,7 +227,8 @@ def mul(kind, u, v, n_bits: int, out=None, stream=None, report: bool = True, che
 def mul_params(kind, u, v, n_bits: int, b: int, N: int, limit: float = 0.0, out=None,
                stream=None, report: bool = True, check: bool = True):
     """tm_mul_params: the product with the caller's digit size b and transform
-    length N (the paper's empirical parameters). Returns (out, report dict or None)."""
+    length N (the paper's empirical parameters). Returns (out, report dict or None);
+    report["status"] is TM_UNCERTIFIED when (b, N) is outside the worst-case bound."""
     import torch
     k = _kind(kind)
     if out is None:
@@ -236,7 +238,7 @@ def mul_params(kind, u, v, n_bits: int, b: int, N: int, limit: float = 0.0, out=
     rc = load().tm_mul_params(k, _ptr(out), _ptr(u), _ptr(v), int(n_bits), ctypes.byref(prm),
                               _stream_ptr(stream),
                               ctypes.byref(rep) if rep is not None else None)
-    if check and rc:
+    if check and rc < 0:             # TM_UNCERTIFIED (> 0) is a result, not an error
         raise TruncMulError(rc, "tm_mul_params")
     return out, (rep.as_dict() if rep is not None else None)
 

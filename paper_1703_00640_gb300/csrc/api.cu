@@ -671,10 +671,17 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
   if (rc) return rc;
   rc = enqueue(kind, out, u, v, n, s, p, *pe, *ws, coeff_out, events);
   if (rc) return rc;
-  if (!rep) return TM_OK;
+  // a caller's (b, N) outside the worst-case bound never reports plain success
+  const bool certified = p.e_max < 0.5;
+  if (!rep) return certified ? TM_OK : TM_UNCERTIFIED;
   fill_plan_report(p, pe->fft, rep);
   rep->table_bytes = pe->table_bytes;
-  return read_status(s, ws->status, rep);
+  rc = read_status(s, ws->status, rep);
+  if (rc == TM_OK && !certified) {
+    rc = TM_UNCERTIFIED;
+    rep->status = rc;
+  }
+  return rc;
 }
 
 // ------------------------------------------- products without allocation
@@ -734,7 +741,6 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   while ((int64_t(1) << lgN) < N) ++lgN;
   const int nkappa = kind == TM_HI ? int(std::min<int64_t>(N, 3 + (lgN + 64 + b - 1) / b)) : 0;
   const int ntheta = kind == TM_HI ? int(std::min<int64_t>(N + 1, (60 + b - 1) / b + 3)) : 0;
-  double host_small[96];
   if (nkappa + ntheta > 96) return TM_ERANGE;
   const size_t small_off = take(size_t(nkappa + ntheta) * 8);
   const size_t ws_bytes = workspace_bytes(e->p);
@@ -760,14 +766,9 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
     launch_init_maptab(e->bwd_tab, kind == TM_LO ? kTabBeta : kTabDeltaPrime, N, b,
                        kind == TM_LO ? rb : e->p.lam_bwd, s);
   if (r2 > 0) launch_init_maptab(e->bwd_tab2, kTabDelta, N, b, r2, s);
-  if (kind == TM_HI) {
-    const double lr = std::log(e->p.rho);
-    for (int i = 0; i < nkappa; ++i) host_small[i] = std::exp(b * std::log(2.0) - (i + 1) * lr);
-    for (int j = 0; j < ntheta; ++j) host_small[nkappa + j] = std::exp(-j * lr);
-    // pageable source: the copy has consumed host_small when the call returns
-    TM_CHECK(cudaMemcpyAsync(e->small, host_small, size_t(nkappa + ntheta) * 8,
-                             cudaMemcpyHostToDevice, s));
-  }
+  // kappa and rho^-j computed on the device: no host-to-device copy, so a call
+  // without a report enqueues only kernels and one memset
+  if (kind == TM_HI) launch_init_rho_powers(e->small, nkappa, ntheta, b, std::log(e->p.rho), s);
   return TM_OK;
 }
 
@@ -781,10 +782,10 @@ int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, ui
   if (overlaps(out, ob, u, in_bytes) || overlaps(out, ob, v, in_bytes)) return TM_EALIAS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PlanEntry pe;
-  int rc = choose_params_noalloc(kind, n, &pe.p);
+  int rc = choose_params(kind, n, &pe.p);
   if (rc) return rc;
   pe.M = pe.p.N / 2;
-  rc = make_fft_plan_noalloc(pe.M, &pe.fft);
+  rc = make_fft_plan(pe.M, &pe.fft);
   if (rc) return rc;
   char* base = nullptr;
   rc = static_scratch(&base);
@@ -1478,6 +1479,7 @@ int tm_release(void) {
 const char* tm_strerror(int code) {
   switch (code) {
     case TM_OK: return "ok";
+    case TM_UNCERTIFIED: return "ok within the caller's limit, not certified by the error bound";
     case TM_EINVAL: return "invalid argument";
     case TM_ENOMEM: return "out of memory";
     case TM_EPRECISION: return "rounding margin above the error bound: result not trusted";

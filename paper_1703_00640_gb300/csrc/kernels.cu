@@ -197,6 +197,15 @@ __global__ void k_init_maptab_fx(long long* tab, int which, long long N, int b, 
   }
 }
 
+// High product: tab[i] = kappa_i = 2^b / rho^(i+1) (eq. 4.4), i < nkappa, then
+// tab[nkappa + j] = rho^-j, j < ntheta, from lr = ln rho; the host planner's
+// formula, evaluated on the device so that a call needs no host-to-device copy.
+__global__ void k_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nkappa) tab[i] = exp(b * 0.6931471805599453 - (i + 1) * lr);
+  else if (i < nkappa + ntheta) tab[i] = exp(-(i - nkappa) * lr);
+}
+
 // ------------------------------------------------------------ digits
 
 // bits [pos, pos + cnt) of the n-bit integer in `limbs` (cnt <= 32, pos may be
@@ -1824,6 +1833,13 @@ void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int ro
                            cudaStream_t s) {
   if (rows <= 0) return;
   k_init_maptab_fx<<<unsigned((N + 255) / 256), 256, 0, s>>>(tab, which, N, b, rows, Q);
+}
+
+void launch_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr,
+                            cudaStream_t s) {
+  if (nkappa + ntheta <= 0) return;
+  k_init_rho_powers<<<unsigned((nkappa + ntheta + 127) / 128), 128, 0, s>>>(tab, nkappa, ntheta,
+                                                                           b, lr);
 }
 
 void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cudaStream_t s) {

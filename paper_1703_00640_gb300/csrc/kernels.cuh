@@ -218,6 +218,11 @@ void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cu
 void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,
                            cudaStream_t s);
 
+// High product: tab[i] = 2^b / rho^(i+1), i < nkappa, then tab[nkappa + j] = rho^-j,
+// j < ntheta (lr = ln rho).
+void launch_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr,
+                            cudaStream_t s);
+
 // Sums of squares of the balanced digits of u and v (and the top digits of the high
 // product) into sums[0..3] (zeroed by the caller).
 void launch_digit_norms(const unsigned long long* u, const unsigned long long* v,

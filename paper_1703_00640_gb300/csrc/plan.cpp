@@ -252,6 +252,10 @@ int64_t smooth_at_least(int64_t x) {
   return best;
 }
 
+// No heap allocation (tm_mul_static plans with it): for each b the candidate
+// lengths are walked per odd part, stopping at the first certified one or at the
+// shortest found so far, which gives the shortest certified length up to kSpan x
+// the minimal one.
 int choose_params(int kind, uint64_t n, PlanParams* out) {
   if (n == 0 || (kind != TM_FULL && kind != TM_LO && kind != TM_HI)) return TM_EINVAL;
   if (n > TM_MAX_BITS) return TM_ERANGE;
@@ -267,30 +271,41 @@ int choose_params(int kind, uint64_t n, PlanParams* out) {
     } else {
       lmin = 2 * full_digit_count(n, b) - 1;
     }
-    for (int64_t N : candidate_lengths(lmin)) {
-      if (kind == TM_HI && !hi_hypothesis(n, b, N)) continue;
-      double E;
-      int lf = 0, lb = 0;
-      int64_t nd;
-      if (kind == TM_LO) {
-        Bound B = bound_lo(b, N);
-        E = B.E; lf = B.lf; lb = B.lb; nd = N;
-      } else if (kind == TM_HI) {
-        Bound B = bound_hi(b, N);
-        E = B.E; lf = B.lf; lb = B.lb; nd = N + 1;
-      } else {
-        E = bound_full(n, b, N);
-        nd = full_digit_count(n, b);
-      }
-      if (E <= kTarget) {
-        if (!found || N < best.N || (N == best.N && b > best.b)) {
-          best.kind = kind; best.n = n; best.b = b; best.N = N; best.n_digits = nd;
-          best.lam_fwd = lf; best.lam_bwd = lb; best.e_max = E;
-          best.rho = kind == TM_HI ? rho_of(N, b) : 0.0;
-          found = true;
+    const int64_t x = std::max<int64_t>(4, lmin);
+    const int64_t top = std::max<int64_t>(smooth_at_least(x), int64_t(kSpan * double(x)));
+    PlanParams cand;
+    bool have = false;
+    for (int m : kOddParts) {
+      int64_t N = 2 * int64_t(m);
+      while (N < x) N *= 2;
+      for (; N <= top; N *= 2) {
+        if (have && N >= cand.N) break;
+        if (kind == TM_HI && !hi_hypothesis(n, b, N)) continue;
+        double E;
+        int lf = 0, lb = 0;
+        int64_t nd;
+        if (kind == TM_LO) {
+          Bound B = bound_lo(b, N);
+          E = B.E; lf = B.lf; lb = B.lb; nd = N;
+        } else if (kind == TM_HI) {
+          Bound B = bound_hi(b, N);
+          E = B.E; lf = B.lf; lb = B.lb; nd = N + 1;
+        } else {
+          E = bound_full(n, b, N);
+          nd = full_digit_count(n, b);
         }
-        break;
+        if (E <= kTarget) {
+          cand.kind = kind; cand.n = n; cand.b = b; cand.N = N; cand.n_digits = nd;
+          cand.lam_fwd = lf; cand.lam_bwd = lb; cand.e_max = E;
+          cand.rho = kind == TM_HI ? rho_of(N, b) : 0.0;
+          have = true;
+          break;
+        }
       }
+    }
+    if (have && (!found || cand.N < best.N || (cand.N == best.N && b > best.b))) {
+      best = cand;
+      found = true;
     }
   }
   if (!found) return TM_ERANGE;
@@ -441,15 +456,17 @@ int make_fft_plan(int64_t M, FftPlan* out, bool single, const FftShape* shape_in
   const FftShape sh = shape_in ? *shape_in : FftShape{};
   FftPlan f;
   f.M = M;
-  std::vector<int> primes;
+  int primes[64];                 // no heap allocation (tm_mul_static plans with it)
+  int nprimes = 0;
   int64_t rest = M;
   for (int p : {7, 5, 3, 2})
-    while (rest % p == 0) { primes.push_back(p); rest /= p; }
+    while (rest % p == 0 && nprimes < 64) { primes[nprimes++] = p; rest /= p; }
   if (rest != 1) return TM_EINVAL;
   int np = single ? 1 : (M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3));
   if (!single && M > 64 && (sh.passes == 2 || sh.passes == 3)) np = sh.passes;
   int64_t Ls[kMaxPasses] = {1, 1, 1};
-  for (int p : primes) {
+  for (int ip = 0; ip < nprimes; ++ip) {
+    const int p = primes[ip];
     int best = 0;
     if (p != 2 && sh.split == 1) {
       best = 0;                             // odd primes to the first pass
@@ -491,117 +508,6 @@ int make_fft_plan(int64_t M, FftPlan* out, bool single, const FftShape* shape_in
   for (int i = 0; i < np; ++i) {
     radices_of(f.pass[i].L, &f.pass[i]);
     shape(&f.pass[i], want, std::max(32, sh.points));
-  }
-  *out = f;
-  return TM_OK;
-}
-
-// ------------------------------------------------ allocation-free variants
-
-int choose_params_noalloc(int kind, uint64_t n, PlanParams* out) {
-  if (n == 0 || (kind != TM_FULL && kind != TM_LO && kind != TM_HI)) return TM_EINVAL;
-  if (n > TM_MAX_BITS) return TM_ERANGE;
-  bool found = false;
-  PlanParams best;
-  for (int b = kBMin; b <= kBMax; ++b) {
-    int64_t lmin;
-    if (kind == TM_LO) {
-      lmin = std::max<int64_t>(3, int64_t((n + b - 1) / b));
-    } else if (kind == TM_HI) {
-      lmin = std::max<int64_t>(3, int64_t((n + 2 + b - 1) / b) - 1);
-      while (!hi_hypothesis(n, b, lmin)) ++lmin;
-    } else {
-      lmin = 2 * full_digit_count(n, b) - 1;
-    }
-    const int64_t x = std::max<int64_t>(4, lmin);
-    const int64_t top = std::max<int64_t>(smooth_at_least(x), int64_t(kSpan * double(x)));
-    // the shortest candidate length that meets the bound, as in choose_params
-    PlanParams cand;
-    bool have = false;
-    for (int m : kOddParts) {
-      int64_t N = 2 * int64_t(m);
-      while (N < x) N *= 2;
-      for (; N <= top; N *= 2) {
-        if (have && N >= cand.N) break;
-        if (kind == TM_HI && !hi_hypothesis(n, b, N)) continue;
-        double E;
-        int lf = 0, lb = 0;
-        int64_t nd;
-        if (kind == TM_LO) {
-          Bound B = bound_lo(b, N);
-          E = B.E; lf = B.lf; lb = B.lb; nd = N;
-        } else if (kind == TM_HI) {
-          Bound B = bound_hi(b, N);
-          E = B.E; lf = B.lf; lb = B.lb; nd = N + 1;
-        } else {
-          E = bound_full(n, b, N);
-          nd = full_digit_count(n, b);
-        }
-        if (E <= kTarget) {
-          cand.kind = kind; cand.n = n; cand.b = b; cand.N = N; cand.n_digits = nd;
-          cand.lam_fwd = lf; cand.lam_bwd = lb; cand.e_max = E;
-          cand.rho = kind == TM_HI ? rho_of(N, b) : 0.0;
-          have = true;
-          break;
-        }
-      }
-    }
-    if (have && (!found || cand.N < best.N || (cand.N == best.N && b > best.b))) {
-      best = cand;
-      found = true;
-    }
-  }
-  if (!found) return TM_ERANGE;
-  *out = best;
-  return TM_OK;
-}
-
-int make_fft_plan_noalloc(int64_t M, FftPlan* out) {
-  FftPlan f;
-  f.M = M;
-  int primes[64];
-  int nprimes = 0;
-  int64_t rest = M;
-  for (int p : {7, 5, 3, 2})
-    while (rest % p == 0 && nprimes < 64) { primes[nprimes++] = p; rest /= p; }
-  if (rest != 1) return TM_EINVAL;
-  const int np = M <= 64 ? 1 : (M <= (int64_t(1) << 22) ? 2 : 3);
-  int64_t Ls[kMaxPasses] = {1, 1, 1};
-  for (int i = 0; i < nprimes; ++i) {
-    int best = 0;
-    for (int k = 1; k < np; ++k)
-      if (Ls[k] < Ls[best]) best = k;
-    Ls[best] *= primes[i];
-  }
-  for (int i = 0; i < np; ++i)
-    if (Ls[i] > kMaxSubLen) return TM_ERANGE;
-  f.npass = np;
-  if (np == 1) {
-    FftPass& p = f.pass[0];
-    p.L = int(M); p.Q = 1; p.Qc = 1; p.IS = 1; p.OS = 1; p.Mp = 0;
-  } else if (np == 2) {
-    const int64_t L1 = Ls[0], L2 = Ls[1];
-    FftPass& a = f.pass[0];
-    a.L = int(L1); a.Q = L2; a.Qc = L2; a.IA = 0; a.IC = 1; a.IS = L2;
-    a.OA = 0; a.OC = 1; a.OS = L2; a.Mp = M;
-    FftPass& c = f.pass[1];
-    c.L = int(L2); c.Q = L1; c.Qc = L1; c.IA = 0; c.IC = L2; c.IS = 1;
-    c.OA = 0; c.OC = 1; c.OS = L1; c.Mp = 0;
-  } else {
-    const int64_t L1 = Ls[0], L2 = Ls[1], L3 = Ls[2], Mq = L2 * L3;
-    FftPass& a = f.pass[0];
-    a.L = int(L1); a.Q = Mq; a.Qc = Mq; a.IA = 0; a.IC = 1; a.IS = Mq;
-    a.OA = 0; a.OC = 1; a.OS = Mq; a.Mp = M;
-    FftPass& b = f.pass[1];
-    b.L = int(L2); b.Q = L3 * L1; b.Qc = L3; b.IA = Mq; b.IC = 1; b.IS = L3;
-    b.OA = Mq; b.OC = 1; b.OS = L3; b.Mp = Mq;
-    FftPass& c = f.pass[2];
-    c.L = int(L3); c.Q = L1 * L2; c.Qc = L1; c.IA = L3; c.IC = Mq; c.IS = 1;
-    c.OA = L1; c.OC = 1; c.OS = L1 * L2; c.Mp = 0;
-  }
-  for (int i = 0; i < np; ++i) {
-    radices_of(f.pass[i].L, &f.pass[i]);
-    shape(&f.pass[i], 2 * 152, 1024);
   }
   *out = f;
   return TM_OK;

@@ -55,7 +55,8 @@ struct PlanParams {
   double limit = 0.0;    // largest distance the device accepts (0: e_max)
 };
 
-// Chooses (b, N, lambda) for kind and n; returns 0 or a TM_E* code.
+// Chooses (b, N, lambda) for kind and n; returns 0 or a TM_E* code. Allocates no
+// heap memory.
 int choose_params(int kind, uint64_t n, PlanParams* out);
 
 // The plan for a caller's digit size b and transform length N (the cyclic length
@@ -85,14 +86,9 @@ struct FftShape {
 // Splits the complex length M into at most kMaxPasses sub-FFT passes and picks
 // their radices and launch shapes. Twiddle offsets are left for the caller.
 // single = true: one sub-FFT of length M (M <= kMaxSubLen), for CTA-resident products.
-// Returns TM_ERANGE / TM_EINVAL when `shape` cannot lay out M.
+// Returns TM_ERANGE / TM_EINVAL when `shape` cannot lay out M. Allocates no heap
+// memory.
 int make_fft_plan(int64_t M, FftPlan* out, bool single = false, const FftShape* shape = nullptr);
-
-// The same two plans computed without any heap allocation (for the entry point
-// whose callers cannot allocate): identical choice of (b, N, lambda); the FFT
-// layout may differ only in how the prime factors are grouped.
-int choose_params_noalloc(int kind, uint64_t n, PlanParams* out);
-int make_fft_plan_noalloc(int64_t M, FftPlan* out);
 
 // Data-dependent digit size. Measured norms of the balanced digits of u and v for
 // one (b, N): nu, nv = ||U||_2, ||V||_2 (high product: of F_0 .. F_(N-1)), tu, tv

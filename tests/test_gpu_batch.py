@@ -1,12 +1,14 @@
-"""Batched products (tm_batch_*, tm_mul_batch): every product of a batch equals
-the same product computed alone with tm_mul, bit for bit, for mixed kinds and
-uneven sizes; a recorded batch relaunched on new operand values recomputes
-them (marked gpu)."""
+"""Batched products (tm_batch_*, tm_mul_batch): every product of a batch is the
+oracle's (low and full products bit for bit, high products the exact round(t) of
+Algorithm 3) and equals the same product computed alone with tm_mul, for mixed
+kinds and uneven sizes, at the edge between the CTA-resident kernel and the
+per-phase launches, and on adversarial operands; a recorded batch relaunched on
+new operand values recomputes them (marked gpu)."""
 import numpy as np
 import pytest
 
 import workloads
-from gpu_util import dev
+from gpu_util import check_product, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +35,13 @@ def _make(pkg, sizes, kinds, seed):
 
 
 def _check(pkg, items):
+    """Each product against the oracle (low and full bit for bit, high the exact
+    round(t) of Algorithm 3 for n <= 2^18, else admissible) and against the same
+    product computed alone with tm_mul."""
     import torch
     for kind, n, out, u, v in items:
+        pl = pkg.plan(kind, n)
+        check_product(kind, host(out), host(u), host(v), n, pl["b"], pl["N"])
         ref, _ = pkg.mul(kind, u, v, n)
         assert torch.equal(out, ref), (kind, n)
 
@@ -80,4 +87,41 @@ def test_batch_config_shape_small(pkg):
     b = pkg.Batch(items)
     b.launch()
     assert b.status()["rc"] == 0
+    _check(pkg, items)
+
+
+def _edge_sizes(pkg, kind, M_max=2048):
+    """The largest n whose plan has complex length M <= M_max (the last size the
+    CTA-resident kernel takes) and the next n (the first size above it)."""
+    lo, hi = 1, 1 << 20
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if pkg.plan(kind, mid)["N"] // 2 <= M_max:
+            lo = mid
+        else:
+            hi = mid
+    return [lo, hi]
+
+
+def test_batch_edge_of_cta_resident_kernel(pkg):
+    """Products at M = kSmallMaxM and just above, n = 1, ragged n and adversarial
+    operands, all in one batch, against the oracle."""
+    import torch
+    items = []
+    seed = 700
+    for kind in ("lo", "hi", "full"):
+        sizes = _edge_sizes(pkg, kind) + [1, 2, 63, 65, 4097]
+        for n in sizes:
+            b = pkg.plan(kind, n)["b"]
+            for pattern in ("random", "ones", "balanced_worst", "top"):
+                u, v = workloads.pattern_limbs(pattern, n, seed=seed, b=b)
+                seed += 1
+                out = torch.full((pkg.out_limbs(kind, n),), -1, dtype=torch.int64,
+                                 device="cuda")
+                items.append((kind, n, out, dev(u), dev(v)))
+    for kind in ("lo", "hi", "full"):
+        e = _edge_sizes(pkg, kind)
+        assert pkg.plan(kind, e[0])["N"] // 2 <= 2048 < pkg.plan(kind, e[1])["N"] // 2
+    rep = pkg.mul_batch(items)
+    assert rep["status"] == 0 and rep["margin"] <= rep["e_max"]
     _check(pkg, items)

@@ -6,8 +6,11 @@ correct bound never trips it, so the test injects the failure on the host: a chi
 process runs with TRUNCMUL_FAULT_EMAX_SCALE set, which scales every bound the device
 sees down by 10^-12. Every entry point must then report TM_EPRECISION (synchronous
 calls, the asynchronous status query, host buffers, kept operands, batches, the
-request loop, division) while the products themselves stay the exact ones a normal
-process computes; in a normal process the same calls succeed."""
+request loop, division, the allocation-free entry point) while the products
+themselves stay the exact ones a normal process computes; in a normal process the
+same calls succeed. The allocation-free entry point reads its status word through
+its own branch (copy, clear, wait); a later call on a zero operand must report
+TM_OK, which shows that branch left the word cleared."""
 import json
 import os
 import subprocess
@@ -23,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 N_BITS = 100003
+N_STATIC = 60001          # tm_mul_static's sizes stop at 65536 bits
 
 CHILD = r'''
 import json, sys
@@ -77,6 +81,20 @@ bar = pkg.Barrett(torch.from_numpy(m.view(np.int64)).cuda(), k)
 x = torch.from_numpy(np.concatenate([u[: k // 64], v[: k // 64]]).view(np.int64)).cuda()
 res["codes"]["divrem"] = code(lambda: bar.divrem(x))
 bar.close()
+ns = int(sys.argv[3])
+us, vs = workloads.pattern_limbs("random", ns, seed=4)
+dus = torch.from_numpy(us.view(np.int64)).cuda()
+dvs = torch.from_numpy(vs.view(np.int64)).cuda()
+for kind in ("lo", "hi", "full"):
+    o = torch.full((pkg.out_limbs(kind, ns),), -1, dtype=torch.int64, device="cuda")
+    rc, _ = pkg.mul_static(kind, dus, dvs, ns, o)
+    res["codes"]["static_" + kind] = rc
+    res["out"]["static_" + kind] = o.cpu().numpy().view(np.uint64).tolist()
+# a zero operand rounds every coefficient exactly (distance 0), so this call
+# reports TM_OK only if the flagged calls before it left the status word cleared
+o = torch.empty(pkg.out_limbs("lo", ns), dtype=torch.int64, device="cuda")
+rc, _ = pkg.mul_static("lo", torch.zeros_like(dus), dvs, ns, o)
+res["codes"]["static_clear_after"] = rc
 print(json.dumps(res))
 '''
 
@@ -86,7 +104,7 @@ def _child(scale):
     env.pop("TRUNCMUL_FAULT_EMAX_SCALE", None)
     if scale is not None:
         env["TRUNCMUL_FAULT_EMAX_SCALE"] = scale
-    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(N_BITS)], env=env,
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(N_BITS), str(N_STATIC)], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -108,15 +126,24 @@ def test_injected_margin_failure_is_reported_everywhere(pkg):
     E = pkg.TM_EPRECISION
     codes = res["codes"]
     for key in ("sync_lo", "sync_hi", "sync_full", "async_status", "host", "operand",
-                "batch", "divrem"):
+                "batch", "divrem", "static_lo", "static_hi", "static_full"):
         assert codes[key] == E, (key, codes)
     assert codes["server"] == [E, E]
+    assert codes["static_clear_after"] == 0, codes
     # the arithmetic is untouched: the limbs equal this (uninjected) process's
     u, v = workloads.pattern_limbs("random", N_BITS, seed=3)
     for kind in ("lo", "hi", "full"):
         ref, rep = pkg.mul(kind, dev(u), dev(v), N_BITS)
         assert rep["status"] == 0
         assert np.array_equal(np.array(res["out"][kind], dtype=np.uint64), host(ref)), kind
+    import torch
+    us, vs = workloads.pattern_limbs("random", N_STATIC, seed=4)
+    for kind in ("lo", "hi", "full"):
+        o = torch.empty(pkg.out_limbs(kind, N_STATIC), dtype=torch.int64, device="cuda")
+        rc, _ = pkg.mul_static(kind, dev(us), dev(vs), N_STATIC, o)
+        assert rc == 0
+        got = np.array(res["out"]["static_" + kind], dtype=np.uint64)
+        assert np.array_equal(got, host(o)), "static " + kind
 
 
 @pytest.mark.parametrize("scale", [None, "2", "0", "junk"])

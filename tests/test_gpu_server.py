@@ -1,12 +1,13 @@
 """Serving layer (tm_server_*): results of requests served in a mixed stream
-with continuous batching equal the same products computed alone with tm_mul,
-bit for bit, whatever the admission order, budget or arrival pattern
-(marked gpu)."""
+with continuous batching are the oracle's (low and full products bit for bit,
+high products the exact round(t) of Algorithm 3) and equal the same products
+computed alone with tm_mul, whatever the admission order, budget or arrival
+pattern (marked gpu)."""
 import numpy as np
 import pytest
 
 import workloads
-from gpu_util import dev
+from gpu_util import check_product, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -57,9 +58,14 @@ def _serve_all(srv, reqs, stagger=0):
 
 
 def _check(pkg, reqs, done):
+    """Each served result against the oracle (low and full bit for bit, high the
+    exact round(t) of Algorithm 3 for n <= 2^18, else admissible) and against the
+    same product computed alone with tm_mul."""
     import torch
     assert all(st == 0 for st in done.values())
     for kind, n, out, u, v in reqs:
+        pl = pkg.plan(kind, n)
+        check_product(kind, host(out), host(u), host(v), n, pl["b"], pl["N"])
         ref, _ = pkg.mul(kind, u, v, n)
         assert torch.equal(out, ref), (kind, n)
 

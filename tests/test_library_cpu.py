@@ -167,7 +167,7 @@ def test_host_side_errors(pkg):
     assert lib.tm_barrett_divrem(None, fake, fake, fake, None, None) == pkg.TM_EINVAL
     assert lib.tm_barrett_reciprocal(None, fake, None) == pkg.TM_EINVAL
     assert lib.tm_barrett_destroy(None) == pkg.TM_OK
-    for code in (0, -1, -2, -3, -4, -5, -6, -7, 99):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, 99):
         assert pkg.strerror(code)
 
 
