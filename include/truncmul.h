@@ -494,6 +494,35 @@ int tm_stream_status(void* stream, tm_report* rep);
  * No call may be in flight on that device. */
 int tm_release(void);
 
+/*
+ * tm_table_values: writes the twiddle tables the FFT kernels use into the
+ * caller's device buffer `out` (enqueued on `stream`), so that their accuracy can
+ * be checked; a checking facility with no counterpart in the paper.
+ *   which 0: out[2m], out[2m+1] = cos, -sin of 2 pi m / len, m < count;
+ *   which 1: the tangent-form records of a radix-4 stage with Ns = len
+ *            (count must equal len): out[4k..4k+3] = t1, c1, t2, c2s with
+ *            exp(-2 pi i k / (4 len)) = c1 (1 - i t1) and exp(-4 pi i k / (4 len))
+ *            = c2 (1 - i t2), or -i c2 (1 - i t2) with c2s = -c2 when its angle
+ *            is pi/2 or more;
+ *   which 2: the twist coefficients of real length N = len: out[2k], out[2k+1]
+ *            = cos(2 pi k / N) (cos, -sin)(2 pi k / N) / N, k < count.
+ * Each value is the double nearest to the exact one, up to 2^-40 of an ulp
+ * (the tangent t is nearest to sin / c with the stored c). Returns TM_OK,
+ * TM_EINVAL or TM_ECUDA.
+ */
+int tm_table_values(int which, int64_t len, int64_t count, double* out, void* stream);
+
+/*
+ * tm_probe_dfma: a measurement helper with no counterpart in the paper. Enqueues
+ * on `stream` one kernel that keeps every SM's FP64 pipe busy with independent
+ * fused multiply-adds (8 CTAs of 256 threads per SM, 8 chains of `iters` FMAs per
+ * thread) and stores the flops it performs (2 per FMA) in *flops; the caller
+ * times it with events on the stream. The FP64 pipe bounds the FFT passes, so
+ * flops / time is the peak their roofline fraction is taken against. Returns
+ * TM_OK, TM_EINVAL (iters <= 0, NULL flops) or TM_ECUDA.
+ */
+int tm_probe_dfma(int iters, void* stream, double* flops);
+
 /* Text for a status code (static storage). */
 const char* tm_strerror(int code);
 

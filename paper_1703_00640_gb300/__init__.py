@@ -83,7 +83,7 @@ EXPORTS = ["tm_mul", "tm_mul_params", "tm_mul_adaptive", "tm_mul_full", "tm_mul_
            "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
-           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror"]
+           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror", "tm_probe_dfma", "tm_table_values"]
 
 _lib = None
 
@@ -118,6 +118,10 @@ def load(path: str = None):
     lib.tm_mul_events.argtypes = [ctypes.c_int, P, P, P, ctypes.c_uint64, P,
                                   ctypes.POINTER(ctypes.c_void_p), R]
     lib.tm_plan_query.argtypes = [ctypes.c_int, ctypes.c_uint64, R]
+    lib.tm_probe_dfma.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
+    lib.tm_probe_dfma.restype = ctypes.c_int
+    lib.tm_table_values.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P]
+    lib.tm_table_values.restype = ctypes.c_int
     D = ctypes.POINTER(Desc)
     lib.tm_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), D, ctypes.c_uint32, P]
     lib.tm_batch_launch.argtypes = [P, P]
@@ -273,6 +277,29 @@ def mul_events(kind, u, v, n_bits: int, events, out=None, stream=None):
     if rc:
         raise TruncMulError(rc, "tm_mul_events")
     return out
+
+
+def table_values(which: int, length: int, count: int):
+    """tm_table_values: the FFT kernels' twiddle table `which` (0 twiddles, 1
+    tangent-form radix-4 records, 2 twist coefficients) as a float64 numpy array."""
+    import numpy as np
+    import torch
+    per = 4 if which == 1 else 2
+    out = torch.empty(per * count, dtype=torch.float64, device="cuda")
+    rc = load().tm_table_values(int(which), int(length), int(count), _ptr(out), _stream_ptr(None))
+    if rc:
+        raise TruncMulError(rc, "tm_table_values")
+    return out.cpu().numpy().astype(np.float64)
+
+
+def probe_dfma(iters: int, stream=None) -> float:
+    """tm_probe_dfma: enqueues the FP64 FMA issue-rate probe on `stream` and
+    returns the flops it performs (time it with events on the same stream)."""
+    fl = ctypes.c_double()
+    rc = load().tm_probe_dfma(int(iters), _stream_ptr(stream), ctypes.byref(fl))
+    if rc:
+        raise TruncMulError(rc, "tm_probe_dfma")
+    return fl.value
 
 
 def mul_static(kind, u, v, n_bits: int, out, stream=None, report: bool = True):

@@ -1476,6 +1476,27 @@ int tm_release(void) {
   return TM_OK;
 }
 
+int tm_table_values(int which, int64_t len, int64_t count, double* out, void* stream) {
+  if (!out || len < 1 || count < 0 || len > (int64_t(1) << 40)) return TM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (which) {
+    case 0: tmul::launch_init_twiddles(reinterpret_cast<double2*>(out), len, count, s); break;
+    case 1:
+      if (count != len || len > (int64_t(1) << 30)) return TM_EINVAL;
+      tmul::launch_init_tw4(reinterpret_cast<tmul::Tan4*>(out), int(len), s);
+      break;
+    case 2: tmul::launch_init_twist_coef(reinterpret_cast<double2*>(out), len, count, s); break;
+    default: return TM_EINVAL;
+  }
+  return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
+int tm_probe_dfma(int iters, void* stream, double* flops) {
+  if (iters <= 0 || !flops) return TM_EINVAL;
+  *flops = tmul::launch_probe_dfma(iters, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
 const char* tm_strerror(int code) {
   switch (code) {
     case TM_OK: return "ok";

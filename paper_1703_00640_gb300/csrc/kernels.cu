@@ -15,18 +15,20 @@ namespace tmul {
 
 // ------------------------------------------------------------ constants
 
-constexpr double kC5_1 = 0.30901699437494745;   // cos(2 pi/5)
-constexpr double kC5_2 = -0.8090169943749473;   // cos(4 pi/5)
-constexpr double kS5_1 = 0.9510565162951535;    // sin(2 pi/5)
-constexpr double kS5_2 = 0.5877852522924732;    // sin(4 pi/5)
-constexpr double kC7_1 = 0.6234898018587336;    // cos(2 pi k/7), k = 1, 2, 3
-constexpr double kC7_2 = -0.22252093395631434;
-constexpr double kC7_3 = -0.900968867902419;
-constexpr double kS7_1 = 0.7818314824680298;    // sin(2 pi k/7)
-constexpr double kS7_2 = 0.9749279121818236;
-constexpr double kS7_3 = 0.43388373911755823;
-constexpr double kSqrt3_2 = 0.8660254037844386;
-constexpr double kSqrt1_2 = 0.7071067811865476;
+// The radix-3/5/7 and radix-8 DFT constants, each the double nearest to its exact
+// value (hex literals; the error bound takes every constant within 2^-53 of it).
+constexpr double kC5_1 = 0x1.3c6ef372fe950p-2;    // cos(2 pi/5)   0.30901699437494745
+constexpr double kC5_2 = -0x1.9e3779b97f4a8p-1;   // cos(4 pi/5)  -0.8090169943749475
+constexpr double kS5_1 = 0x1.e6f0e134454ffp-1;    // sin(2 pi/5)   0.9510565162951535
+constexpr double kS5_2 = 0x1.2cf2304755a5ep-1;    // sin(4 pi/5)   0.5877852522924731
+constexpr double kC7_1 = 0x1.3f3a0e28bedd1p-1;    // cos(2 pi k/7), k = 1, 2, 3
+constexpr double kC7_2 = -0x1.c7b90e3024582p-3;
+constexpr double kC7_3 = -0x1.cd4bca9cb5c71p-1;
+constexpr double kS7_1 = 0x1.904c37505de4bp-1;    // sin(2 pi k/7)
+constexpr double kS7_2 = 0x1.f329c0558e969p-1;
+constexpr double kS7_3 = 0x1.bc4c04d71abc1p-2;
+constexpr double kSqrt3_2 = 0x1.bb67ae8584caap-1; // sqrt(3)/2
+constexpr double kSqrt1_2 = 0x1.6a09e667f3bcdp-1; // sqrt(1/2)
 
 // ------------------------------------------------------- complex helpers
 
@@ -94,60 +96,140 @@ __device__ __forceinline__ long long round_dist(double x, unsigned long long* di
 
 // -------------------------------------------------------- table kernels
 
-// cos and sin of 2 pi m / len. The angle is reduced to the first half-quadrant
-// with integer arithmetic, then sincospi of an argument in [0, 1/4].
-__device__ void cossin_2pi(long long m, long long len, double* cs, double* sn) {
+// Every twiddle table entry is computed in double-double arithmetic and rounded
+// once, so each stored component is within 2^-53 (1 + 2^-40) of its exact value;
+// the FFT error bound relies on that. Error-free transformations: Knuth's
+// two-sum and the FMA form of Dekker's exact product; double-double sums,
+// products and quotients after Dekker (1971), each with relative error below
+// 2^-100 for the operands used here.
+struct DD {
+  double hi, lo;
+};
+
+// (The operations use the _rn intrinsics, which the compiler never contracts
+// into FMAs: the transformations need every sum and product rounded as written.)
+__device__ __forceinline__ DD dd_two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  return DD{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DD dd_fast_two_sum(double a, double b) {   // |a| >= |b| or a = 0
+  const double s = __dadd_rn(a, b);
+  return DD{s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+  DD s = dd_two_sum(x.hi, y.hi);
+  const DD t = dd_two_sum(x.lo, y.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = dd_fast_two_sum(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DD dd_mul(DD x, DD y) {
+  const double p = __dmul_rn(x.hi, y.hi);
+  const double e = __fma_rn(x.hi, y.hi, -p);
+  const double c = __dadd_rn(__dmul_rn(x.hi, y.lo), __dmul_rn(x.lo, y.hi));
+  return dd_fast_two_sum(p, __dadd_rn(e, c));
+}
+
+// x / y for a double y != 0: the quotient of the leading parts, then one
+// correction from the remainder (x.hi - q1 y is formed exactly)
+__device__ __forceinline__ DD dd_div_d(DD x, double y) {
+  const double q1 = __ddiv_rn(x.hi, y);
+  const double p = __dmul_rn(q1, y);
+  const double pe = __fma_rn(q1, y, -p);     // q1 y = p + pe exactly
+  DD r = dd_two_sum(x.hi, -p);
+  r.lo = __dadd_rn(r.lo, __dsub_rn(x.lo, pe));
+  const double q2 = __ddiv_rn(__dadd_rn(r.hi, r.lo), y);
+  return dd_fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ DD dd_neg(DD x) { return DD{-x.hi, -x.lo}; }
+
+// pi / 2 to 2^-109 relative
+__device__ __constant__ const double kPi2Hi = 0x1.921fb54442d18p+0;
+__device__ __constant__ const double kPi2Lo = 0x1.1a62633145c07p-54;
+
+// sin x and cos x for 0 <= x <= pi/4 from their Taylor series, summed in
+// double-double up to the terms of degree 31 / 30 (below 2^-110 of the sums).
+__device__ void dd_sincos_small(DD x, DD* sn, DD* cs) {
+  const DD x2 = dd_mul(x, x);
+  DD ts = x, tc = DD{1.0, 0.0};
+  DD ss = x, cc = DD{1.0, 0.0};
+  for (int j = 1; j <= 15; ++j) {
+    ts = dd_div_d(dd_mul(ts, x2), -double((2 * j) * (2 * j + 1)));
+    tc = dd_div_d(dd_mul(tc, x2), -double((2 * j - 1) * (2 * j)));
+    ss = dd_add(ss, ts);
+    cc = dd_add(cc, tc);
+  }
+  *sn = ss;
+  *cs = cc;
+}
+
+// cos and sin of 2 pi m / len in double-double. The angle is reduced with
+// integers to a quadrant and a complement, leaving pi/2 (r / len) with
+// r / len in [0, 1/2].
+__device__ void dd_cossin_2pi(long long m, long long len, DD* cs, DD* sn) {
   const long long m4 = 4 * m;
   const long long q = m4 / len;              // quadrant 0..3
   long long r = m4 - q * len;                // angle = pi/2 (q + r/len)
   bool swap = false;
   if (2 * r > len) { r = len - r; swap = true; }   // use the complement angle
-  double s, c;
-  sincospi((double)r / (2.0 * (double)len), &s, &c);   // angle pi r / (2 len)
-  if (swap) { const double t = s; s = c; c = t; }
+  const DD frac = dd_div_d(DD{double(r), 0.0}, double(len));
+  DD s, c;
+  dd_sincos_small(dd_mul(DD{kPi2Hi, kPi2Lo}, frac), &s, &c);
+  if (swap) { const DD t = s; s = c; c = t; }
   switch (q) {
     case 0: *cs = c; *sn = s; break;
-    case 1: *cs = -s; *sn = c; break;
-    case 2: *cs = -c; *sn = -s; break;
-    default: *cs = s; *sn = -c; break;
+    case 1: *cs = dd_neg(s); *sn = c; break;
+    case 2: *cs = dd_neg(c); *sn = dd_neg(s); break;
+    default: *cs = s; *sn = dd_neg(c); break;
   }
 }
 
-// tab[m] = exp(-2 pi i m / len), m < count.
+// tab[m] = exp(-2 pi i m / len), m < count, each component rounded once.
 __global__ void k_init_twiddles(double2* tab, long long len, long long count) {
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= count) return;
-  double cs, sn;
-  cossin_2pi(m, len, &cs, &sn);
-  tab[m] = make_double2(cs, -sn);
+  DD cs, sn;
+  dd_cossin_2pi(m, len, &cs, &sn);
+  tab[m] = make_double2(cs.hi, -sn.hi);
 }
 
 // tab[k] = (1 + w^2) / (2N) = cos(2 pi k / N) w / N, w = exp(-2 pi i k / N), k < count:
-// the one twiddle of the fused real-FFT twist (see twist_pair).
+// the one twiddle of the fused real-FFT twist (see twist_pair), each component
+// rounded once.
 __global__ void k_init_twist_coef(double2* tab, long long N, long long count) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= count) return;
-  double cs, sn;
-  cossin_2pi(k, N, &cs, &sn);
-  tab[k] = make_double2(cs * cs / (double)N, -(cs * sn) / (double)N);
+  DD cs, sn;
+  dd_cossin_2pi(k, N, &cs, &sn);
+  const DD re = dd_div_d(dd_mul(cs, cs), double(N));
+  const DD im = dd_div_d(dd_mul(cs, sn), double(N));
+  tab[k] = make_double2(re.hi, -im.hi);
 }
 
-// Tangent-form twiddles of a radix-4 stage (see launch_init_tw4).
+// Tangent-form twiddles of a radix-4 stage (see launch_init_tw4). The cosine c is
+// rounded first and the tangent is taken as the double nearest to sin / c (with
+// the rounded c), so the twiddle c (1 - i t) the butterfly applies is within
+// 2^-53 (1 + 2^-40) of exp(-i theta), as for a rounded (cos, sin) pair.
 __global__ void k_init_tw4(Tan4* tab, int Ns) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Ns) return;
-  double s1, c1, s2, c2;
-  sincospi((double)k / (2.0 * Ns), &s1, &c1);          // theta = 2 pi k / (4 Ns) < pi/2
-  double c2s;
-  if (2 * k < Ns) {
-    sincospi((double)k / (double)Ns, &s2, &c2);        // 2 theta < pi/2
-    c2s = c2;
-  } else {
-    sincospi((double)(2 * k - Ns) / (2.0 * Ns), &s2, &c2);   // 2 theta - pi/2
-    c2s = -c2;
-  }
+  const long long len = 4LL * Ns;
+  DD c1, s1, c2, s2;
+  dd_cossin_2pi(k, len, &c1, &s1);                   // theta = 2 pi k / (4 Ns) < pi/2
+  const bool rot = 2 * k >= Ns;
+  dd_cossin_2pi(rot ? 2LL * k - Ns : 2LL * k, len, &c2, &s2);   // 2 theta, or 2 theta - pi/2
   Tan4 e;
-  e.t1 = s1 / c1; e.c1 = c1; e.t2 = s2 / c2; e.c2s = c2s;
+  e.c1 = c1.hi;
+  e.t1 = dd_div_d(s1, e.c1).hi;
+  const double cr2 = c2.hi;
+  e.t2 = dd_div_d(s2, cr2).hi;
+  e.c2s = rot ? -cr2 : cr2;
   tab[k] = e;
 }
 
@@ -1833,6 +1915,33 @@ void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int ro
                            cudaStream_t s) {
   if (rows <= 0) return;
   k_init_maptab_fx<<<unsigned((N + 255) / 256), 256, 0, s>>>(tab, which, N, b, rows, Q);
+}
+
+// FP64 FMA issue-rate probe: every thread runs 8 independent chains of `iters`
+// dependent FMAs (2 flops each), then thread 0 of each block stores the block's
+// first thread's sum, so the chains cannot be dropped.
+__device__ double g_probe_sink[4096];
+__global__ void __launch_bounds__(256) k_probe_dfma(int iters, double a, double c) {
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 1e-3 * threadIdx.x + j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (threadIdx.x == 0) g_probe_sink[blockIdx.x & 4095] = s;
+}
+
+double launch_probe_dfma(int iters, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8;              // 8 CTAs of 256 threads: every warp slot
+  k_probe_dfma<<<blocks, 256, 0, s>>>(iters, 0.9999999, 1e-7);
+  return 2.0 * 8.0 * double(iters) * 256.0 * double(blocks);
 }
 
 void launch_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr,

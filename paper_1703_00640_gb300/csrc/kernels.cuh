@@ -218,6 +218,9 @@ void launch_init_maptab(double* tab, int which, long long N, int b, int rows, cu
 void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,
                            cudaStream_t s);
 
+// FP64 FMA issue-rate probe on every SM; returns the flops it enqueued.
+double launch_probe_dfma(int iters, cudaStream_t s);
+
 // High product: tab[i] = 2^b / rho^(i+1), i < nkappa, then tab[nkappa + j] = rho^-j,
 // j < ntheta (lr = ln rho).
 void launch_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr,

@@ -245,3 +245,21 @@ def test_plan_matches_oracle_plan_random_sizes(pkg):
             (ref["b"], ref["N"], ref["n_digits"]), (kind, n)
         assert (mine["lam_fwd"], mine["lam_bwd"]) == (ref["lam_fwd"], ref["lam_bwd"]), (kind, n)
         assert mine["e_max"] == pytest.approx(ref["e_max"], rel=1e-9), (kind, n)
+
+
+def test_dft_constants_are_the_nearest_doubles():
+    """The radix-3/5/7/8 DFT constants written in the kernels are the doubles
+    nearest to cos / sin of 2 pi k / R (the FFT error bound takes each within
+    2^-53 of its exact value)."""
+    import hp_trig
+    src = open(os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")).read()
+    vals = dict(re.findall(r"constexpr double (k[CS]\d_\d|kSqrt3_2|kSqrt1_2) = "
+                           r"(-?0x[0-9a-fp.+-]+);", src))
+    want = {"kSqrt3_2": hp_trig.cossin_2pi(1, 3)[1], "kSqrt1_2": hp_trig.cossin_2pi(1, 8)[0]}
+    for R, count in ((5, 2), (7, 3)):
+        for k in range(1, count + 1):
+            c, s = hp_trig.cossin_2pi(k, R)
+            want[f"kC{R}_{k}"], want[f"kS{R}_{k}"] = c, s
+    assert set(vals) == set(want), set(want) ^ set(vals)
+    for name, text in vals.items():
+        assert float.fromhex(text) == float(want[name]), name
