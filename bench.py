@@ -9,11 +9,16 @@ t_trunc / t_full ratios. Each product is timed with CUDA events on its stream,
 with the L2 flushed (256 MB written) between products. Before timing, the plans
 (b, N) and the FFT layouts are tuned (tm_autotune_plan, tm_autotune).
 
-Further sections of the JSON line: end to end from page-locked host memory
-(e2e), squares / kept operands / data-dependent digit size, Barrett division,
-single products at n = 2^16 and 2^20 (sizes), the paper's Table 2 parameters
-(paper_parameters), n = 2^28 (large), the 4096-product batch (batched), and the
-CPU oracle on the host cores (cpu_baseline). --served runs the served stream.
+Further keys of the JSON line: the FP64 roofline of the FFT passes against the
+FP64 FMA rate measured in the same run (tm_probe_dfma); end to end from
+page-locked host memory (e2e); squares / kept operands / data-dependent digit
+size; Barrett division; the CPU oracle on the host cores (cpu_baseline); in
+"detail": single products at n = 2^16 and 2^20 (sizes), n = 2^28 (large), the
+4096-product batch against per-product launches (batched), and a served stream of
+4000 requests against per-product launches (served); and last, "summary": every
+configuration's headline figures in a few hundred bytes. --served runs the
+20000-request served stream alone; --paper-params adds the paper's Table 2
+parameters (uncertified).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 Multi-GPU (torchrun, one rank per GPU): replicas, each rank multiplies its own
@@ -33,11 +38,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50/p99 ms"
 UNIT = "Gbit/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
-FP64_DFMA_MEASURED = 1.008   # DFMA/DADD/DMUL issue ceiling measured on this GB300 pool
-# DRAM bytes per k_fft_pass launch from profiles/k_fft_pass_n2p24.md (n = 2^24 only)
-FFT_TRAFFIC_N2P24 = 23.5e6
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(n, world=1):
+    """The config of the headline workload, shared by both arms of the bench."""
+    return {"workload": f"single low + high product (full product for the ratio), n = {n} "
+                        "bits, uniform random uint64 limbs (seeded PCG64)",
+            "n_bits": n, "l2": "flushed (256 MB write) before every product",
+            "parallelism": f"replicas x{world}"}
+
+
+def sig(x, d=4):
+    """x rounded to d significant digits (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, float):
+        return float(f"{x:.{d}g}")
+    return x
 
 
 def parse():
@@ -51,7 +70,12 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--served", action="store_true",
                     help="run the served-stream configuration instead of the default")
-    ap.add_argument("--served-count", type=int, default=20000)
+    ap.add_argument("--served-count", type=int, default=20000,
+                    help="requests of the served stream under --served")
+    ap.add_argument("--served-quick-count", type=int, default=4000,
+                    help="requests of the served stream inside the default run")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served stream inside the default run")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run the batched configuration alone (graph launches)")
@@ -73,8 +97,9 @@ def parse():
                     help="run the large single-product section alone")
     ap.add_argument("--large-kinds", default="lo,hi,full",
                     help="products of the large section (comma list of lo, hi, full)")
-    ap.add_argument("--no-paper-params", action="store_true",
-                    help="skip the products with the paper's Table 2 parameters")
+    ap.add_argument("--paper-params", action="store_true",
+                    help="also time the products with the paper's Table 2 parameters "
+                         "(uncertified; not part of the default run)")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the single products at n = 2^16 and 2^20")
     return ap.parse_args()
@@ -200,18 +225,18 @@ def run_reference(args):
     t = oracle_products(n, range(2000, 2000 + args.steps), depth)
     total = sum(t)
     value = 2 * n * args.steps / total / 1e9
-    cores = min(threads_for(depth), ncpu)
+    threads = min(threads_for(depth), ncpu)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"single low + high product, n = {n} bits, uniform random "
-                               "uint64 limbs (seeded PCG64)", "n_bits": n},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "config": workload_config(n, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncpu, "threads": threads,
+                         "kind": "oracle",
                          "sample": f"{args.steps} steps of one low + one high product at n={n} "
-                                   "(C Karatsuba full product + truncation), "
-                                   f"{threads_for(depth)} threads"},
+                                   "(C Karatsuba full product + truncation by definition), "
+                                   f"{threads} threads on {ncpu} host cores"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -327,22 +352,15 @@ def serve(pkg, reqs, arrivals, budget, slots):
     return total, [lat[i] for i in range(len(reqs))]
 
 
-def run_served(args):
-    import numpy as np
-    import torch
-    import paper_1703_00640_gb300 as pkg
-    rank, local_rank, world = dist_env()
-    torch.cuda.set_device(local_rank)
-    pkg.build()
-    pkg.load()
-    count = args.served_count
-    reqs = served_requests(pkg, torch, np, count, seed=5 + rank)
-    budget = 2 << 30                        # device bytes for workspaces in flight
-    slots = 8
+def served_section(pkg, torch, np, count, seed, budget=2 << 30, slots=8):
+    """The served stream: `count` requests (served_requests) through the request
+    loop, first all at once (saturated capacity), then with Poisson arrivals at 0.5x
+    and 0.8x that capacity (latency p50 / p99 from arrival to completion); next to
+    it the same requests as plain per-product launches (tm_mul, one stream, all at
+    once), and a sample of results against the same products alone."""
+    reqs = served_requests(pkg, torch, np, count, seed=seed)
     bits = float(sum(r[1] for r in reqs))
-    # warm: plans and tables of every request
-    total_w, _ = serve(pkg, reqs, [0.0] * count, budget, slots)
-    # saturated: every request arrives at once
+    serve(pkg, reqs, [0.0] * count, budget, slots)           # plans and tables of every size
     total_s, lat_s = serve(pkg, reqs, [0.0] * count, budget, slots)
     rate_sat = count / total_s
     loads = {}
@@ -355,28 +373,95 @@ def run_served(args):
                              "gbit_s": bits / total / 1e9,
                              "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                                             "p99": 1e3 * float(np.percentile(lat, 99))}}
-    # results in the mix equal the same products alone (a sample)
-    same = True
-    for i in np.random.default_rng(1).choice(count, 64, replace=False):
-        kind, n, out, u, v = reqs[int(i)]
-        ref, _ = pkg.mul(kind, u, v, n)
-        same = same and bool(torch.equal(out, ref))
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "config": {"workload": f"served stream: {count} requests, Poisson "
-                "arrivals, n log-uniform in [2^10, 2^24] bits, 40% high products with the top n "
-                "bits of a fixed 2^24-bit Barrett reciprocal, 30% low, 30% high; device-memory "
-                f"budget {budget >> 20} MiB, {slots} slots"},
-            "unit": UNIT, "value": bits / total_s / 1e9, "higher_is_better": True,
+    # baseline: the same request mix as individual tm_mul launches on one stream
+    s = torch.cuda.Stream()
+    refs = [torch.empty_like(r[2]) for r in reqs]
+    for (kind, n, out, u, v), o in zip(reqs, refs):           # warm
+        pkg.mul(kind, u, v, n, out=o, stream=s, report=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (kind, n, out, u, v), o in zip(reqs, refs):
+        pkg.mul(kind, u, v, n, out=o, stream=s, report=False)
+    torch.cuda.synchronize()
+    t_pp = time.perf_counter() - t0
+    assert pkg.stream_status(s)["rc"] == 0
+    same = all(torch.equal(r[2], o) for r, o in zip(reqs, refs))
+    return {"requests": count, "budget_mib": budget >> 20, "slots": slots,
             "saturated": {"wall_s": total_s, "throughput_per_s": rate_sat,
                           "gbit_s": bits / total_s / 1e9,
                           "latency_ms": {"p50": 1e3 * float(np.percentile(lat_s, 50)),
                                          "p99": 1e3 * float(np.percentile(lat_s, 99))}},
-            "loads": loads, "bit_exact_sample_vs_alone": same, "n_gpus": world,
-            "dtype": "f64", "data": "synthetic"}), flush=True)
+            "loads": loads,
+            "per_product_launches": {"wall_s": t_pp, "throughput_per_s": count / t_pp,
+                                     "gbit_s": bits / t_pp / 1e9},
+            "bit_exact_vs_per_product": same}
+
+
+SERVED_WORKLOAD = ("served stream: {count} requests, Poisson arrivals, n log-uniform in "
+                   "[2^10, 2^24] bits, 40% high products with the top n bits of a fixed "
+                   "2^24-bit Barrett reciprocal, 30% low, 30% high; device-memory budget "
+                   "2048 MiB, 8 slots")
+
+
+def run_served(args):
+    import numpy as np
+    import torch
+    import paper_1703_00640_gb300 as pkg
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    pkg.build()
+    pkg.load()
+    res = served_section(pkg, torch, np, args.served_count, seed=5 + rank)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC,
+            "config": {"workload": SERVED_WORKLOAD.format(count=args.served_count)},
+            "unit": UNIT, "value": res["saturated"]["gbit_s"], "higher_is_better": True,
+            "served": res, "n_gpus": world, "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
 # ------------------------------------------------------------ CUDA arm
+
+def summary_of(n, t_lo, t_hi, t_full, steps, e2e_val, achieved, dfma_peak, sizes, large,
+               batched, served):
+    """Every configuration's headline figures in a few hundred bytes."""
+    out = {f"n={n}": {"lo_gbit_s": sig(n * steps / (t_lo * 1e-3) / 1e9),
+                      "hi_gbit_s": sig(n * steps / (t_hi * 1e-3) / 1e9),
+                      "t_lo/full": sig(t_lo / t_full), "t_hi/full": sig(t_hi / t_full),
+                      "e2e_gbit_s": sig(e2e_val)},
+           "fft_tflops": sig(achieved), "dfma_peak_tflops": sig(dfma_peak)}
+    for key, row in (sizes or {}).items():
+        out[f"n={key}"] = {"lo_us": sig(1e3 * row["lo"]["ms"]), "hi_us": sig(1e3 * row["hi"]["ms"]),
+                           "full_us": sig(1e3 * row["full"]["ms"]),
+                           "t_lo/full": sig(row["t_lo_over_full"]),
+                           "t_hi/full": sig(row["t_hi_over_full"])}
+    if large:
+        r = {"lo_ms": sig(large["lo"]["ms"]) if "lo" in large else None,
+             "hi_ms": sig(large["hi"]["ms"]) if "hi" in large else None,
+             "full_ms": sig(large["full"]["ms"]) if "full" in large else None}
+        for k in ("lo", "hi"):
+            if k in large and "t_over_full" in large[k]:
+                r[f"t_{k}/full"] = sig(large[k]["t_over_full"])
+        if "lo" in large:
+            r["fft_tflops_lo"] = sig(large["lo"]["fft_fp64_tflops"])
+        out[f"n={large['n_bits']}"] = r
+    if batched:
+        out["batch"] = {"products": batched["products"],
+                        "graph_ms": sig(batched["graph_launch_ms"]["p50"]),
+                        "per_product_launches_ms": sig(batched["per_product_launches_ms"]["p50"]),
+                        "products_per_s": sig(batched["products_per_s"]),
+                        "gbit_s": sig(batched["gbit_s"])}
+    if served:
+        out["served"] = {"requests": served["requests"],
+                         "saturated_req_per_s": sig(served["saturated"]["throughput_per_s"]),
+                         "per_product_launch_req_per_s":
+                             sig(served["per_product_launches"]["throughput_per_s"]),
+                         "p50_p99_ms_0.5x": [sig(served["loads"]["0.5x"]["latency_ms"]["p50"]),
+                                             sig(served["loads"]["0.5x"]["latency_ms"]["p99"])],
+                         "p50_p99_ms_0.8x": [sig(served["loads"]["0.8x"]["latency_ms"]["p50"]),
+                                             sig(served["loads"]["0.8x"]["latency_ms"]["p99"])]}
+    return out
+
 
 def run_cuda(args):
     import numpy as np
@@ -454,6 +539,18 @@ def run_cuda(args):
             ev[k] = e
         record.append(ev)
 
+    # the FP64 pipe's peak on this GPU, measured outside the timed region
+    # (tm_probe_dfma: independent FMAs on every SM, CUDA events, best of 5)
+    probe = []
+    for _ in range(6):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fl = pkg.probe_dfma(4096, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        probe.append(fl / (a.elapsed_time(b) * 1e-3) / 1e12)
+    dfma_peak = max(probe[1:])
+
     for _ in range(args.warmup):
         one_step(None)
     torch.cuda.synchronize()
@@ -496,12 +593,12 @@ def run_cuda(args):
             for i in range(pkg.NPHASES):
                 phase[k][i].append(e[i].elapsed_time(e[i + 1]))
 
-    # roofline of the dominant kernel (the FFT passes): 3 complex FFTs of length
-    # M = N/2 per product at the conventional 5 M log2 M flops each
+    # roofline of the dominant kernel (the FFT passes): 3 real transforms of length
+    # N per product at the conventional 2.5 N log2 N flops each
     fft_flops, fft_ms, fft_launches = 0.0, 0.0, 0
     for k in kinds:
-        M = plans[k]["N"] // 2
-        fft_flops += nphase_steps * 3 * 5.0 * M * np.log2(M)
+        N = plans[k]["N"]
+        fft_flops += nphase_steps * 3 * 2.5 * N * np.log2(N)
         fft_ms += sum(phase[k][1]) + sum(phase[k][3])
         fft_launches += nphase_steps * 2 * plans[k]["fft_passes"]
     achieved = fft_flops / (fft_ms * 1e-3) / 1e12
@@ -604,7 +701,7 @@ def run_cuda(args):
                           tune=not args.no_autotune)
 
     paper_params = None
-    if not args.no_paper_params:
+    if args.paper_params:
         paper_params = run_paper_params(pkg, torch, np, workloads, max(3, min(args.steps, 7)),
                                         args.warmup, stream, flush, seed=2017 + rank)
         pkg.release()                   # the rows' plan tables (about 50 GB)
@@ -620,6 +717,10 @@ def run_cuda(args):
         batched = run_batched(pkg, torch, np, args.batch_count, max(3, min(args.steps, 10)),
                               args.warmup, stream, seed=4 + rank)
 
+    served = None
+    if not args.no_served:
+        served = served_section(pkg, torch, np, args.served_quick_count, seed=5 + rank)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -627,46 +728,26 @@ def run_cuda(args):
     cpu = None
     if not args.no_cpu_baseline:
         ts = oracle_products(n, range(3000, 3001), 0)
-        cpu = {"value": 2 * n / sum(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": 2 * n / sum(ts) / 1e9, "unit": UNIT, "cores": os.cpu_count() or 1,
+               "threads": 1, "kind": "oracle",
                "sample": f"one low + one high product at n={n} bits (C Karatsuba full "
                          "product + truncation by definition), 1 thread"}
     phases = {k: {pkg.PHASES[i]: round(statistics.median(phase[k][i]), 4)
                   for i in range(pkg.NPHASES)} for k in kinds}
+    ms = {k: {"p50": sig(statistics.median(per[k])), "p99": sig(float(np.percentile(per[k], 99)))}
+          for k in kinds}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"single low + high (+ full for the ratio) product, n = {n} bits, "
-                               "uniform random uint64 limbs (seeded PCG64)",
-                   "n_bits": n, "l2": "flushed (256 MB write) before every product",
-                   "parallelism": f"replicas x{world}"},
-        "lo_gbit_s": n * args.steps / (t_lo * 1e-3) / 1e9,
-        "hi_gbit_s": n * args.steps / (t_hi * 1e-3) / 1e9,
-        "full_gbit_s": n * args.steps / (t_full * 1e-3) / 1e9,
-        "t_lo_over_full": t_lo / t_full, "t_hi_over_full": t_hi / t_full,
-        "ms": {k: {"p50": statistics.median(per[k]),
-                   "p99": float(np.percentile(per[k], 99))} for k in kinds},
-        "phases_ms_median": phases,
-        "plans": {k: {x: plans[k][x] for x in ("b", "N", "lam_fwd", "lam_bwd", "fft_passes",
-                                                 "e_max")} for k in kinds},
-        "margin": margin, "status_after_timed_region": st["rc"],
-        "roofline": {"bound": "alu", "kernel": "k_fft_pass", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": FFT_TRAFFIC_N2P24 if n == 1 << 24 else None,
-                     "peak_measured_dfma": FP64_DFMA_MEASURED,
-                     "frac_of_measured": achieved / FP64_DFMA_MEASURED,
-                     "note": "FP64; 5 M log2 M flops per complex FFT of length M = N/2, 3 per "
-                             "product; peak = nominal FP64 (recipe table), frac_of_measured "
-                             "against the measured DFMA issue ceiling; traffic = ncu DRAM "
-                             "bytes per launch (profiles/k_fft_pass_n2p24.md)"},
-        "batched": batched,
-        "sizes": sizes,
-        "large": large,
-        "paper_parameters": paper_params,
-        "autotune": tuned,
-        "square_and_kept_operand": variants,
-        "division": division,
+        "data": "synthetic", "config": workload_config(n, world),
+        "roofline": {"bound": "alu", "kernel": "k_fft_pass", "achieved": sig(achieved),
+                     "peak": sig(dfma_peak), "unit": "TFLOP/s", "frac": sig(achieved / dfma_peak),
+                     "traffic": None,
+                     "note": "FP64-bound FFT passes: 2.5 N log2 N flops per real transform, 3 "
+                             "per product, over their device time (phase events); peak = FP64 "
+                             "FMA rate measured in this run (tm_probe_dfma); nominal FP64 1.25; "
+                             "traffic not taken for the tuned plans"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 2 * nl * 8,
@@ -674,7 +755,18 @@ def run_cuda(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s_timed": wall,
+        "ms": ms, "phases_ms_median": phases,
+        "plans": {k: {x: plans[k][x] for x in ("b", "N", "lam_fwd", "lam_bwd", "fft_passes")}
+                  | {"e_max": sig(plans[k]["e_max"]), "margin": sig(margin[k])} for k in kinds},
+        "status_after_timed_region": st["rc"],
+        "square_and_kept_operand": variants, "division": division,
+        "paper_parameters": paper_params,
     }
+    line["summary"] = summary_of(n, t_lo, t_hi, t_full, args.steps, e2e_val, achieved, dfma_peak,
+                                 sizes, large, batched, served)
+    line["detail"] = {"sizes": sizes, "large": large, "batched": batched, "served": served}
+    # the compact summary last: the end of the line carries every configuration
+    line["summary"] = line.pop("summary")
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -765,7 +857,7 @@ def run_large(pkg, torch, np, workloads, n, reps, warmup, stream, flush, seed,
                                                  res["full"]["adaptive"]["ms"])
     return {"n_bits": n, "operands": "uniform random uint64 limbs (seeded PCG64)",
             "l2": "flushed (256 MB write) before every product", "reps": reps,
-            **checks, "fp64_peak_tflops": FP64_PEAK_TFLOPS, **res}
+            **checks, **res}
 
 
 def run_sizes(pkg, torch, np, workloads, sizes, reps, warmup, stream, flush, seed,
