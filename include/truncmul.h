@@ -495,6 +495,24 @@ int tm_stream_status(void* stream, tm_report* rep);
 int tm_release(void);
 
 /*
+ * tm_convolution: the Convolution step of Section 2.1 on its own - the cyclic
+ * convolution out = x * y of two real sequences of length N in FP64, computed by
+ * the same kernels as the products (two forward FFTs of the packed sequences, the
+ * fused twist and pointwise product, one inverse FFT).
+ *   out, x, y  device arrays of N doubles; out must not overlap x or y (x == y is
+ *              allowed).
+ *   N          a transform length the products use: even, 2^a m with m one of the
+ *              odd parts listed for tm_mul_params, 4 <= N <= 2^31.
+ *   eta        optional (NULL): receives the error bound of this computation:
+ *              |out_k - (x*y)_k| <= eta ||x||_2 ||y||_2 for every k, derived for
+ *              the kernels' arithmetic (every FFT pass layout).
+ * Asynchronous on `stream`; uses the stream's workspace and the length's tables.
+ * Returns TM_OK, TM_EINVAL, TM_ENOMEM or TM_ECUDA.
+ */
+int tm_convolution(double* out, const double* x, const double* y, int64_t N, void* stream,
+                   double* eta);
+
+/*
  * tm_table_values: writes the twiddle tables the FFT kernels use into the
  * caller's device buffer `out` (enqueued on `stream`), so that their accuracy can
  * be checked; a checking facility with no counterpart in the paper.

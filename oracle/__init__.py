@@ -20,11 +20,18 @@ Contents (each function cites the passage of the paper it follows):
                (Sections 3.3 and 4.3) in exact arithmetic for small N.
 - ``fp64_ref`` Algorithms 1-3 step by step in numpy float64, with numpy's FFT as
                the Convolution black box (Section 2.1).
-- ``plan``     the oracle's own choice of (b, N, lambda) from the FP64 error bound.
+- ``plan``     the oracle's own choice of (b, N, lambda) from the FP64 error bound,
+               with the convolution's error (eta_conv) derived for the arithmetic of
+               the FFT kernels (Section 2.1's Convolution step).
+- ``tft``      the truncated-FFT question at the end of Section 2.2 as an
+               experiment: Algorithm 2 with a length-N cyclic product (any N) and
+               with the product at the points of a truncated FFT, and the ring maps
+               from R[X]/A(X) to both.
 - ``division`` the reciprocal floor((2^(2k) - 1) / m) and floor division by
                definition, plus binary long division as a cross-check (Section 1
                names Barrett's reduction as an application of the high product).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py``; none is "parity unpinned".
+``tests/test_oracle_*.py`` (the convolution bound also by
+``tests/test_fft_error_bound.py``); none is "parity unpinned".
 """

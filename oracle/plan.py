@@ -12,11 +12,9 @@ empirically, and the bounds below replace that by a proof-style budget):
   satisfies the method's hypothesis is used: N >= n/b (Theorem 2.2),
   (N+1) b >= n + lg N + 2 (Theorem 2.3), L >= 2 N_d - 1 with N_d b >= n + 1
   (full product, Theorem 2.1 with any cyclic length that holds the product);
-- the convolution error is ||x||_2 ||y||_2 ((1+u)^3K (1+sqrt5 u)^(3K+1)
-  (1+tau)^3K - 1), the explicit FFT bound the paper points to in Section 2.1
-  (Brent-Zimmermann Theorem 3.6), with K radix-2-equivalent levels per
-  transform: lg L, plus 2 for every odd prime factor, plus 2 for the real-data
-  pre/post-processing;
+- the convolution error is ||x||_2 ||y||_2 eta_conv(L), derived for the
+  arithmetic of the FFT kernels (Section 2.1 leaves the Convolution step's
+  explicit bound to the implementation; see eta_conv below);
 - the maps' coefficient bounds follow Lemmas 3.5 and 4.7 (with the proof of
   Lemma 4.7 carried to |gamma_{k,r}| <= 2^-rb exp((r-1) H_r / N)), their norm
   growth Lemmas 3.8/3.9 and 4.8/4.9 (with ||X H|| <= (1 + 2^-b)||H|| mod A
@@ -29,7 +27,6 @@ empirically, and the bounds below replace that by a proof-style budget):
 import math
 
 U = 2.0 ** -53
-TAU = 2.0 * U
 E_TARGET = 0.45
 B_MIN, B_MAX = 4, 24
 ODD_PARTS = (1, 3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49, 63, 75, 81, 105, 125, 135, 147,
@@ -71,14 +68,74 @@ def smooth_at_least(x: int) -> int:
     return best
 
 
-def levels(L: int) -> int:
-    return ceil_log2(L) + 2 * odd_prime_factor_count(L) + 2
+# ---------------------------------------------- error of the FP64 convolution
+#
+# The convolution of real length L runs as two forward complex FFTs of length
+# M = L/2, the fused twist / pointwise product and one inverse FFT. Rounding model:
+# every floating-point operation (and FMA) is exact times (1 + e), |e| <= U, and
+# every twiddle-table entry and DFT constant is within U of its exact value.
+# Per stage kind, with the butterfly input x (R complex values):
+#   LOCAL_L2[kind]: ||error of the stage outputs||_2 <= c U sqrt(R) ||x||_2,
+#   LOCAL_L1[kind]: |error of any one output|        <= c U ||x||_1,
+# for a radix-R butterfly whose inputs 1..R-1 are first multiplied by table
+# twiddles ("tw": each product within 3U |x|: U from the table, 2U from the
+# complex product), the tangent-form radix-4 butterfly, and the four-step
+# twiddle product between passes.
+TWIDDLE_PRODUCT = 3.0
+LOCAL_L1 = {"r2tw": TWIDDLE_PRODUCT + 1.0, "r4tan": 6.0, "outer": TWIDDLE_PRODUCT}
+LOCAL_L2 = {"r2tw": TWIDDLE_PRODUCT + 1.0, "r4tan": (math.sqrt(112.0) + 2.0) / 2.0,
+            "outer": TWIDDLE_PRODUCT}
+for _R in (3, 5, 7):
+    # symmetric sums / differences (1 rounding each, twiddle errors on their
+    # inputs), constants within U, then (R-1)/2 roundings in each half's FMA chain
+    # and one final addition: per output sqrt(2) (3 + 2) U + (R - 1) U + U of ||x||_1
+    LOCAL_L1[f"r{_R}tw"] = math.sqrt(2.0) * (TWIDDLE_PRODUCT + 2.0) + (_R - 1) + 1.0
+    LOCAL_L2[f"r{_R}tw"] = math.sqrt(_R) * LOCAL_L1[f"r{_R}tw"]
+TWIST = 20.0          # roundings of the twist, relative to ||x||_2 ||y||_2 (1 + eF)^2
+Q_NORM = 2.0          # ||Q||_1 <= 2 ||x||_2 ||y||_2 for the inverse FFT's input
+SECOND_ORDER = 1.0 + 2.0 ** -20
+
+
+def stage_lists(M: int):
+    """Every stage multiset a layout of the complex FFT of length M can have, priced
+    at the dearer variant (with twiddles): for 1, 2 and 3 passes, the odd primes of
+    M one stage each, the factor 2^a as radix-4 stages plus as many radix-2 stages as
+    passes allow (at most one per pass, same parity as a), and passes - 1 four-step
+    twiddle stages."""
+    a, m = 0, M
+    while m % 2 == 0:
+        m //= 2
+        a += 1
+    odd = []
+    for R in (3, 5, 7):
+        while m % R == 0:
+            m //= R
+            odd.append(f"r{R}tw")
+    assert m == 1, M
+    lists = []
+    for passes in (1, 2, 3):
+        r2 = min(passes, a)
+        if (a - r2) % 2:
+            r2 -= 1
+        lists.append(odd + ["r4tan"] * ((a - r2) // 2) + ["r2tw"] * r2
+                     + ["outer"] * (passes - 1))
+    return lists
 
 
 def eta_conv(L: int) -> float:
-    K = levels(L)
-    return math.expm1(3 * K * math.log1p(U) + (3 * K + 1) * math.log1p(math.sqrt(5) * U)
-                      + 3 * K * math.log1p(TAU))
+    """Bound eta with |computed_k - (x*y)_k| <= eta ||x||_2 ||y||_2 for the FP64 cyclic
+    convolution of real length L (Section 2.1's Convolution step) as the FFT kernels
+    compute it: the forward errors eF (2-norm) of both operands, the twist's
+    roundings, and the inverse FFT's per-output error on an input of 1-norm
+    Q_NORM (1 + eF)^2 ||x|| ||y||; the worst of the possible layouts."""
+    worst = 0.0
+    for stages in stage_lists(L // 2):
+        eF = math.prod(1.0 + SECOND_ORDER * LOCAL_L2[k] * U for k in stages) - 1.0
+        eI = math.prod(1.0 + SECOND_ORDER * LOCAL_L1[k] * U for k in stages) - 1.0
+        grow = (1.0 + eF) ** 2
+        twist = SECOND_ORDER * TWIST * U * grow
+        worst = max(worst, 2.0 * eF + eF * eF + twist + (Q_NORM * grow + twist) * eI)
+    return worst
 
 
 _H = [0.0]
@@ -269,8 +326,6 @@ def choose(kind: str, n: int) -> dict:
 
 # ------------------------------------------------ measured digit norms
 
-MEASURE_SPAN = 3.5    # measure only when b + 1's worst-case bound is <= this x E_TARGET
-
 def bound_lo_measured(b: int, N: int, nu: float, nv: float) -> float:
     """bound_lo with the measured norms ||U||_2, ||V||_2 of the balanced digits in
     place of the worst case 2^(b-1) sqrt(N); per-coefficient terms unchanged."""
@@ -330,8 +385,10 @@ def measured_length(kind: str, n: int, b: int) -> int:
 def adaptive_choice(kind: str, n: int, u: int, v: int) -> dict:
     """The plan of the data-dependent digit size: the worst-case plan's b plus one,
     at its shortest admissible length, when the bound on the operands' measured
-    digit norms is <= E_TARGET and that length is shorter; else the worst-case
-    plan. Norms come from the balanced digits of the split step (trace.split)."""
+    digit norms is <= E_TARGET and that length is shorter (b + 1 is then
+    certified for these operands); else the worst-case plan. Norms come from the
+    balanced digits of the split step (trace.split). A caller may still keep the
+    worst-case plan where b + 1 is admissible (for example to skip measuring)."""
     from . import trace
     base = choose(kind, n)
     b = base["b"] + 1
@@ -341,17 +398,6 @@ def adaptive_choice(kind: str, n: int, u: int, v: int) -> dict:
     if N >= base["N"]:
         return base
     count = full_digits(n, b) if kind == "full" else N
-    # the library measures only when b + 1's worst-case bound is within MEASURE_SPAN
-    # of the target
-    w = 2.0 ** (b - 1) * math.sqrt(count)
-    if kind == "lo":
-        Ew = bound_lo_measured(b, N, w, w)
-    elif kind == "hi":
-        Ew = bound_hi_measured(b, N, w, w, 2.0 ** b, 2.0 ** b)
-    else:
-        Ew = bound_full_measured(N, w, w)
-    if Ew > MEASURE_SPAN * E_TARGET:
-        return base
     du = trace.split(kind, u, n, b, count)
     dv = trace.split(kind, v, n, b, count)
     if kind == "hi":

@@ -83,7 +83,7 @@ EXPORTS = ["tm_mul", "tm_mul_params", "tm_mul_adaptive", "tm_mul_full", "tm_mul_
            "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
-           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror", "tm_probe_dfma", "tm_table_values"]
+           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror", "tm_probe_dfma", "tm_table_values", "tm_convolution"]
 
 _lib = None
 
@@ -122,6 +122,8 @@ def load(path: str = None):
     lib.tm_probe_dfma.restype = ctypes.c_int
     lib.tm_table_values.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P]
     lib.tm_table_values.restype = ctypes.c_int
+    lib.tm_convolution.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_double)]
+    lib.tm_convolution.restype = ctypes.c_int
     D = ctypes.POINTER(Desc)
     lib.tm_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), D, ctypes.c_uint32, P]
     lib.tm_batch_launch.argtypes = [P, P]
@@ -277,6 +279,21 @@ def mul_events(kind, u, v, n_bits: int, events, out=None, stream=None):
     if rc:
         raise TruncMulError(rc, "tm_mul_events")
     return out
+
+
+def convolution(x, y, out=None, stream=None):
+    """tm_convolution: the FP64 cyclic convolution of the real float64 device
+    tensors x and y (length N). Returns (out, eta) with |out_k - (x*y)_k| <=
+    eta ||x||_2 ||y||_2."""
+    import torch
+    if out is None:
+        out = torch.empty_like(x)
+    eta = ctypes.c_double()
+    rc = load().tm_convolution(_ptr(out), _ptr(x), _ptr(y), int(x.numel()), _stream_ptr(stream),
+                               ctypes.byref(eta))
+    if rc:
+        raise TruncMulError(rc, "tm_convolution")
+    return out, eta.value
 
 
 def table_values(which: int, length: int, count: int):

@@ -1476,6 +1476,39 @@ int tm_release(void) {
   return TM_OK;
 }
 
+int tm_convolution(double* out, const double* x, const double* y, int64_t N, void* stream,
+                   double* eta) {
+  using namespace tmul;
+  if (!out || !x || !y || N < 4 || N > (int64_t(1) << 31) || !is_valid_length(N))
+    return TM_EINVAL;
+  if (eta) *eta = conv_error_bound(N);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PlanParams p;
+  p.kind = TM_FULL;               // twiddle and twist tables only (no map rows)
+  p.b = 0;                        // a cache key of its own
+  p.n = 64;
+  p.N = N;
+  std::shared_ptr<PlanEntry> pe;
+  int rc = get_tables(p, false, s, &pe);
+  if (rc) return rc;
+  Workspace* ws = nullptr;
+  rc = get_workspace(s, workspace_bytes(p), &ws);
+  if (rc) return rc;
+  ensure_kernel_attributes();
+  const int64_t M = N / 2;
+  double2* R0 = reinterpret_cast<double2*>(ws->base);
+  double2* R1 = reinterpret_cast<double2*>(ws->base + region_bytes(p, M));
+  double2* bufs[2] = {R0, R1};
+  // the real sequences are their packed complex sequences (x_2j + i x_2j+1)
+  TM_CHECK(cudaMemcpyAsync(R0, x, size_t(N) * 8, cudaMemcpyDeviceToDevice, s));
+  TM_CHECK(cudaMemcpyAsync(R0 + M, y, size_t(N) * 8, cudaMemcpyDeviceToDevice, s));
+  int cur = launch_fft(*pe, bufs, 0, -1, 2, M, s);
+  launch_twist(bufs[cur], bufs[cur] + M, bufs[cur ^ 1], M, pe->tw + pe->twc_off, N, 1, 0, 0, s);
+  cur = launch_fft(*pe, bufs, cur ^ 1, 1, 1, M, s);
+  TM_CHECK(cudaMemcpyAsync(out, bufs[cur], size_t(N) * 8, cudaMemcpyDeviceToDevice, s));
+  return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;
+}
+
 int tm_table_values(int which, int64_t len, int64_t count, double* out, void* stream) {
   if (!out || len < 1 || count < 0 || len > (int64_t(1) << 40)) return TM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

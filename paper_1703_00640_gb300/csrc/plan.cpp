@@ -27,7 +27,6 @@ namespace tmul {
 namespace {
 
 constexpr double kU = 1.0 / 9007199254740992.0;  // 2^-53
-constexpr double kTau = 2.0 * kU;                // twiddle table error
 constexpr double kTarget = 0.45;
 constexpr int kBMin = 4, kBMax = 24;
 constexpr double kSpan = 1.25;
@@ -47,10 +46,72 @@ int odd_factor_count(int64_t L) {
   return c;
 }
 
+// Error of one FP64 cyclic convolution of real length L as the kernels compute it:
+// two forward complex FFTs of length M = L/2 (Stockham stages of radix 2, 3, 4, 5, 7
+// in one to three passes, four-step twiddles between passes), the fused twist and
+// pointwise product, one inverse FFT. For real inputs x, y every output satisfies
+// |computed_k - (x*y)_k| <= eta_conv(L) ||x||_2 ||y||_2. Derivation (Section 2.1's
+// Convolution step, with the rounding model fl(a op b) = (a op b)(1 + e), |e| <= u,
+// and every table entry and DFT constant within u of its exact value):
+//  - a stage's local error per butterfly is at most gamma sqrt(R) ||in||_2 in the
+//    2-norm and at most delta ||in||_1 in each output (constants below, units of
+//    u); the forward FFT's relative 2-norm error is eF = prod(1 + gamma_s) - 1;
+//  - a forward error dZ of the packed spectrum is the spectrum of a real vector
+//    of norm ||dZ|| / sqrt(M), so its effect on each output is at most
+//    eF ||x|| ||y|| (Cauchy-Schwarz on the cyclic convolution), for each operand;
+//  - the twist's roundings add at most kTwist (1 + eF)^2 ||x|| ||y|| to the
+//    1-norm of the inverse FFT's input Q, whose 1-norm is at most
+//    2 (1 + eF)^2 ||x|| ||y|| (Q_k = ((1 + i w^-k) P_k + (1 - i w^-k) P_(k+M)) / N
+//    with P = X X', and |1 + i w^-k|^2 + |1 - i w^-k|^2 = 4);
+//  - each inverse output's error is at most ||Q||_1 (prod(1 + delta_s) - 1): a
+//    stage-s node reaches an output along one path of unit-modulus factors, and
+//    the nodes of stage s that reach one output hold partial sums of disjoint
+//    parts of Q.
+// The layout (passes, placement of the odd primes) is the autotuner's, so the
+// bound takes the worst one: every stage priced with twiddles, as many radix-2
+// stages as the pass count allows, two four-step twiddle stages.
+namespace fftbound {
+constexpr double kMu = 3.0;             // product by a table twiddle: table u, cmul 2u
+constexpr double kR2 = kMu + 1.0;       // radix 2 with a twiddle (both norms)
+constexpr double kR4tG = 6.3;           // tangent-form radix 4: 2-norm, (sqrt(112) + 2) / 2
+constexpr double kR4tD = 6.0;           // tangent-form radix 4: per output
+constexpr double kOuter = kMu;          // four-step twiddle product
+constexpr double kTwist = 20.0;         // twist + pointwise roundings, relative to ||x|| ||y||
+constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
+// radix R = 3, 5, 7 with twiddles, h = (R - 1) / 2 chained FMAs per output half:
+// per output sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt(R) times that
+double odd_delta(int R) { return std::sqrt(2.0) * (kMu + 2.0) + 2.0 * ((R - 1) / 2) + 1.0; }
+}  // namespace fftbound
+
 double eta_conv(int64_t L) {
-  const double K = ceil_lg(L) + 2.0 * odd_factor_count(L) + 2.0;
-  return std::expm1(3 * K * std::log1p(kU) + (3 * K + 1) * std::log1p(std::sqrt(5.0) * kU) +
-                    3 * K * std::log1p(kTau));
+  using namespace fftbound;
+  int64_t m = L / 2;
+  int a = 0;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  double oddG = 1.0, oddD = 1.0;                    // products over the odd-radix stages
+  for (int R : {3, 5, 7})
+    while (m % R == 0) {
+      m /= R;
+      oddG *= 1.0 + kSlack * std::sqrt(double(R)) * odd_delta(R) * kU;
+      oddD *= 1.0 + kSlack * odd_delta(R) * kU;
+    }
+  double worst = 0.0;
+  for (int P = 1; P <= 3; ++P) {
+    int r2 = std::min(P, a);
+    if ((a - r2) % 2) --r2;                         // radix-2 stages: one per pass at most
+    const int r4 = (a - r2) / 2;
+    const double g = oddG * std::pow(1.0 + kSlack * kR4tG * kU, r4) *
+                     std::pow(1.0 + kSlack * kR2 * kU, r2) *
+                     std::pow(1.0 + kSlack * kOuter * kU, P - 1);
+    const double d = oddD * std::pow(1.0 + kSlack * kR4tD * kU, r4) *
+                     std::pow(1.0 + kSlack * kR2 * kU, r2) *
+                     std::pow(1.0 + kSlack * kOuter * kU, P - 1);
+    const double eF = g - 1.0, eI = d - 1.0, grow = (1.0 + eF) * (1.0 + eF);
+    const double e = 2.0 * eF + eF * eF + kSlack * kTwist * kU * grow +
+                     (2.0 * grow + kSlack * kTwist * kU * grow) * eI;
+    worst = std::max(worst, e);
+  }
+  return worst;
 }
 
 // |gamma_{k,r}| <= 2^-rb exp((r-1) H_r / N): the proof of Lemma 4.7 with
@@ -387,6 +448,8 @@ int64_t measured_length(int kind, uint64_t n, int b) {
 }
 
 double bound_target() { return kTarget; }
+
+double conv_error_bound(int64_t L) { return eta_conv(L); }
 
 DigitNorms worst_norms(int kind, uint64_t n, int b, int64_t N) {
   DigitNorms w;

@@ -108,6 +108,9 @@ int measured_params(int kind, uint64_t n, int b, int64_t N, const DigitNorms& dn
 // and the target every plan's bound must meet.
 DigitNorms worst_norms(int kind, uint64_t n, int b, int64_t N);
 double bound_target();
+// eta with |computed_k - (x*y)_k| <= eta ||x||_2 ||y||_2 for the FP64 cyclic
+// convolution of real length L as the FFT kernels compute it (any pass layout).
+double conv_error_bound(int64_t L);
 
 // Exposed for tests of the planner.
 bool is_valid_length(int64_t L);

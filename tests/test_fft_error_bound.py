@@ -1,0 +1,253 @@
+"""Pins of the FP64 convolution error bound (oracle.plan.eta_conv and its stage
+constants) against the arithmetic the FFT kernels perform, on the CPU.
+
+tests/fft_model.py performs the kernels' operation sequences (butterflies,
+table-twiddle products, four-step twiddles, the fused twist) on binary64 floats
+with a correctly rounded FMA and the tables' values. Here:
+- every butterfly kind's exact rounding error (against its exact result, with the
+  exact twiddles and DFT constants, to about 200 bits) stays within the oracle's
+  local constants, per output in the 1-norm of the inputs and for the whole
+  butterfly in the 2-norm, over every twiddle angle of several stages, both
+  directions and inputs of mixed magnitudes;
+- the model convolution's exact error (integer inputs: the exact convolution is
+  an integer) stays within eta_conv(N) ||x||_2 ||y||_2 on extreme-digit inputs,
+  for one- and two-pass layouts and every radix;
+- the two norm facts the bound composes with are checked at inputs that attain
+  them: a forward error dZ acts on each output as the convolution of a real
+  vector of norm ||dZ|| / sqrt(M) (Cauchy-Schwarz, attained by a reversed copy),
+  and the inverse FFT's input Q has ||Q||_1 <= 2 ||x||_2 ||y||_2, with inputs that
+  come close to 2 (so the factor cannot be 1).
+Worst-case rounding alignment is not reached by sampling (the measured errors
+are about a third of the per-butterfly constants and a hundredth of eta), so these
+pins establish validity on what they sample and the exact norm algebra, not
+sharpness of the rounding constants."""
+import math
+import random
+from decimal import Decimal, localcontext
+
+import numpy as np
+import pytest
+
+import fft_model as F
+import hp_trig
+from oracle import plan as P
+
+U = P.U
+
+
+def _dexp(num, den):
+    c, s = hp_trig.cossin_2pi(num % den, den)
+    return (c, -s)
+
+
+def _dmul(a, b):
+    return (a[0] * b[0] - a[1] * b[1], a[0] * b[1] + a[1] * b[0])
+
+
+def _exact_butterfly(x, R, S, tw):
+    """sum_t exp(2 pi i S j t / R) tw_t x_t for every j (tw_t the exact twiddle
+    multipliers of the direction S)."""
+    out = []
+    for j in range(R):
+        acc = (Decimal(0), Decimal(0))
+        for t in range(R):
+            root = _dexp(j * t, R)
+            if S > 0:
+                root = (root[0], -root[1])
+            w = _dmul(tw[t], root)
+            v = _dmul((Decimal(x[t][0]), Decimal(x[t][1])), w)
+            acc = (acc[0] + v[0], acc[1] + v[1])
+        out.append(acc)
+    return out
+
+
+def _errors(y, ex):
+    return [float(((Decimal(a[0]) - b[0]) ** 2 + (Decimal(a[1]) - b[1]) ** 2).sqrt())
+            for a, b in zip(y, ex)]
+
+
+def _inputs(rnd, R):
+    kind = rnd.randrange(4)
+    if kind == 0:
+        return [(rnd.uniform(-1, 1), rnd.uniform(-1, 1)) for _ in range(R)]
+    if kind == 1:                     # mixed magnitudes
+        return [(rnd.uniform(-1, 1) * 2.0 ** rnd.randint(-30, 0),
+                 rnd.uniform(-1, 1) * 2.0 ** rnd.randint(-30, 0)) for _ in range(R)]
+    if kind == 2:                     # extreme digits
+        return [(float(rnd.choice([-2048, 2048])), float(rnd.choice([-2048, 2048])))
+                for _ in range(R)]
+    return [(rnd.uniform(0.5, 1), 0.0) for _ in range(R)]
+
+
+KINDS = [("r2tw", 2), ("r4tan", 4), ("r3tw", 3), ("r5tw", 5), ("r7tw", 7)]
+
+
+@pytest.mark.parametrize("key,R", KINDS, ids=[k for k, _ in KINDS])
+def test_butterflies_within_local_constants(key, R):
+    """Twiddled butterflies (and the same radix without twiddles, which the bound
+    prices at the twiddled constant) within the oracle's LOCAL_L1 / LOCAL_L2."""
+    rnd = random.Random(R)
+    tables = F.Tables()
+    worst1 = worst2 = 0.0
+    with localcontext() as ctx:
+        ctx.prec = 60
+        for Ns in (1, 2, 8, 32):
+            for kk in range(Ns):
+                for S in (-1, 1):
+                    x = _inputs(rnd, R)
+                    if R == 4 and Ns > 1:
+                        y = F.radix4_tan(x, tables.tan(kk, Ns), S)
+                        tw = [_dexp(0, 1)] + [_dexp(kk * t, 4 * Ns) for t in (1, 2, 3)]
+                    else:
+                        xs = list(x)
+                        if Ns > 1:
+                            for t in range(1, R):
+                                w = tables.tw(kk * t, Ns * R)
+                                xs[t] = F.cmul(xs[t], w) if S < 0 else F.cmulc(xs[t], w)
+                        y = F.DFT[R](xs, S)
+                        tw = [_dexp(kk * t, Ns * R) for t in range(R)]
+                    if S > 0:
+                        tw = [(t[0], -t[1]) for t in tw]
+                    ex = _exact_butterfly(x, R, S, tw)
+                    err = _errors(y, ex)
+                    n1 = sum(math.hypot(*v) for v in x)
+                    n2 = math.sqrt(sum(a * a + b * b for a, b in x))
+                    r1 = max(err) / (U * n1)
+                    r2 = math.sqrt(sum(e * e for e in err)) / (U * math.sqrt(R) * n2)
+                    assert r1 <= P.LOCAL_L1[key], (key, Ns, kk, S, r1)
+                    assert r2 <= P.LOCAL_L2[key], (key, Ns, kk, S, r2)
+                    worst1, worst2 = max(worst1, r1), max(worst2, r2)
+    print(f"{key}: worst per-output {worst1:.2f} U (bound {P.LOCAL_L1[key]:.2f}), "
+          f"worst 2-norm {worst2:.2f} U (bound {P.LOCAL_L2[key]:.2f})")
+
+
+def test_twiddle_product_within_constant():
+    """The four-step twiddle product (one table entry, one complex product)."""
+    rnd = random.Random(3)
+    tables = F.Tables()
+    with localcontext() as ctx:
+        ctx.prec = 60
+        for length in (12, 40, 96, 1000):
+            for m in range(0, length, max(1, length // 50)):
+                for S in (-1, 1):
+                    a = (rnd.uniform(-1, 1), rnd.uniform(-1, 1))
+                    w = tables.tw(m, length)
+                    got = F.cmul(a, w) if S < 0 else F.cmulc(a, w)
+                    e = _dexp(m, length)
+                    if S > 0:
+                        e = (e[0], -e[1])
+                    want = _dmul((Decimal(a[0]), Decimal(a[1])), e)
+                    err = _errors([got], [want])[0]
+                    assert err <= P.TWIDDLE_PRODUCT * U * math.hypot(*a)
+
+
+CONV_CASES = [(8, None), (12, None), (20, None), (28, None), (40, None), (56, None),
+              (96, (4, 12)), (120, (12, 5)), (168, (12, 7)), (256, (8, 16)),
+              (420, (14, 15))]
+
+
+@pytest.mark.parametrize("N,split", CONV_CASES, ids=[f"N{n}" for n, _ in CONV_CASES])
+def test_model_convolution_within_eta(N, split):
+    rnd = random.Random(N)
+    tables = F.Tables()
+    b = 13
+    worst = 0.0
+    for trial in range(4):
+        if trial == 0:
+            x = [2 ** (b - 1)] * N
+            y = [-(2 ** (b - 1))] * N
+        elif trial == 1:
+            x = [rnd.choice([-1, 1]) * 2 ** (b - 1) for _ in range(N)]
+            y = [rnd.choice([-1, 1]) * 2 ** (b - 1) for _ in range(N)]
+        else:
+            x = [rnd.randint(-2 ** (b - 1), 2 ** (b - 1)) for _ in range(N)]
+            y = [rnd.randint(-2 ** (b - 1), 2 ** (b - 1)) for _ in range(N)]
+        got = F.convolution(x, y, split, tables)
+        want = F.exact_cyclic(x, y)
+        err = max(abs(Decimal(g) - w) for g, w in zip(got, want))
+        norm = math.sqrt(sum(v * v for v in x)) * math.sqrt(sum(v * v for v in y))
+        ratio = float(err) / (P.eta_conv(N) * norm)
+        assert ratio <= 1.0, (N, trial, ratio)
+        worst = max(worst, ratio)
+    print(f"N={N}: largest error {worst:.4f} of eta ||x|| ||y||")
+
+
+def _pack(x):
+    return x[0::2] + 1j * x[1::2]
+
+
+def _twist_exact(Zu, Zv, N):
+    """The twist formula in complex128 (the norm facts need no rounding model)."""
+    M = N // 2
+    k = np.arange(M)
+    km = (-k) % M
+    w = np.exp(-2j * np.pi * k / N)
+    c = (1 + w * w) / (2 * N)
+    A, B = Zu, np.conj(Zu[km])
+    A1, B1 = Zv, np.conj(Zv[km])
+    Q = (2 / N) * A * A1 - c * (A - B) * (A1 - B1)
+    return Q
+
+
+@pytest.mark.parametrize("N", [16, 60, 256])
+def test_twist_is_the_packed_product_spectrum(N):
+    """F*_M Q(Z_x, Z_y) is the packed cyclic convolution of x and y for real x, y
+    (the identity the bound's composition rests on), and Q_k =
+    ((1 + i w^-k) P_k + (1 - i w^-k) P_(k+M)) / N with P = X X'."""
+    rng = np.random.default_rng(N)
+    x, y = rng.normal(size=N), rng.normal(size=N)
+    M = N // 2
+    Q = _twist_exact(np.fft.fft(_pack(x)), np.fft.fft(_pack(y)), N)
+    q = np.fft.ifft(Q) * M
+    conv = np.real(np.fft.ifft(np.fft.fft(x) * np.fft.fft(y)))
+    assert np.allclose(q, _pack(conv), atol=1e-9 * np.abs(conv).max())
+    X, Y = np.fft.fft(x), np.fft.fft(y)
+    Pk = X * Y
+    k = np.arange(M)
+    wi = np.exp(2j * np.pi * k / N)
+    assert np.allclose(Q, ((1 + 1j * wi) * Pk[:M] + (1 - 1j * wi) * Pk[M:]) / N,
+                       atol=1e-9 * np.abs(Q).max())
+
+
+@pytest.mark.parametrize("N", [16, 64, 240])
+def test_forward_error_acts_as_a_real_convolution(N):
+    """A spectrum error dZ (any complex vector) changes the packed result by the
+    convolution of the real vector dx with pack(dx) = F^-1 dZ, ||dx|| =
+    ||dZ|| / sqrt(M): each output changes by at most ||dZ|| ||y|| / sqrt(M), and a
+    reversed copy of y attains it."""
+    rng = np.random.default_rng(N)
+    M = N // 2
+    y = rng.normal(size=N)
+    Zy = np.fft.fft(_pack(y))
+    for trial in range(3):
+        if trial < 2:
+            dZ = rng.normal(size=M) + 1j * rng.normal(size=M)
+        else:                                  # dx = y reversed: output 0 attains it
+            dx = np.roll(y[::-1], 1)
+            dZ = np.fft.fft(_pack(dx))
+        dq = np.fft.ifft(_twist_exact(dZ, Zy, N)) * M
+        change = np.concatenate([dq.real[:, None], dq.imag[:, None]], axis=1).ravel()
+        bound = np.linalg.norm(dZ) / math.sqrt(M) * np.linalg.norm(y)
+        assert np.abs(change).max() <= bound * (1 + 1e-12)
+        if trial == 2:
+            assert np.abs(change).max() >= bound * (1 - 1e-9)
+
+
+@pytest.mark.parametrize("N", [64, 256, 1024])
+def test_inverse_input_one_norm(N):
+    """||Q||_1 <= 2 ||x||_2 ||y||_2 on random and extremal inputs; a pure tone at
+    the frequency where |1 - i w^-k| is largest comes within a few percent of 2."""
+    rng = np.random.default_rng(N)
+    M = N // 2
+    worst = 0.0
+    cases = [(rng.normal(size=N), rng.normal(size=N)) for _ in range(5)]
+    n = np.arange(N)
+    for f in (N // 4 + 1, N // 4 + N // 16, 3 * N // 8):
+        tone = np.cos(2 * np.pi * f * n / N + 0.3)
+        cases.append((tone, tone))
+    for x, y in cases:
+        Q = _twist_exact(np.fft.fft(_pack(x)), np.fft.fft(_pack(y)), N)
+        ratio = np.abs(Q).sum() / (np.linalg.norm(x) * np.linalg.norm(y))
+        assert ratio <= P.Q_NORM * (1 + 1e-12)
+        worst = max(worst, ratio)
+    assert worst > 1.3, worst            # the factor 2 is needed, 1 would be wrong
