@@ -63,8 +63,9 @@ extern "C" {
 #define TM_ENOMEM     -2   /* device or host allocation failed                   */
 #define TM_EPRECISION -3   /* margin above the a-priori bound, or 2^b not
                               dividing c_0: the output must not be trusted       */
-#define TM_ETIMEOUT   -4   /* reserved: no call of this version waits on the
-                              device                                             */
+#define TM_ETIMEOUT   -4   /* a single-launch product's grid-wide wait gave up
+                              after about a second (see tm_set_fused); the
+                              output must not be trusted                        */
 #define TM_ECUDA      -5   /* a CUDA runtime call failed                         */
 #define TM_ERANGE     -6   /* n too large for any FP64 plan of this library      */
 #define TM_EALIAS     -7   /* out overlaps u or v                                */
@@ -74,7 +75,11 @@ extern "C" {
  * library first enqueues a product), every bound the device checks the margin
  * against is multiplied by it: a small value such as 1e-12 makes every product
  * report TM_EPRECISION through every entry point while computing the same limbs.
- * Other values are ignored. */
+ * Other values are ignored.
+ * With TRUNCMUL_FAULT_BARRIER=1 (read once), the last CTA of every single-launch
+ * product and persistent batch leaves at the first grid barrier without counting
+ * itself in; the other CTAs' bounded waits (about a second) run out and the call
+ * reports TM_ETIMEOUT, the device staying usable. */
 
 /* ---- product kinds ---- */
 #define TM_FULL 0          /* Algorithm 1 */
@@ -230,14 +235,15 @@ int tm_mul_events(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v,
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
  *   Every call on a device shares the same array and leaves its contents for
- *   the next call (each call rebuilds its tables and clears its status word), so
- *   calls that overlap on the GPU - on different streams, threads or in flight
- *   at once - race and must be serialised by the caller.
- *   Cost of the rebuild: before the product, every call enqueues one memset and
- *   four to six small table kernels (twiddles, tangent-form and twist tables, map
- *   rows, and for the high product kappa and rho^-j, all computed on the
- *   device; no host-to-device copy), a few microseconds next to the product's
- *   own kernels at n = 65536.
+ *   the next call: each call clears its status word, and rebuilds the plan's
+ *   tables unless the previous call on the device used the same plan (kind and
+ *   n giving the same digit size and length). Calls that overlap on the GPU - on
+ *   different streams, threads or in flight at once - race and must be
+ *   serialised by the caller.
+ *   Cost of a rebuild: four to six table kernels (twiddles, tangent-form and
+ *   twist tables in double-double arithmetic, map rows, and for the high
+ *   product kappa and rho^-j, all computed on the device; no host-to-device
+ *   copy) before the product's own kernels.
  *   rep as for tm_mul (NULL = asynchronous; a non-NULL rep waits and reports).
  */
 #define TM_STATIC_MAX_BITS 65536
@@ -493,6 +499,30 @@ int tm_stream_status(void* stream, tm_report* rep);
 /* tm_release: frees every plan table and workspace of the current device.
  * No call may be in flight on that device. */
 int tm_release(void);
+
+/*
+ * tm_set_fused: how products run. A product is either a sequence of per-phase
+ * kernel launches (maps, FFT passes, twist, back map, carry scan), or one
+ * cooperative launch that runs the same phases with grid-wide barriers between
+ * them, which removes the launch gaps that dominate small and medium sizes. The
+ * arithmetic is the same, so the results are identical.
+ *   mode 0  automatic (the default): per-phase launches, and batches as a
+ *           graph of per-phase launches (measured faster on GB300: a grid
+ *           barrier costs about as much as a launch gap, and the 4096-product
+ *           batch takes 29 ms as one persistent launch against 19.5 ms);
+ *   mode 1  always per-phase launches (the same as mode 0 in this version);
+ *   mode 2  one cooperative launch per single product, and every batch created
+ *           afterwards as one persistent launch under a one-node CUDA graph,
+ *           whenever the FFT layout allows it (sub-transforms of at most 2048
+ *           points).
+ * Applies to tm_mul and the calls built on it and to batches created afterwards
+ * (process wide). tm_mul_events, tm_coeffs and kept operands always use
+ * per-phase launches.
+ * The barrier waits are bounded: a wait that gives up (about a second) makes the
+ * call report TM_ETIMEOUT instead of hanging. No counterpart in the paper.
+ * Returns TM_OK or TM_EINVAL.
+ */
+int tm_set_fused(int mode);
 
 /*
  * tm_convolution: the Convolution step of Section 2.1 on its own - the cyclic

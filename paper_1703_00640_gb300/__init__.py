@@ -83,7 +83,7 @@ EXPORTS = ["tm_mul", "tm_mul_params", "tm_mul_adaptive", "tm_mul_full", "tm_mul_
            "tm_reciprocal",
            "tm_barrett_create", "tm_barrett_divrem", "tm_barrett_reciprocal",
            "tm_barrett_destroy", "tm_coeffs",
-           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror", "tm_probe_dfma", "tm_table_values", "tm_convolution"]
+           "tm_plan_query", "tm_stream_status", "tm_release", "tm_strerror", "tm_probe_dfma", "tm_table_values", "tm_convolution", "tm_set_fused"]
 
 _lib = None
 
@@ -124,6 +124,8 @@ def load(path: str = None):
     lib.tm_table_values.restype = ctypes.c_int
     lib.tm_convolution.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_double)]
     lib.tm_convolution.restype = ctypes.c_int
+    lib.tm_set_fused.argtypes = [ctypes.c_int]
+    lib.tm_set_fused.restype = ctypes.c_int
     D = ctypes.POINTER(Desc)
     lib.tm_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), D, ctypes.c_uint32, P]
     lib.tm_batch_launch.argtypes = [P, P]
@@ -279,6 +281,17 @@ def mul_events(kind, u, v, n_bits: int, events, out=None, stream=None):
     if rc:
         raise TruncMulError(rc, "tm_mul_events")
     return out
+
+
+FUSED_AUTO, FUSED_NEVER, FUSED_ALWAYS = 0, 1, 2
+
+
+def set_fused(mode: int) -> None:
+    """tm_set_fused: 0 automatic, 1 per-phase launches only, 2 one cooperative
+    launch per product wherever the layout allows."""
+    rc = load().tm_set_fused(int(mode))
+    if rc:
+        raise TruncMulError(rc, "tm_set_fused")
 
 
 def convolution(x, y, out=None, stream=None):

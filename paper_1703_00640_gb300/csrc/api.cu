@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/truncmul.h): plan cache, per-stream
 // workspaces and the launch sequence of one product.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -86,6 +87,14 @@ int cuda_fail(cudaError_t e) {
 }  // namespace
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool fault_leave_barrier() {
+  static const bool on = [] {
+    const char* v = std::getenv("TRUNCMUL_FAULT_BARRIER");
+    return v && v[0] == '1' && v[1] == 0;
+  }();
+  return on;
+}
 
 unsigned long long emax_fixed(double e_max) {
   static const double scale = [] {
@@ -430,7 +439,7 @@ int read_status(cudaStream_t s, DevStatus* status, tm_report* rep, bool may_allo
     TM_CHECK(cudaMemsetAsync(status, 0, sizeof(DevStatus), s));
     TM_CHECK(cudaStreamSynchronize(s));
   }
-  const int code = st.flags ? TM_EPRECISION : TM_OK;
+  const int code = (st.flags & kFlagTimeout) ? TM_ETIMEOUT : st.flags ? TM_EPRECISION : TM_OK;
   if (rep) {
     rep->margin = std::ldexp(double(st.margin_fx), -63);
     rep->status = code;
@@ -526,10 +535,181 @@ struct NvtxRange {
 };
 }  // namespace
 
+// ------------------------------------------------ single-launch products
+
+// tm_set_fused: 0 = automatic, 1 = never, 2 = whenever the layout allows it. A grid
+// barrier of the single-launch kernel (global atomics, about 3-4 us on GB300) costs
+// as much as a launch gap under programmatic dependent launch, and the persistent
+// batch kernel (one CTA pair per SM running every phase's block bodies) reaches 45%
+// of the FP64 pipe against the per-phase graph's overlapping branches, so automatic
+// mode uses per-phase launches and the per-phase batch graph.
+std::atomic<int> g_fused_mode{0};
+
+PassArgs pass_args(const PlanEntry& pe, int i, long long stride) {
+  const FftPass& fp = pe.fft.pass[i];
+  PassArgs a{};
+  a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
+  std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
+  a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
+  a.OA = fp.OA; a.OC = fp.OC; a.OS = fp.OS; a.Mp = fp.Mp;
+  a.batch_stride = stride;
+  a.tw_sub = pe.tw + fp.tw_sub;
+  a.tw_outer = fp.Mp ? pe.tw + fp.tw_outer : nullptr;
+  a.tw4 = reinterpret_cast<const Tan4*>(pe.tw + fp.tw4);
+  a.tw4_len = fp.tw4_len;
+  std::copy(fp.tw4_off, fp.tw4_off + kMaxStages, a.tw4_off);
+  a.need_wL = fp.need_wL ? 1 : 0;
+  return a;
+}
+
+size_t pass_smem(const FftPass& fp, int C) {
+  return (size_t((C * fp.L + 1) & ~1) + 2 * size_t(fp.tw4_len) +
+          (fp.need_wL ? size_t(fp.L) : 0)) * sizeof(double2);
+}
+
+// Sequences per CTA in a single-launch product: spread the pass over the resident
+// CTAs, at most as many points as kFusedThreads threads hold one radix-4 butterfly
+// each.
+int fused_C(const FftPass& fp, int resident) {
+  const int64_t cap = std::max(1, 4 * kFusedThreads / fp.L);
+  const int64_t spread = (fp.Q + resident - 1) / std::max(1, resident);
+  return int(std::max<int64_t>(1, std::min(cap, spread)));
+}
+
+// Resident CTAs of the single-launch kernel per (device, kind, shared memory),
+// queried once.
+int fused_resident(int kind, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_tuple(dev, kind, (smem + 1023) / 1024 * 1024);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  const int r = fused_max_blocks(kind, std::get<2>(key));
+  cache[key] = r;
+  return r;
+}
+
+// Whether a product of this plan runs as one cooperative launch.
+bool use_fused(const PlanEntry& pe) {
+  if (g_fused_mode.load() != 2) return false;
+  for (int i = 0; i < pe.fft.npass; ++i)
+    if (pe.fft.pass[i].L > 4 * kFusedThreads) return false;
+  return true;
+}
+
+// Every phase of the product in one cooperative launch (k_fused_product), on the
+// same buffers and with the same block arguments as the per-phase launches.
+int enqueue_fused(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
+                  cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws) {
+  const int64_t N = p.N, M = pe.M;
+  const size_t region = region_bytes(p, M);
+  double2* R0 = reinterpret_cast<double2*>(ws.base);
+  double2* R1 = reinterpret_cast<double2*>(ws.base + region);
+  double* theta = reinterpret_cast<double*>(ws.base + ws.size - 256);
+  unsigned* sync = reinterpret_cast<unsigned*>(ws.base + ws.size - 64);
+  const bool square = u == v;
+  FusedArgs A{};
+  A.square = square ? 1 : 0;
+  A.npass = pe.fft.npass;
+  fwd_args(kind, u, v, n, p, pe, reinterpret_cast<double*>(R0), theta, square, nullptr, square,
+           &A.fa);
+  double2* bufs[2] = {R0, R1};
+  int cur = 0;
+  size_t smem = 0, smem_cap = 0;
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    const FftPass& fp = pe.fft.pass[i];
+    smem_cap = std::max(smem_cap, pass_smem(fp, std::max(1, 4 * kFusedThreads / fp.L)));
+  }
+  const int resident = fused_resident(kind, smem_cap);
+  if (resident <= 0) return TM_ECUDA;
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    A.fwd[i] = pass_args(pe, i, M);
+    A.fwd[i].C = fused_C(pe.fft.pass[i], resident);
+    A.fwd_in[i] = bufs[cur];
+    A.fwd_out[i] = bufs[cur ^ 1];
+    cur ^= 1;
+    smem = std::max(smem, pass_smem(pe.fft.pass[i], A.fwd[i].C));
+  }
+  A.Zu = bufs[cur];
+  A.Zv = square ? bufs[cur] : bufs[cur] + M;
+  A.Q = bufs[cur ^ 1];
+  A.M = M;
+  A.tc = pe.tw + pe.twc_off;
+  A.two_over_N = 2.0 / double(N);
+  cur ^= 1;
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    A.inv[i] = pass_args(pe, i, 0);
+    A.inv[i].C = A.fwd[i].C;
+    A.inv_in[i] = bufs[cur];
+    A.inv_out[i] = bufs[cur ^ 1];
+    cur ^= 1;
+  }
+  double2* wbuf = bufs[cur];
+  long long* cbuf = reinterpret_cast<long long*>(bufs[cur ^ 1]);
+  BackArgs& ba = A.ba;
+  ba.w = reinterpret_cast<const double*>(wbuf);
+  ba.N = N;
+  ba.b = p.b;
+  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
+  ba.tab = pe.bwd_tab;
+  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  ba.kappa = pe.small;
+  ba.nkappa = pe.nkappa;
+  ba.theta = theta;
+  ba.rho = p.rho;
+  ba.c = cbuf;
+  ba.count = kind == TM_HI ? N + 1 : N;
+  ba.emax_fx = emax_fixed(p.limit > 0.0 ? p.limit : p.e_max);
+  ba.status = ws.status;
+  A.back_small = kind != TM_FULL && (N <= 64 || N < 2 * ba.lam + ba.nkappa + 2) ? 1 : 0;
+  int64_t nS, shift, rbit;
+  carry_shape(p, &nS, &shift, &rbit);
+  char* scratch = reinterpret_cast<char*>(wbuf);
+  CarryArgs& ca = A.ca;
+  ca.c = cbuf;
+  ca.K = kind == TM_HI ? N + 1 : N;
+  ca.b = p.b;
+  ca.kind = kind;
+  ca.nS = nS;
+  ca.round_bit = rbit;
+  ca.shift_bits = shift;
+  ca.nout = out_limbs(kind, n);
+  ca.top_mask = (kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+  ca.out = reinterpret_cast<unsigned long long*>(out);
+  ca.r = reinterpret_cast<unsigned long long*>(scratch);
+  ca.fblock = reinterpret_cast<unsigned char*>(scratch + align_up(size_t(2) * nS * 8));
+  ca.cin_block = ca.fblock + align_up(size_t(nS / 512 + 2));
+  A.sync = sync;
+  A.status = ws.status;
+  A.leave_barrier = fault_leave_barrier() ? 1 : 0;
+  // grid: the widest phase, at most what stays resident
+  int64_t want = (N + 1023) / 1024;
+  for (int i = 0; i < pe.fft.npass; ++i) {
+    const int64_t C = A.fwd[i].C;
+    want = std::max<int64_t>(want, ((pe.fft.pass[i].Q + C - 1) / C) * (square ? 1 : 2));
+  }
+  want = std::max<int64_t>(want, (M / 2 + kFusedThreads) / kFusedThreads);
+  want = std::max<int64_t>(want, (nS + 511) / 512);
+  const int grid = int(std::min<int64_t>(want, resident));
+  if (!ws.sync_ready) {               // the barrier words restore themselves after use
+    TM_CHECK(cudaMemsetAsync(sync, 0, 8, s));
+    ws.sync_ready = true;
+  }
+  TM_CHECK(launch_fused(kind, A, grid, smem, s));
+  return TM_OK;
+}
+
 int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
             cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
             int64_t* coeff_out, void* const* events, const KeptOperand* kept) {
   NvtxRange product(kKindNames[kind]);
+  if (!events && !coeff_out && !kept && use_fused(pe)) {
+    ensure_kernel_attributes();
+    return enqueue_fused(kind, out, u, v, n, s, p, pe, ws);
+  }
   bool phase_open = false;
   auto mark = [&](int i) {
     if (events) cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s);
@@ -677,6 +857,7 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
   fill_plan_report(p, pe->fft, rep);
   rep->table_bytes = pe->table_bytes;
   rc = read_status(s, ws->status, rep);
+  if (rc == TM_ETIMEOUT) ws->sync_ready = false;   // barrier words left mid-count
   if (rc == TM_OK && !certified) {
     rc = TM_UNCERTIFIED;
     rep->status = rc;
@@ -692,6 +873,13 @@ int run(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
+// the plan whose tables the array holds, per device
+struct StaticTables {
+  bool valid;
+  int kind, b;
+  int64_t N;
+};
+StaticTables g_static_last[kMaxDevices] = {};
 
 }  // namespace
 }  // namespace tmul
@@ -756,9 +944,18 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   ws->base = base + ws_off;
   ws->size = ws_bytes;
   ws->status = reinterpret_cast<DevStatus*>(base + status_off);
-  // the previous call's contents stay in the array: clear the status word and
-  // rebuild every table this call reads
+  // the previous call's contents stay in the array: clear the status word, and
+  // rebuild the tables unless the previous call on this device built the same plan
+  // (the tables and their offsets depend only on kind, b and N)
   TM_CHECK(cudaMemsetAsync(ws->status, 0, sizeof(DevStatus), s));
+  int dev = 0;
+  TM_CHECK(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticTables& last = g_static_last[dev];
+    if (last.valid && last.kind == kind && last.b == b && last.N == N) return TM_OK;
+    last.valid = false;
+  }
   init_twiddles(*e, s);
   if (rf > 0)
     launch_init_maptab_fx(e->fwd_tab, kind == TM_LO ? kTabAlpha : kTabGamma, N, b, rf, fx_q(b), s);
@@ -769,6 +966,9 @@ int static_plan(int kind, char* base, cudaStream_t s, PlanEntry* e, Workspace* w
   // kappa and rho^-j computed on the device: no host-to-device copy, so a call
   // without a report enqueues only kernels and one memset
   if (kind == TM_HI) launch_init_rho_powers(e->small, nkappa, ntheta, b, std::log(e->p.rho), s);
+  TM_CHECK(cudaGetLastError());
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  g_static_last[dev] = StaticTables{true, kind, b, N};
   return TM_OK;
 }
 
@@ -1476,6 +1676,12 @@ int tm_release(void) {
   return TM_OK;
 }
 
+int tm_set_fused(int mode) {
+  if (mode < 0 || mode > 2) return TM_EINVAL;
+  tmul::g_fused_mode.store(mode);
+  return TM_OK;
+}
+
 int tm_convolution(double* out, const double* x, const double* y, int64_t N, void* stream,
                    double* eta) {
   using namespace tmul;
@@ -1537,7 +1743,7 @@ const char* tm_strerror(int code) {
     case TM_EINVAL: return "invalid argument";
     case TM_ENOMEM: return "out of memory";
     case TM_EPRECISION: return "rounding margin above the error bound: result not trusted";
-    case TM_ETIMEOUT: return "device-side wait timed out (reserved)";
+    case TM_ETIMEOUT: return "a bounded device-side wait timed out";
     case TM_ECUDA: return "CUDA runtime error";
     case TM_ERANGE: return "operand size outside the supported range";
     case TM_EALIAS: return "output overlaps an input";

@@ -1,5 +1,6 @@
 // Batched products: plan groups, one workspace per group, one CUDA graph.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -17,6 +18,10 @@ namespace tmul {
 namespace {
 
 constexpr int kBranches = 12;  // concurrent graph branches
+// steps by which half of a persistent batch's work starts later (mixing one half's
+// FFT passes with the other half's maps and carries in each step); measured on the
+// 4096-product batch, a stagger of 5 steps gave the same time as none
+constexpr int kBatchStagger = 0;
 
 #define TB_CHECK(x)                                    \
   do {                                                 \
@@ -62,6 +67,12 @@ struct tm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double e_max_min = 1.0;
+  // one persistent launch (k_batch_persistent) in place of the per-phase graph
+  bool persistent = false;
+  tmul::BatchArgs pargs{};
+  int pgrid = 0;
+  size_t psmem = 0;
+  bool sync_stale = false;       // a barrier wait timed out: zero the words first
 };
 
 namespace tmul {
@@ -199,6 +210,107 @@ void destroy(tm_batch* B) {
   delete B;
 }
 
+// ------------------------------------------------ the batch as one persistent launch
+
+// Virtual blocks of every phase of group g (the counts k_batch_persistent walks).
+void phase_units(const BatchGroup& G, long long* units) {
+  const long long cnt = G.cnt;
+  for (int ph = 0; ph < kBatchPhases; ++ph) units[ph] = 0;
+  units[kPhFwdMap] = (G.fa.N + kFwdTile - 1) / kFwdTile * cnt;
+  for (int i = 0; i < G.npass; ++i) {
+    const long long bx = (G.fwd[i].Q + G.fwd[i].C - 1) / G.fwd[i].C;
+    units[kPhFwdPass + i] = bx * 2 * cnt;
+    units[kPhInvPass + i] = bx * cnt;
+  }
+  units[kPhTwist] = (G.M / 2 + kFusedThreads) / kFusedThreads * cnt;
+  if (G.kind == TM_FULL) units[kPhBack] = G.back_nvb * cnt;
+  else if (G.back_small) units[kPhBack] = cnt;
+  else units[kPhBack] = (G.ba.N + kBackTile - 1) / kBackTile * cnt;
+  units[kPhCarryLocal] = G.ca.nblocks_max * cnt;
+  units[kPhCarryBlocks] = cnt;
+  units[kPhCarryApply] = G.ca.nblocks_max * cnt;
+}
+
+// The arguments of every phase of one group, on the group's buffers and items (the
+// same layout as enqueue_group).
+BatchGroup batch_group(tm_batch* B, const Group& g, size_t* smem) {
+  const PlanParams& p = g.p;
+  const PlanEntry& pe = *g.pe;
+  const int kind = p.kind;
+  const int64_t N = p.N, M = pe.M;
+  const int cnt = int(g.members.size());
+  char* base = B->mem + g.off;
+  const size_t slab = size_t(cnt) * 2 * M * sizeof(double2);
+  double2* R0 = reinterpret_cast<double2*>(base);
+  double2* R1 = reinterpret_cast<double2*>(base + align_up(slab));
+  char* items = base + 2 * align_up(slab);
+  FwdItem* fi = reinterpret_cast<FwdItem*>(items);
+  BackItem* bi = reinterpret_cast<BackItem*>(items + align_up(cnt * sizeof(FwdItem)));
+  CarryItem* ci = reinterpret_cast<CarryItem*>(reinterpret_cast<char*>(bi) +
+                                               align_up(cnt * sizeof(BackItem)));
+  BatchGroup G{};
+  G.kind = kind;
+  G.npass = pe.fft.npass;
+  G.cnt = cnt;
+  FwdArgs& fa = G.fa;
+  fa.items = fi;
+  fa.b = p.b;
+  fa.N = N;
+  fa.lam = kind == TM_FULL ? 0 : p.lam_fwd;
+  fa.tab = pe.fwd_tab;
+  fa.kappa = pe.small;
+  fa.nkappa = pe.nkappa;
+  fa.rho_pow = pe.small ? pe.small + pe.nkappa : nullptr;
+  fa.ntheta = pe.ntheta;
+  double2* bufs[2] = {R0, R1};
+  int cur = 0;
+  for (int i = 0; i < G.npass; ++i) {
+    const FftPass& fp = pe.fft.pass[i];
+    // sequences per CTA: as many points as the CTA's threads hold radix-4 butterflies
+    const int C = int(std::max<int64_t>(1, std::min<int64_t>(4 * kFusedThreads / fp.L, fp.Q)));
+    G.fwd[i] = pass_args(pe, i, M);
+    G.fwd[i].C = C;
+    G.fwd_in[i] = bufs[cur];
+    G.fwd_out[i] = bufs[cur ^ 1];
+    cur ^= 1;
+    *smem = std::max(*smem, pass_smem(fp, C));
+  }
+  G.Zu = bufs[cur];
+  G.Q = bufs[cur ^ 1];
+  G.M = M;
+  G.tc = pe.tw + pe.twc_off;
+  G.two_over_N = 2.0 / double(N);
+  cur ^= 1;
+  for (int i = 0; i < G.npass; ++i) {
+    G.inv[i] = pass_args(pe, i, 2 * M);
+    G.inv[i].C = G.fwd[i].C;
+    G.inv_in[i] = bufs[cur];
+    G.inv_out[i] = bufs[cur ^ 1];
+    cur ^= 1;
+  }
+  BackArgs& ba = G.ba;
+  ba.items = bi;
+  ba.N = N;
+  ba.b = p.b;
+  ba.lam = kind == TM_FULL ? 0 : p.lam_bwd;
+  ba.tab = pe.bwd_tab;
+  ba.tab2 = kind == TM_HI ? pe.bwd_tab2 : pe.bwd_tab;
+  ba.kappa = pe.small;
+  ba.nkappa = pe.nkappa;
+  ba.rho = p.rho;
+  ba.count = kind == TM_HI ? N + 1 : N;
+  ba.status = B->status;
+  G.back_small = kind != TM_FULL && (N <= 64 || N < 2 * ba.lam + ba.nkappa + 2) ? 1 : 0;
+  G.back_nvb = std::min<long long>((ba.count + kFusedThreads - 1) / kFusedThreads, 152 * 8);
+  CarryArgs& ca = G.ca;
+  ca.items = ci;
+  ca.nblocks_max = g.nblocks_max;
+  ca.K = kind == TM_HI ? N + 1 : N;
+  ca.b = p.b;
+  ca.kind = kind;
+  return G;
+}
+
 }  // namespace
 
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
@@ -253,12 +365,115 @@ SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
   return it;
 }
 
+// The persistent form: every group's phase arguments and the phase tables in device
+// memory, then one cooperative launch recorded as a one-node graph (a direct launch
+// per tm_batch_launch when the runtime cannot record it).
+int create_persistent(tm_batch* B, size_t groups_off, size_t start_off, size_t sync_off,
+                      cudaStream_t s) {
+  const int ng = int(B->groups.size());
+  std::vector<BatchGroup> gs(ng);
+  std::vector<std::array<long long, kBatchPhases>> units(ng);
+  size_t smem = 0;
+  std::vector<std::pair<double, int>> order(ng);
+  for (int g = 0; g < ng; ++g) {
+    gs[g] = batch_group(B, B->groups[g], &smem);
+    phase_units(gs[g], units[g].data());
+    const double N = double(B->groups[g].p.N);
+    order[g] = {double(B->groups[g].members.size()) * N * (std::log2(N) + 8.0), g};
+  }
+  // stagger: half of the estimated work starts kBatchStagger steps later, so that
+  // each step mixes one half's FFT passes with the other half's maps and carries
+  std::sort(order.rbegin(), order.rend());
+  std::vector<int> off(ng, 0);
+  double w0 = 0, w1 = 0;
+  for (const auto& o : order) {
+    if (w1 < w0) { off[o.second] = kBatchStagger; w1 += o.first; }
+    else w0 += o.first;
+  }
+  const int nsteps = kBatchPhases + kBatchStagger;
+  std::vector<int> step_seg(nsteps + 1, 0), seg_group, seg_phase;
+  std::vector<long long> seg_start(1, 0);
+  long long widest = 1;
+  for (int st = 0; st < nsteps; ++st) {
+    step_seg[st] = int(seg_group.size());
+    long long in_step = 0;
+    for (int g = 0; g < ng; ++g) {
+      const int ph = st - off[g];
+      if (ph < 0 || ph >= kBatchPhases || units[g][ph] == 0) continue;
+      seg_group.push_back(g);
+      seg_phase.push_back(ph);
+      seg_start.push_back(seg_start.back() + units[g][ph]);
+      in_step += units[g][ph];
+    }
+    widest = std::max(widest, in_step);
+  }
+  step_seg[nsteps] = int(seg_group.size());
+  const size_t nseg = seg_group.size();
+  // device copies: groups, then the step and segment tables
+  BatchGroup* dg = reinterpret_cast<BatchGroup*>(B->mem + groups_off);
+  char* tab = B->mem + start_off;
+  int* d_step = reinterpret_cast<int*>(tab);
+  long long* d_start = reinterpret_cast<long long*>(tab + align_up((nsteps + 1) * sizeof(int)));
+  int* d_group = reinterpret_cast<int*>(reinterpret_cast<char*>(d_start) +
+                                        align_up((nseg + 1) * sizeof(long long)));
+  int* d_phase = reinterpret_cast<int*>(reinterpret_cast<char*>(d_group) +
+                                        align_up(nseg * sizeof(int) + 4));
+  unsigned* sync = reinterpret_cast<unsigned*>(B->mem + sync_off);
+  if (ng) TB_CHECK(cudaMemcpyAsync(dg, gs.data(), ng * sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
+  TB_CHECK(cudaMemcpyAsync(d_step, step_seg.data(), step_seg.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, s));
+  TB_CHECK(cudaMemcpyAsync(d_start, seg_start.data(), seg_start.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice, s));
+  if (nseg) {
+    TB_CHECK(cudaMemcpyAsync(d_group, seg_group.data(), nseg * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
+    TB_CHECK(cudaMemcpyAsync(d_phase, seg_phase.data(), nseg * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
+  }
+  TB_CHECK(cudaMemsetAsync(sync, 0, 8, s));
+  TB_CHECK(cudaStreamSynchronize(s));
+  const int resident = batch_max_blocks(smem);
+  if (resident <= 0) return TM_ECUDA;
+  B->pargs.groups = dg;
+  B->pargs.ngroups = ng;
+  B->pargs.nsteps = nsteps;
+  B->pargs.step_seg = d_step;
+  B->pargs.seg_start = d_start;
+  B->pargs.seg_group = d_group;
+  B->pargs.seg_phase = d_phase;
+  B->pargs.sync = sync;
+  B->pargs.status = B->status;
+  B->pargs.leave_barrier = fault_leave_barrier() ? 1 : 0;
+  B->pgrid = int(std::min<long long>(widest, resident));
+  B->psmem = smem;
+  if (ng == 0) return TM_OK;
+  cudaStream_t cs;
+  TB_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    const cudaError_t le = launch_batch_persistent(B->pargs, B->pgrid, B->psmem, cs);
+    ce = cudaStreamEndCapture(cs, &B->graph);
+    if (le == cudaSuccess && ce == cudaSuccess) ce = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    else if (ce == cudaSuccess) ce = le;
+  }
+  cudaStreamDestroy(cs);
+  if (ce != cudaSuccess) {            // launch directly instead
+    (void)cudaGetLastError();
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+  }
+  return TM_OK;
+}
+
 int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s) {
   if (!out || (!descs && count)) return TM_EINVAL;
   std::unique_ptr<tm_batch, void (*)(tm_batch*)> B(new tm_batch(), destroy);
   TB_CHECK(cudaGetDevice(&B->dev));
   B->descs.assign(descs, descs + count);
   B->params.resize(count);
+  B->persistent = g_fused_mode.load() == 2;
   std::map<std::tuple<int, int, int64_t>, size_t> index;
   for (uint32_t i = 0; i < count; ++i) {
     const tm_desc& d = B->descs[i];
@@ -271,7 +486,7 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
     if (rc) return rc;
     const PlanParams& q = B->params[i];
     B->e_max_min = std::min(B->e_max_min, q.e_max);
-    if (q.N / 2 <= kSmallMaxM) {          // CTA-resident
+    if (!B->persistent && q.N / 2 <= kSmallMaxM) {   // CTA-resident
       B->small.push_back(i);
       continue;
     }
@@ -324,6 +539,14 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
     g.bytes = group_bytes(g);
     total += align_up(g.bytes);
   }
+  const size_t ng = B->groups.size();
+  const size_t pgroups_off = total;
+  const size_t pstart_off = pgroups_off + align_up(ng * sizeof(BatchGroup));
+  const size_t nseg_max = size_t(kBatchPhases) * ng;
+  const size_t psync_off = pstart_off + align_up((kBatchPhases + kBatchStagger + 1) * sizeof(int)) +
+                           align_up((nseg_max + 1) * sizeof(long long)) +
+                           2 * align_up(nseg_max * sizeof(int) + 4);
+  if (B->persistent) total = psync_off + 256;
   TB_CHECK(cudaMalloc(&B->mem, total));
   B->status = reinterpret_cast<DevStatus*>(B->mem);
   TB_CHECK(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), s));
@@ -353,6 +576,15 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
     TB_CHECK(cudaStreamSynchronize(s));
   }
   ensure_kernel_attributes();
+  for (const Group& g : B->groups)         // one radix-4 butterfly per thread at most
+    for (int i = 0; i < g.pe->fft.npass; ++i)
+      if (g.pe->fft.pass[i].L > 4 * kFusedThreads) B->persistent = false;
+  if (B->persistent) {
+    const int rc = create_persistent(B.get(), pgroups_off, pstart_off, psync_off, s);
+    if (rc) return rc;
+    *out = B.release();
+    return TM_OK;
+  }
   // record the graph: groups spread over kBranches forked capture streams
   cudaStream_t cs[kBranches];
   cudaEvent_t fork, join[kBranches];
@@ -419,8 +651,27 @@ int tm_batch_create(tm_batch** batch, const tm_desc* descs, uint32_t count, void
 
 int tm_batch_launch(tm_batch* batch, void* stream) {
   if (!batch) return TM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (batch->persistent) {
+    if (batch->pargs.ngroups == 0) return TM_OK;
+    if (batch->sync_stale) {
+      if (cudaMemsetAsync(batch->pargs.sync, 0, 8, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TM_ECUDA;
+      }
+      batch->sync_stale = false;
+    }
+    const cudaError_t e = batch->exec ? cudaGraphLaunch(batch->exec, s)
+                                      : tmul::launch_batch_persistent(batch->pargs, batch->pgrid,
+                                                                      batch->psmem, s);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return TM_ECUDA;
+    }
+    return TM_OK;
+  }
   if (!batch->exec) return TM_OK;
-  const cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGraphLaunch(batch->exec, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return TM_ECUDA;
@@ -432,6 +683,7 @@ int tm_batch_status(tm_batch* batch, void* stream, tm_report* rep) {
   if (!batch) return TM_EINVAL;
   const int rc = tmul::read_status(static_cast<cudaStream_t>(stream), batch->status, rep);
   if (rep) rep->e_max = batch->e_max_min;
+  if (rc == TM_ETIMEOUT) batch->sync_stale = true;
   return rc;
 }
 

@@ -190,47 +190,111 @@ __device__ void dd_cossin_2pi(long long m, long long len, DD* cs, DD* sn) {
   }
 }
 
+// The table kernels take runs of kTwRun consecutive entries per thread: the run's
+// first angle from the Taylor series, the others by rotation with the one-step
+// twiddle (double-double complex products; after a run the error stays below
+// 2^-95, far below the rounding to double). Entries whose cosine or sine is
+// exactly 0 or +-1 (4m a multiple of len) take the exact values.
+constexpr int kTwRun = 16;
+constexpr int kTwThreads = 64;
+
+// (c + i s) <- (c + i s)(c1 + i s1)
+__device__ __forceinline__ void dd_rotate(DD& c, DD& s, const DD c1, const DD s1) {
+  const DD cc = dd_add(dd_mul(c, c1), dd_neg(dd_mul(s, s1)));
+  const DD ss = dd_add(dd_mul(s, c1), dd_mul(c, s1));
+  c = cc;
+  s = ss;
+}
+
+__device__ __forceinline__ void dd_exact_axes(long long m, long long len, DD* c, DD* s) {
+  if ((4 * m) % len == 0) {
+    const int q = int(((4 * m) / len) & 3);
+    *c = DD{q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0), 0.0};
+    *s = DD{q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0), 0.0};
+  }
+}
+
+// cos and sin of 2 pi / len for the whole block (thread 0 computes, all read)
+__device__ void dd_block_step(long long step, long long len, DD* c1, DD* s1) {
+  __shared__ DD sc, ss;
+  if (threadIdx.x == 0) dd_cossin_2pi(step, len, &sc, &ss);
+  __syncthreads();
+  *c1 = sc;
+  *s1 = ss;
+}
+
 // tab[m] = exp(-2 pi i m / len), m < count, each component rounded once.
-__global__ void k_init_twiddles(double2* tab, long long len, long long count) {
-  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (m >= count) return;
-  DD cs, sn;
-  dd_cossin_2pi(m, len, &cs, &sn);
-  tab[m] = make_double2(cs.hi, -sn.hi);
+__global__ void __launch_bounds__(kTwThreads) k_init_twiddles(double2* tab, long long len,
+                                                                long long count) {
+  DD c1, s1;
+  dd_block_step(1, len, &c1, &s1);
+  const long long m0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kTwRun;
+  if (m0 >= count) return;
+  DD c, s;
+  dd_cossin_2pi(m0, len, &c, &s);
+  for (int i = 0; i < kTwRun && m0 + i < count; ++i) {
+    if (i) dd_rotate(c, s, c1, s1);
+    DD cc = c, ss = s;
+    dd_exact_axes(m0 + i, len, &cc, &ss);
+    tab[m0 + i] = make_double2(cc.hi, -ss.hi);
+  }
 }
 
 // tab[k] = (1 + w^2) / (2N) = cos(2 pi k / N) w / N, w = exp(-2 pi i k / N), k < count:
 // the one twiddle of the fused real-FFT twist (see twist_pair), each component
 // rounded once.
-__global__ void k_init_twist_coef(double2* tab, long long N, long long count) {
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  DD cs, sn;
-  dd_cossin_2pi(k, N, &cs, &sn);
-  const DD re = dd_div_d(dd_mul(cs, cs), double(N));
-  const DD im = dd_div_d(dd_mul(cs, sn), double(N));
-  tab[k] = make_double2(re.hi, -im.hi);
+__global__ void __launch_bounds__(kTwThreads) k_init_twist_coef(double2* tab, long long N,
+                                                                  long long count) {
+  DD c1, s1;
+  dd_block_step(1, N, &c1, &s1);
+  const long long k0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kTwRun;
+  if (k0 >= count) return;
+  DD c, s;
+  dd_cossin_2pi(k0, N, &c, &s);
+  for (int i = 0; i < kTwRun && k0 + i < count; ++i) {
+    if (i) dd_rotate(c, s, c1, s1);
+    DD cs = c, sn = s;
+    dd_exact_axes(k0 + i, N, &cs, &sn);
+    const DD re = dd_div_d(dd_mul(cs, cs), double(N));
+    const DD im = dd_div_d(dd_mul(cs, sn), double(N));
+    tab[k0 + i] = make_double2(re.hi, -im.hi);
+  }
 }
 
 // Tangent-form twiddles of a radix-4 stage (see launch_init_tw4). The cosine c is
 // rounded first and the tangent is taken as the double nearest to sin / c (with
 // the rounded c), so the twiddle c (1 - i t) the butterfly applies is within
 // 2^-53 (1 + 2^-40) of exp(-i theta), as for a rounded (cos, sin) pair.
-__global__ void k_init_tw4(Tan4* tab, int Ns) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Ns) return;
+__global__ void __launch_bounds__(kTwThreads) k_init_tw4(Tan4* tab, int Ns) {
   const long long len = 4LL * Ns;
+  DD a1, b1, a2, b2;                                  // steps of theta and of 2 theta
+  dd_block_step(1, len, &a1, &b1);
+  __syncthreads();
+  dd_block_step(2, len, &a2, &b2);
+  const long long k0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kTwRun;
+  if (k0 >= Ns) return;
   DD c1, s1, c2, s2;
-  dd_cossin_2pi(k, len, &c1, &s1);                   // theta = 2 pi k / (4 Ns) < pi/2
-  const bool rot = 2 * k >= Ns;
-  dd_cossin_2pi(rot ? 2LL * k - Ns : 2LL * k, len, &c2, &s2);   // 2 theta, or 2 theta - pi/2
-  Tan4 e;
-  e.c1 = c1.hi;
-  e.t1 = dd_div_d(s1, e.c1).hi;
-  const double cr2 = c2.hi;
-  e.t2 = dd_div_d(s2, cr2).hi;
-  e.c2s = rot ? -cr2 : cr2;
-  tab[k] = e;
+  dd_cossin_2pi(k0, len, &c1, &s1);                   // theta = 2 pi k / (4 Ns) < pi/2
+  dd_cossin_2pi(2 * k0, len, &c2, &s2);               // 2 theta
+  for (int i = 0; i < kTwRun && k0 + i < Ns; ++i) {
+    const long long k = k0 + i;
+    if (i) {
+      dd_rotate(c1, s1, a1, b1);
+      dd_rotate(c2, s2, a2, b2);
+    }
+    DD x1 = c1, y1 = s1, x2 = c2, y2 = s2;
+    dd_exact_axes(k, len, &x1, &y1);
+    dd_exact_axes(2 * k, len, &x2, &y2);
+    const bool rot = 2 * k >= Ns;                     // 2 theta >= pi/2: use 2 theta - pi/2
+    const DD cw = rot ? y2 : x2;                      // cos(2 theta - pi/2) = sin 2 theta
+    const DD sw = rot ? dd_neg(x2) : y2;              // sin(2 theta - pi/2) = -cos 2 theta
+    Tan4 e;
+    e.c1 = x1.hi;
+    e.t1 = dd_div_d(y1, e.c1).hi;
+    e.t2 = dd_div_d(sw, cw.hi).hi;
+    e.c2s = rot ? -cw.hi : cw.hi;
+    tab[k] = e;
+  }
 }
 
 // Coefficient rows of the ring maps (Sections 3.2 and 4.2), tab[(r-1) N + k]:
@@ -408,7 +472,6 @@ void launch_digit_norms(const unsigned long long* u, const unsigned long long* v
     default: launch_pdl(KERNEL<0>, TM_UNPAREN CFG, TM_UNPAREN ARGS); break;          \
   }
 
-constexpr int kFwdTile = 1024;
 constexpr int kFwdThreads = 256;
 constexpr int kMaxLam = 24;
 constexpr int kMaxB = 24;
@@ -487,20 +550,40 @@ __device__ void fill_digits(int* d, const unsigned long long* st, DigitStage g,
 // S_j = U_j 2^Q + sum_r (A_{k,r} U_k) >> rb is exact up to the table rounding and
 // the shifts, |S_j| < 2^61, and U~_j = S_j 2^-Q after one rounding conversion.
 // Full product (lam = 0): X_j = U_j for j < nd, 0 for nd <= j < N (Algorithm 1, split step).
+// Shared memory of one forward-map block (one instance per kernel: the bodies are
+// also run inside the single-launch kernels, where one union serves every phase).
+struct FwdLoShared {
+  int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  unsigned long long stu[kStageLimbs], stv[kStageLimbs];
+};
+struct FwdHiShared {
+  int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
+  double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
+  unsigned long long stu[kStageLimbs], stv[kStageLimbs];
+  double topu, topv;
+};
+union FwdShared {
+  FwdLoShared lo;
+  FwdHiShared hi;
+};
+
 template <int ROWS>
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kind) {
+__device__ __forceinline__ void fwd_lo_full_body(FwdArgs a0, int kind, const uint3 bid, const uint3 gdim,
+                                                 FwdLoShared& sh) {
   FwdArgs a = a0;
   if (a0.items) {
-    const FwdItem it = a0.items[blockIdx.y];
+    const FwdItem it = a0.items[bid.y];
     a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
     a.X = it.X; a.theta = it.theta;
   }
   pdl_trigger();
   pdl_wait();
-  __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
-  __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
+  int* du = sh.du;
+  int* dv = sh.dv;
+  unsigned long long* stu = sh.stu;
+  unsigned long long* stv = sh.stv;
   const bool two = !a.one_operand;
-  const long long j0 = (long long)blockIdx.x * kFwdTile;
+  const long long j0 = (long long)bid.x * kFwdTile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
   const int span = kFwdTile + halo;
   const long long limit = a.N < a.nd ? a.N : a.nd;
@@ -556,6 +639,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kin
   }
 }
 
+template <int ROWS>
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_lo_full(FwdArgs a0, int kind) {
+  __shared__ FwdLoShared sh;
+  fwd_lo_full_body<ROWS>(a0, kind, blockIdx, gridDim, sh);
+}
+
 // High product: gamma-dagger (Algorithm 3, convert step; Proposition 4.18).
 // F' = F mod C: F'_i = F_i + kappa_i F_N (eq. 4.5), then
 // U~_j = sum_{r<lam} gamma_{(j-r) mod N, r} F'_{(j-r) mod N}, and
@@ -569,25 +658,30 @@ __device__ __forceinline__ double fx_coef(const long long* tab, long long N, int
 }
 
 template <int ROWS>
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
+__device__ __forceinline__ void fwd_hi_body(FwdArgs a0, const uint3 bid, const uint3 gdim,
+                                            FwdHiShared& sh) {
   FwdArgs a = a0;
   if (a0.items) {
-    const FwdItem it = a0.items[blockIdx.y];
+    const FwdItem it = a0.items[bid.y];
     a.u = it.u; a.v = it.v; a.n = it.n; a.nlimbs = it.nlimbs; a.nd = it.nd; a.s0 = it.s0;
     a.X = it.X; a.theta = it.theta;
   }
   pdl_trigger();
   pdl_wait();
-  __shared__ int du[kFwdTile + kMaxLam], dv[kFwdTile + kMaxLam];
-  __shared__ double fu[kFwdTile + kMaxLam], fv[kFwdTile + kMaxLam];
-  __shared__ unsigned long long stu[kStageLimbs], stv[kStageLimbs];
-  __shared__ double topu, topv;
+  int* du = sh.du;
+  int* dv = sh.dv;
+  double* fu = sh.fu;
+  double* fv = sh.fv;
+  unsigned long long* stu = sh.stu;
+  unsigned long long* stv = sh.stv;
+  double& topu = sh.topu;
+  double& topv = sh.topv;
   const bool two = !a.one_operand;
-  const long long j0 = (long long)blockIdx.x * kFwdTile;
+  const long long j0 = (long long)bid.x * kFwdTile;
   const int halo = a.lam - 1;
   const int span = kFwdTile + halo;
   const long long N = a.N;
-  const bool head = blockIdx.x == 0;
+  const bool head = bid.x == 0;
   const int Q = fx_q(a.b);
   if (threadIdx.x == 0) {
     topu = i2d_exact(balanced_digit(a.u, a.nlimbs, a.n, a.s0, a.b, N, N, true));
@@ -672,6 +766,12 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
     a.theta[threadIdx.x == 0 ? 0 : 1] = th;
     if (!two && a.square_theta && threadIdx.x == 0) a.theta[1] = th;
   }
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
+  __shared__ FwdHiShared sh;
+  fwd_hi_body<ROWS>(a0, blockIdx, gridDim, sh);
 }
 
 void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s) {
@@ -907,7 +1007,7 @@ __device__ __forceinline__ void stockham_stage4t(double2* buf, int L, int C, int
 }
 
 template <int S>
-__global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p) {
+__device__ __forceinline__ void fft_pass_body(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p, const uint3 bid, const uint3 gdim) {
   extern __shared__ double2 smem[];
   const int L = p.L, C = p.C;
   double2* buf = smem;
@@ -919,8 +1019,8 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   if (p.need_wL)
     for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = __ldg(p.tw_sub + t);
   pdl_wait();                       // the plan's tables above; the data below
-  const long long q0 = (long long)blockIdx.x * C;
-  const long long boff = (long long)blockIdx.y * p.batch_stride;
+  const long long q0 = (long long)bid.x * C;
+  const long long boff = (long long)bid.y * p.batch_stride;
   in += boff;
   out += boff;
   const int CL = C * L;
@@ -971,6 +1071,11 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   }
 }
 
+template <int S>
+__global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p) {
+  fft_pass_body<S>(in, out, p, blockIdx, gridDim);
+}
+
 void set_small_smem_attribute(int bytes);
 
 // Shared memory above 48 KB per CTA needs the opt-in; set once before any launch
@@ -982,6 +1087,7 @@ void set_fft_smem_attribute() {
   cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   set_small_smem_attribute(optin);
+  set_fused_smem_attribute(optin);
 }
 
 void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p, int batch,
@@ -1036,16 +1142,24 @@ __device__ __forceinline__ void twist_pair(const double2* Zu, const double2* Zv,
 }
 
 template <bool SQ>
+__device__ __forceinline__ void twist_body(const double2* __restrict__ Zu, const double2* __restrict__ Zv,
+                        double2* __restrict__ Q, long long M,
+                        const double2* __restrict__ tc, double two_over_N, long long zstride,
+                        long long qstride, const uint3 bid, const uint3 gdim) {
+  pdl_trigger();
+  pdl_wait();
+  const long long k = bid.x * (long long)blockDim.x + threadIdx.x;
+  if (k > M / 2) return;
+  twist_pair<SQ>(Zu + bid.y * zstride, Zv + bid.y * zstride, Q + bid.y * qstride,
+                 M, k, tc, two_over_N);
+}
+
+template <bool SQ>
 __global__ void k_twist(const double2* __restrict__ Zu, const double2* __restrict__ Zv,
                         double2* __restrict__ Q, long long M,
                         const double2* __restrict__ tc, double two_over_N, long long zstride,
                         long long qstride) {
-  pdl_trigger();
-  pdl_wait();
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k > M / 2) return;
-  twist_pair<SQ>(Zu + blockIdx.y * zstride, Zv + blockIdx.y * zstride, Q + blockIdx.y * qstride,
-                 M, k, tc, two_over_N);
+  twist_body<SQ>(Zu, Zv, Q, M, tc, two_over_N, zstride, qstride, blockIdx, gridDim);
 }
 
 void launch_twist(const double2* Zu, const double2* Zv, double2* Q, long long M,
@@ -1096,10 +1210,10 @@ __device__ void back_full_loop(const BackArgs& a, long long start, long long str
   for (long long i = start; i < a.count; i += stride) emit(a, i, a.w[i], false, bmax);
 }
 
-__global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
+__device__ __forceinline__ void back_full_body(BackArgs a0, const uint3 bid, const uint3 gdim) {
   BackArgs a = a0;
   if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
+    const BackItem it = a0.items[bid.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
   pdl_trigger();
@@ -1108,9 +1222,13 @@ __global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
   __shared__ unsigned bflags;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
-  back_full_loop(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                 (long long)gridDim.x * blockDim.x, &bmax);
+  back_full_loop(a, bid.x * (long long)blockDim.x + threadIdx.x,
+                 (long long)gdim.x * blockDim.x, &bmax);
   finish_block(&bmax, &bflags, a);
+}
+
+__global__ void __launch_bounds__(kBackThreads) k_back_full(BackArgs a0) {
+  back_full_body(a0, blockIdx, gridDim);
 }
 
 // Low product (Algorithm 2, convert back and rounding; Proposition 3.16): Wbar = sum_{r<lam} beta*_r W~
@@ -1163,17 +1281,16 @@ __device__ __forceinline__ void block_note_distance(unsigned long long d,
   if ((threadIdx.x & 31) == 0 && d) atomicMax(bmax, d);
 }
 
-constexpr int kBackTile = 1024;
 
 // Tiles of kBackTile coefficients; every thread issues the loads of all map rows
 // and W~ values of an output before the FMAs, unrolled for ROWS = lam - 1 rows
 // (ROWS = 0: any count up to kMaxLam, predicated). Head positions i < lam (block 0)
 // take back_lo_loop's path with the wrapped terms.
 template <int ROWS>
-__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
+__device__ __forceinline__ void back_lo_body(BackArgs a0, const uint3 bid, const uint3 gdim) {
   BackArgs a = a0;
   if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
+    const BackItem it = a0.items[bid.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
   pdl_trigger();
@@ -1181,7 +1298,7 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   const long long N = a.N;
-  const long long i0 = (long long)blockIdx.x * kBackTile;
+  const long long i0 = (long long)bid.x * kBackTile;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
   unsigned long long dmax = 0;
@@ -1211,6 +1328,11 @@ __global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
   }
   block_note_distance(dmax, &bmax);
   finish_block(&bmax, &bflags, a);
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kBackThreads) k_back_lo(BackArgs a0) {
+  back_lo_body<ROWS>(a0, blockIdx, gridDim);
 }
 
 // High product (Algorithm 3, convert back and rounding; Proposition 4.19 with Remark 4.20 for
@@ -1293,10 +1415,10 @@ __device__ void back_hi_head(const BackArgs& a, int lane, double* P, double* Hh,
 // Tiles as in k_back_lo, ROWS = lam rows of delta'. Head positions and J_N are
 // warp 0 of block 0 (back_hi_head).
 template <int ROWS>
-__global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
+__device__ __forceinline__ void back_hi_body(BackArgs a0, const uint3 bid, const uint3 gdim) {
   BackArgs a = a0;
   if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
+    const BackItem it = a0.items[bid.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
   pdl_trigger();
@@ -1306,7 +1428,7 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
   __shared__ double P[kMaxLam];
   __shared__ double Hh[kMaxLam + 64 + 1];
   const long long N = a.N;
-  const long long i0 = (long long)blockIdx.x * kBackTile;
+  const long long i0 = (long long)bid.x * kBackTile;
   const long long head = a.lam + a.nkappa;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
@@ -1333,8 +1455,13 @@ __global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
     dmax = d > dmax ? d : dmax;
   }
   block_note_distance(dmax, &bmax);
-  if (blockIdx.x == 0 && threadIdx.x < 32) back_hi_head(a, threadIdx.x, P, Hh, &bmax, &bflags);
+  if (bid.x == 0 && threadIdx.x < 32) back_hi_head(a, threadIdx.x, P, Hh, &bmax, &bflags);
   finish_block(&bmax, &bflags, a);
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kBackThreads) k_back_hi(BackArgs a0) {
+  back_hi_body<ROWS>(a0, blockIdx, gridDim);
 }
 
 // Small transforms (any N): one thread evaluates the back map from the
@@ -1404,16 +1531,20 @@ __device__ void back_small_body(const BackArgs& a, int kind) {
 }
 
 
-__global__ void k_back_small(BackArgs a0, int kind) {
+__device__ __forceinline__ void back_small_body_k(BackArgs a0, int kind, const uint3 bid, const uint3 gdim) {
   pdl_trigger();
   pdl_wait();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (threadIdx.x != 0 || bid.x != 0) return;
   BackArgs a = a0;
   if (a0.items) {
-    const BackItem it = a0.items[blockIdx.y];
+    const BackItem it = a0.items[bid.y];
     a.w = it.w; a.c = it.c; a.theta = it.theta; a.emax_fx = it.emax_fx;
   }
   back_small_body(a, kind);
+}
+
+__global__ void k_back_small(BackArgs a0, int kind) {
+  back_small_body_k(a0, kind, blockIdx, gridDim);
 }
 
 void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
@@ -1541,10 +1672,10 @@ __device__ void block_fn_scan(unsigned f, unsigned* ex, unsigned* tot) {
 // r_L of every limb and the block's composed carry function. Word 2L of r holds
 // r_L mod 2^64; word 2L+1 holds floor(r_L / 2^64) (-1, 0 or 1) in its low byte and
 // the block-exclusive prefix of carry functions in bits 8..13.
-__global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
+__device__ __forceinline__ void carry_local_body(CarryArgs a0, const uint3 bid, const uint3 gdim) {
   CarryArgs a = a0;
   if (a0.items) {
-    const CarryItem it = a0.items[blockIdx.y];
+    const CarryItem it = a0.items[bid.y];
     a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
@@ -1552,9 +1683,9 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
   pdl_trigger();
   pdl_wait();
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
-  if (blockIdx.x >= my_blocks) return;     // uniform per block
+  if (bid.x >= my_blocks) return;     // uniform per block
   __shared__ long long hs[kCarryThreads];
-  const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
+  const long long L = bid.x * (long long)kCarryThreads + threadIdx.x;
   const __int128 AL = L < a.nS ? limb_sum(a, L) : (__int128)0;
   hs[threadIdx.x] = (long long)(AL >> 64);
   __syncthreads();
@@ -1568,14 +1699,20 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
     a.r[2 * L + 1] = (unsigned long long)((unsigned)(int)(long long)(r >> 64) & 0xFFu) |
                      ((unsigned long long)ex << 8);
   }
-  if (threadIdx.x == 0) a.fblock[blockIdx.x] = (unsigned char)tot;
+  if (threadIdx.x == 0) a.fblock[bid.x] = (unsigned char)tot;
+}
+
+__global__ void __launch_bounds__(kCarryThreads) k_carry_local(CarryArgs a0) {
+  carry_local_body(a0, blockIdx, gridDim);
 }
 
 // carry into every block: cin_0 = 0, cin_(B+1) = F_B(cin_B)
-__global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
+// NT threads scan the blocks' carry functions (one CTA).
+template <int NT>
+__device__ __forceinline__ void carry_blocks_body(CarryArgs a0, const uint3 bid) {
   CarryArgs a = a0;
   if (a0.items) {
-    const CarryItem it = a0.items[blockIdx.y];
+    const CarryItem it = a0.items[bid.y];
     a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
@@ -1583,17 +1720,21 @@ __global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
   pdl_trigger();
   pdl_wait();
   const long long nblocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
-  const long long per = (nblocks + 1023) / 1024;
+  const long long per = (nblocks + NT - 1) / NT;
   const long long b0 = threadIdx.x * per;
   unsigned f = kIdentityFn;
   for (long long i = b0; i < b0 + per && i < nblocks; ++i) f = compose(a.fblock[i], f);
   unsigned ex, tot;
-  block_fn_scan<1024>(f, &ex, &tot);
+  block_fn_scan<NT>(f, &ex, &tot);
   int cin = apply_fn(ex, 0);
   for (long long i = b0; i < b0 + per && i < nblocks; ++i) {
     a.cin_block[i] = (unsigned char)(cin + 1);
     cin = apply_fn(a.fblock[i], cin);
   }
+}
+
+__global__ void __launch_bounds__(1024) k_carry_blocks(CarryArgs a0) {
+  carry_blocks_body<1024>(a0, blockIdx);
 }
 
 // r_L + cin mod 2^64 for limb L (0 beyond the resolved limbs)
@@ -1602,10 +1743,10 @@ __device__ __forceinline__ unsigned long long resolved_lo(const CarryArgs& a, lo
   return L < a.nS ? a.r[2 * L] + (unsigned long long)(long long)cin : 0ull;
 }
 
-__global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
+__device__ __forceinline__ void carry_apply_body(CarryArgs a0, const uint3 bid, const uint3 gdim) {
   CarryArgs a = a0;
   if (a0.items) {
-    const CarryItem it = a0.items[blockIdx.y];
+    const CarryItem it = a0.items[bid.y];
     a.c = it.c; a.nS = it.nS; a.round_bit = it.round_bit; a.shift_bits = it.shift_bits;
     a.nout = it.nout; a.top_mask = it.top_mask; a.out = it.out; a.r = it.r;
     a.fblock = it.fblock; a.cin_block = it.cin_block;
@@ -1613,8 +1754,8 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
   pdl_trigger();
   pdl_wait();
   const long long my_blocks = (a.nS + kCarryThreads - 1) / kCarryThreads;
-  if (blockIdx.x >= my_blocks) return;     // uniform per block
-  const long long L = blockIdx.x * (long long)kCarryThreads + threadIdx.x;
+  if (bid.x >= my_blocks) return;     // uniform per block
+  const long long L = bid.x * (long long)kCarryThreads + threadIdx.x;
   if (L >= a.nS) return;
   const long long sw = a.shift_bits >> 6;
   const int sb = int(a.shift_bits & 63);
@@ -1623,7 +1764,7 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
   const unsigned long long lo = a.r[2 * L], w1 = a.r[2 * L + 1];
   const int hi = (int)(signed char)(w1 & 0xFFu);
   const unsigned pfx = unsigned(w1 >> 8) & 0x3Fu;
-  const int cin = apply_fn(pfx, int(a.cin_block[blockIdx.x]) - 1);
+  const int cin = apply_fn(pfx, int(a.cin_block[bid.x]) - 1);
   unsigned long long o = (lo + (unsigned long long)(long long)cin) >> sb;
   if (sb) {
     // carry out of limb L: floor((r_L + cin) / 2^64)
@@ -1632,6 +1773,10 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
   }
   if (j == a.nout - 1) o &= a.top_mask;
   a.out[j] = o;
+}
+
+__global__ void __launch_bounds__(kCarryThreads) k_carry_apply(CarryArgs a0) {
+  carry_apply_body(a0, blockIdx, gridDim);
 }
 
 __global__ void k_status_publish(DevStatus* status, DevStatus* host) {
@@ -1658,6 +1803,357 @@ void launch_carry(const CarryArgs& a, int batch, cudaStream_t s) {
   launch_pdl(k_carry_apply, grid, dim3(kCarryThreads), 0, s, a);
 }
 
+
+// ------------------------------------------------ single-launch products
+
+// Grid-wide barrier of a cooperative launch (every CTA resident). Thread 0 of
+// each CTA counts itself in and waits for the generation word to move. The wait
+// is bounded by the global nanosecond timer (kBarrierTimeoutNs, one second): on
+// timeout it sets kFlagTimeout in the status word, and every CTA returns at its
+// next barrier instead of waiting on a CTA that has left. Returns false once any
+// CTA timed out. leave = true: this CTA leaves without counting itself in (the
+// host-side fault injection of the single-launch paths).
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(unsigned* sync, DevStatus* status, bool leave = false) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vs = sync;
+    if (leave) {
+      if (gridDim.x == 1) atomicOr(&status->flags, kFlagTimeout);   // nobody else to wait
+    } else {
+      const unsigned gen = vs[1];
+      __threadfence();
+      const unsigned arrived = atomicAdd(sync, 1u) + 1u;
+      if (arrived == gridDim.x) {
+        atomicExch(sync, 0u);                 // ready for the next barrier
+        __threadfence();
+        atomicAdd(sync + 1, 1u);              // release the others
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (vs[1] == gen) {
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicOr(&status->flags, kFlagTimeout);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = !leave && (((volatile unsigned*)&status->flags)[0] & kFlagTimeout) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Every phase of one product in one cooperative launch: forward maps, forward FFT
+// passes, twist, inverse passes, back map and rounding, carry scan, separated by
+// grid barriers. Each phase runs the same block bodies as the per-phase kernels,
+// over its virtual blocks (block v of a phase on CTA v mod grid), so the
+// arithmetic is identical to the multi-kernel path.
+template <int KIND>
+__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_product(FusedArgs A) {
+  __shared__ FwdShared fsh;
+  const unsigned G = gridDim.x;
+  {                                                   // 1. split + convert
+    const unsigned bx = unsigned((A.fa.N + kFwdTile - 1) / kFwdTile);
+    for (unsigned v = blockIdx.x; v < bx; v += G) {
+      if (KIND == TM_HI)
+        fwd_hi_body<0>(A.fa, make_uint3(v, 0, 0), make_uint3(bx, 1, 1), fsh.hi);
+      else
+        fwd_lo_full_body<0>(A.fa, KIND, make_uint3(v, 0, 0), make_uint3(bx, 1, 1), fsh.lo);
+      __syncthreads();
+    }
+  }
+  if (!grid_barrier(A.sync, A.status, A.leave_barrier && blockIdx.x == gridDim.x - 1)) return;
+  const unsigned nb = A.square ? 1u : 2u;
+  for (int i = 0; i < A.npass; ++i) {                 // 2. forward FFTs
+    const PassArgs& p = A.fwd[i];
+    const unsigned bx = unsigned((p.Q + p.C - 1) / p.C);
+    for (unsigned v = blockIdx.x; v < bx * nb; v += G) {
+      fft_pass_body<-1>(A.fwd_in[i], A.fwd_out[i], p, make_uint3(v % bx, v / bx, 0),
+                        make_uint3(bx, nb, 1));
+      __syncthreads();
+    }
+    if (!grid_barrier(A.sync, A.status)) return;
+  }
+  {                                                   // 3. twist + pointwise product
+    const unsigned bx = unsigned((A.M / 2 + kFusedThreads) / kFusedThreads);
+    for (unsigned v = blockIdx.x; v < bx; v += G) {
+      if (A.square)
+        twist_body<true>(A.Zu, A.Zv, A.Q, A.M, A.tc, A.two_over_N, 0, 0, make_uint3(v, 0, 0),
+                         make_uint3(bx, 1, 1));
+      else
+        twist_body<false>(A.Zu, A.Zv, A.Q, A.M, A.tc, A.two_over_N, 0, 0, make_uint3(v, 0, 0),
+                          make_uint3(bx, 1, 1));
+    }
+  }
+  if (!grid_barrier(A.sync, A.status)) return;
+  for (int i = 0; i < A.npass; ++i) {                 // 4. inverse FFT
+    const PassArgs& p = A.inv[i];
+    const unsigned bx = unsigned((p.Q + p.C - 1) / p.C);
+    for (unsigned v = blockIdx.x; v < bx; v += G) {
+      fft_pass_body<1>(A.inv_in[i], A.inv_out[i], p, make_uint3(v, 0, 0), make_uint3(bx, 1, 1));
+      __syncthreads();
+    }
+    if (!grid_barrier(A.sync, A.status)) return;
+  }
+  {                                                   // 5. convert back + round
+    if (KIND == TM_FULL) {
+      long long nvb = (A.ba.count + kFusedThreads - 1) / kFusedThreads;
+      if (nvb > 152 * 8) nvb = 152 * 8;
+      for (unsigned v = blockIdx.x; v < unsigned(nvb); v += G) {
+        back_full_body(A.ba, make_uint3(v, 0, 0), make_uint3(unsigned(nvb), 1, 1));
+        __syncthreads();
+      }
+    } else if (A.back_small) {
+      if (blockIdx.x == 0 && threadIdx.x < 32)
+        back_small_body_k(A.ba, KIND, make_uint3(0, 0, 0), make_uint3(1, 1, 1));
+    } else {
+      const unsigned bx = unsigned((A.ba.N + kBackTile - 1) / kBackTile);
+      for (unsigned v = blockIdx.x; v < bx; v += G) {
+        if (KIND == TM_LO)
+          back_lo_body<0>(A.ba, make_uint3(v, 0, 0), make_uint3(bx, 1, 1));
+        else
+          back_hi_body<0>(A.ba, make_uint3(v, 0, 0), make_uint3(bx, 1, 1));
+        __syncthreads();
+      }
+    }
+  }
+  if (!grid_barrier(A.sync, A.status)) return;
+  const unsigned cb = unsigned((A.ca.nS + kCarryThreads - 1) / kCarryThreads);
+  for (unsigned v = blockIdx.x; v < cb; v += G) {     // 6. overlap-add + carries
+    carry_local_body(A.ca, make_uint3(v, 0, 0), make_uint3(cb, 1, 1));
+    __syncthreads();
+  }
+  if (!grid_barrier(A.sync, A.status)) return;
+  if (blockIdx.x == 0) carry_blocks_body<kFusedThreads>(A.ca, make_uint3(0, 0, 0));
+  if (!grid_barrier(A.sync, A.status)) return;
+  for (unsigned v = blockIdx.x; v < cb; v += G) {
+    carry_apply_body(A.ca, make_uint3(v, 0, 0), make_uint3(cb, 1, 1));
+    __syncthreads();
+  }
+}
+
+// the opt-in limit covers static and dynamic shared memory together
+template <int KIND>
+void set_fused_attribute(int bytes) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_fused_product<KIND>) == cudaSuccess)
+    cudaFuncSetAttribute(k_fused_product<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes - int(fa.sharedSizeBytes));
+  (void)cudaGetLastError();
+}
+
+void set_fused_smem_attribute(int bytes) {
+  set_fused_attribute<TM_FULL>(bytes);
+  set_fused_attribute<TM_LO>(bytes);
+  set_fused_attribute<TM_HI>(bytes);
+}
+
+int fused_max_blocks(int kind, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (kind == TM_HI)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_product<TM_HI>,
+                                                      kFusedThreads, smem);
+  else if (kind == TM_LO)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_product<TM_LO>,
+                                                      kFusedThreads, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_product<TM_FULL>,
+                                                      kFusedThreads, smem);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per * sms;
+}
+
+cudaError_t launch_fused(int kind, const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (kind == TM_HI) return cudaLaunchKernelEx(&cfg, k_fused_product<TM_HI>, a);
+  if (kind == TM_LO) return cudaLaunchKernelEx(&cfg, k_fused_product<TM_LO>, a);
+  return cudaLaunchKernelEx(&cfg, k_fused_product<TM_FULL>, a);
+}
+
+// ------------------------------------------------ persistent batch
+
+// The segment of [a, b) holding running block index x (largest k with seg_start[k] <= x).
+__device__ __forceinline__ int batch_segment_of(const long long* seg_start, int a, int b,
+                                                long long x) {
+  int lo = a, hi = b - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_start[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One virtual block of phase ph of group B (batch_units gives the counts).
+__device__ void batch_unit(int ph, const BatchGroup& B, long long local, FwdShared& fsh) {
+  const unsigned cnt = unsigned(B.cnt);
+  if (ph == kPhFwdMap) {
+    const unsigned bx = unsigned((B.fa.N + kFwdTile - 1) / kFwdTile);
+    const uint3 bid = make_uint3(unsigned(local % bx), unsigned(local / bx), 0);
+    const uint3 gd = make_uint3(bx, cnt, 1);
+    // unrolled bodies for the row counts the planner produces (register arrays)
+#define TM_FWD_ROWS(R)                                              \
+  case R:                                                           \
+    if (B.kind == TM_HI) fwd_hi_body<R>(B.fa, bid, gd, fsh.hi);     \
+    else fwd_lo_full_body<R>(B.fa, B.kind, bid, gd, fsh.lo);        \
+    break;
+    switch (B.fa.lam - 1) {
+      TM_FWD_ROWS(3) TM_FWD_ROWS(4) TM_FWD_ROWS(5) TM_FWD_ROWS(6) TM_FWD_ROWS(7)
+      default:
+        if (B.kind == TM_HI) fwd_hi_body<0>(B.fa, bid, gd, fsh.hi);
+        else fwd_lo_full_body<0>(B.fa, B.kind, bid, gd, fsh.lo);
+    }
+#undef TM_FWD_ROWS
+  } else if (ph >= kPhFwdPass && ph < kPhFwdPass + kMaxPasses) {
+    const int i = ph - kPhFwdPass;
+    const PassArgs& p = B.fwd[i];
+    const unsigned bx = unsigned((p.Q + p.C - 1) / p.C);
+    fft_pass_body<-1>(B.fwd_in[i], B.fwd_out[i], p,
+                      make_uint3(unsigned(local % bx), unsigned(local / bx), 0),
+                      make_uint3(bx, 2 * cnt, 1));
+  } else if (ph == kPhTwist) {
+    const unsigned bx = unsigned((B.M / 2 + kFusedThreads) / kFusedThreads);
+    twist_body<false>(B.Zu, B.Zu + B.M, B.Q, B.M, B.tc, B.two_over_N, 2 * B.M, 2 * B.M,
+                      make_uint3(unsigned(local % bx), unsigned(local / bx), 0),
+                      make_uint3(bx, cnt, 1));
+  } else if (ph >= kPhInvPass && ph < kPhInvPass + kMaxPasses) {
+    const int i = ph - kPhInvPass;
+    const PassArgs& p = B.inv[i];
+    const unsigned bx = unsigned((p.Q + p.C - 1) / p.C);
+    fft_pass_body<1>(B.inv_in[i], B.inv_out[i], p,
+                     make_uint3(unsigned(local % bx), unsigned(local / bx), 0),
+                     make_uint3(bx, cnt, 1));
+  } else if (ph == kPhBack) {
+    if (B.kind == TM_FULL) {
+      const unsigned bx = unsigned(B.back_nvb);
+      back_full_body(B.ba, make_uint3(unsigned(local % bx), unsigned(local / bx), 0),
+                     make_uint3(bx, cnt, 1));
+    } else if (B.back_small) {
+      if (threadIdx.x < 32)
+        back_small_body_k(B.ba, B.kind, make_uint3(0, unsigned(local), 0), make_uint3(1, cnt, 1));
+    } else {
+      const unsigned bx = unsigned((B.ba.N + kBackTile - 1) / kBackTile);
+      const uint3 bid = make_uint3(unsigned(local % bx), unsigned(local / bx), 0);
+      const uint3 gd = make_uint3(bx, cnt, 1);
+#define TM_BACK_ROWS(R)                                             \
+  case R:                                                           \
+    if (B.kind == TM_LO) back_lo_body<R>(B.ba, bid, gd);            \
+    else back_hi_body<R>(B.ba, bid, gd);                            \
+    break;
+      switch (B.kind == TM_LO ? B.ba.lam - 1 : B.ba.lam) {
+        TM_BACK_ROWS(3) TM_BACK_ROWS(4) TM_BACK_ROWS(5) TM_BACK_ROWS(6) TM_BACK_ROWS(7)
+        default:
+          if (B.kind == TM_LO) back_lo_body<0>(B.ba, bid, gd);
+          else back_hi_body<0>(B.ba, bid, gd);
+      }
+#undef TM_BACK_ROWS
+    }
+  } else if (ph == kPhCarryLocal || ph == kPhCarryApply) {
+    const unsigned bx = unsigned(B.ca.nblocks_max);
+    const uint3 bid = make_uint3(unsigned(local % bx), unsigned(local / bx), 0);
+    if (ph == kPhCarryLocal) carry_local_body(B.ca, bid, make_uint3(bx, cnt, 1));
+    else carry_apply_body(B.ca, bid, make_uint3(bx, cnt, 1));
+  } else if (ph == kPhCarryBlocks) {
+    carry_blocks_body<kFusedThreads>(B.ca, make_uint3(0, unsigned(local), 0));
+  }
+}
+
+// Every product of a batch in one cooperative launch: each step runs one phase (maps,
+// an FFT pass, twist, back map or a carry step) of each of its groups, block v of the
+// step on CTA v mod grid, then a grid barrier; a group's phases come in order in
+// consecutive steps. The block bodies are the per-phase kernels'.
+__global__ void __launch_bounds__(kFusedThreads, 2) k_batch_persistent(BatchArgs A) {
+  __shared__ FwdShared fsh;
+  // the unit's group descriptor, staged in shared memory: the block bodies copy
+  // their argument structs per thread, and shared-memory reads of one address
+  // are broadcast to the warp
+  __shared__ __align__(16) unsigned long long gsh[(sizeof(BatchGroup) + 7) / 8];
+  __shared__ int s_group;
+  const unsigned G = gridDim.x;
+  if (threadIdx.x == 0) s_group = -1;
+  __syncthreads();
+  for (int step = 0; step < A.nsteps; ++step) {
+    const int a = A.step_seg[step], b = A.step_seg[step + 1];
+    if (a == b) continue;
+    const long long base = A.seg_start[a];
+    const long long total = A.seg_start[b] - base;
+    for (long long v = blockIdx.x; v < total; v += G) {
+      const int k = batch_segment_of(A.seg_start, a, b, base + v);
+      const int g = A.seg_group[k];
+      if (g != s_group) {                 // uniform: every thread reads the same s_group
+        __syncthreads();
+        const unsigned long long* src =
+            reinterpret_cast<const unsigned long long*>(A.groups + g);
+        for (int t = threadIdx.x; t < int((sizeof(BatchGroup) + 7) / 8); t += blockDim.x)
+          gsh[t] = src[t];
+        __syncthreads();
+        if (threadIdx.x == 0) s_group = g;
+      }
+      batch_unit(A.seg_phase[k], *reinterpret_cast<const BatchGroup*>(gsh),
+                 base + v - A.seg_start[k], fsh);
+      __syncthreads();
+    }
+    const bool leave = A.leave_barrier && blockIdx.x == gridDim.x - 1;
+    if (step < A.nsteps - 1 && !grid_barrier(A.sync, A.status, leave)) return;
+  }
+}
+
+int batch_max_blocks(size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncAttributes fa{};
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaFuncGetAttributes(&fa, k_batch_persistent) == cudaSuccess)
+    cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin - int(fa.sharedSizeBytes));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent, kFusedThreads,
+                                                    smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per * sms;
+}
+
+cudaError_t launch_batch_persistent(const BatchArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch_persistent, a);
+}
 
 // ------------------------------------------------ CTA-resident products
 
@@ -1897,18 +2393,25 @@ void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s) {
 
 // ------------------------------------------------------------ tables
 
+// one thread per run of kTwRun entries, small blocks spread over the SMs
+unsigned tw_blocks(long long count) {
+  const long long per = (long long)kTwThreads * kTwRun;
+  return unsigned((count + per - 1) / per);
+}
+
 void launch_init_twist_coef(double2* tab, long long N, long long count, cudaStream_t s) {
-  k_init_twist_coef<<<unsigned((count + 255) / 256), 256, 0, s>>>(tab, N, count);
+  if (count <= 0) return;
+  k_init_twist_coef<<<tw_blocks(count), kTwThreads, 0, s>>>(tab, N, count);
 }
 
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s) {
   if (count <= 0) return;
-  k_init_twiddles<<<unsigned((count + 255) / 256), 256, 0, s>>>(tab, len, count);
+  k_init_twiddles<<<tw_blocks(count), kTwThreads, 0, s>>>(tab, len, count);
 }
 
 void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s) {
   if (Ns <= 0) return;
-  k_init_tw4<<<unsigned((Ns + 255) / 256), 256, 0, s>>>(tab, Ns);
+  k_init_tw4<<<tw_blocks(Ns), kTwThreads, 0, s>>>(tab, Ns);
 }
 
 void launch_init_maptab_fx(long long* tab, int which, long long N, int b, int rows, int Q,

@@ -38,11 +38,12 @@ void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
 // Device-side outcome of asynchronous calls on one workspace.
 struct DevStatus {
   unsigned long long margin_fx;  // largest rounding distance, units of 2^-63
-  unsigned int flags;            // kFlagPrecision | kFlagC0
+  unsigned int flags;            // kFlagPrecision | kFlagC0 | kFlagTimeout
   unsigned int pad;
 };
 constexpr unsigned kFlagPrecision = 1u;  // a distance above the plan's bound
 constexpr unsigned kFlagC0 = 2u;         // 2^b does not divide c_0
+constexpr unsigned kFlagTimeout = 4u;    // a bounded grid-wide wait gave up
 
 // Tangent-form twiddle pair of one radix-4 butterfly (see launch_init_tw4).
 struct __align__(32) Tan4 {
@@ -152,6 +153,82 @@ struct CarryArgs {
   unsigned char* fblock;         // scratch: per-block carry functions
   unsigned char* cin_block;      // scratch: per-block carry-in (+1 encoded)
 };
+
+// One product in one cooperative launch (all phases, grid barriers between them).
+constexpr int kFusedThreads = 512;
+struct FusedArgs {
+  int square;                    // u == v: one forward map and transform, squared twist
+  int npass;
+  FwdArgs fa;
+  PassArgs fwd[kMaxPasses], inv[kMaxPasses];
+  const double2* fwd_in[kMaxPasses];
+  double2* fwd_out[kMaxPasses];
+  const double2* inv_in[kMaxPasses];
+  double2* inv_out[kMaxPasses];
+  const double2* Zu;             // twist inputs and output
+  const double2* Zv;
+  double2* Q;
+  long long M;
+  const double2* tc;
+  double two_over_N;
+  BackArgs ba;
+  int back_small;                // the back map of small N (one thread)
+  CarryArgs ca;
+  unsigned* sync;                // grid barrier: arrivals, generation (zeroed before launch)
+  DevStatus* status;
+  int leave_barrier;             // fault injection: the last CTA leaves at the first barrier
+};
+void set_fused_smem_attribute(int bytes);
+// CTAs of kFusedThreads a cooperative launch of `kind` can keep resident with `smem`
+// bytes of dynamic shared memory (0 when it cannot be determined).
+int fused_max_blocks(int kind, size_t smem);
+cudaError_t launch_fused(int kind, const FusedArgs& a, int grid, size_t smem, cudaStream_t s);
+
+// Positions per block of the forward and back map kernels.
+constexpr int kFwdTile = 1024;
+constexpr int kBackTile = 1024;
+
+// A batch in one cooperative launch: per plan group, the arguments of every phase
+// in the items form of the per-phase kernels (product index in the block's y).
+constexpr int kPhFwdMap = 0, kPhFwdPass = 1, kPhTwist = kPhFwdPass + kMaxPasses,
+              kPhInvPass = kPhTwist + 1, kPhBack = kPhInvPass + kMaxPasses,
+              kPhCarryLocal = kPhBack + 1, kPhCarryBlocks = kPhCarryLocal + 1,
+              kPhCarryApply = kPhCarryBlocks + 1, kBatchPhases = kPhCarryApply + 1;
+struct BatchGroup {
+  int kind, npass, cnt, back_small;
+  long long back_nvb;            // full product: back-map blocks per product
+  FwdArgs fa;
+  PassArgs fwd[kMaxPasses], inv[kMaxPasses];
+  const double2* fwd_in[kMaxPasses];
+  double2* fwd_out[kMaxPasses];
+  const double2* inv_in[kMaxPasses];
+  double2* inv_out[kMaxPasses];
+  const double2* Zu;             // twist: product i's spectra at Zu + 2 M i (u), + M (v)
+  double2* Q;
+  long long M;
+  const double2* tc;
+  double two_over_N;
+  BackArgs ba;
+  CarryArgs ca;
+};
+// The launch runs nsteps steps separated by grid barriers. Step s is a list of
+// segments [step_seg[s], step_seg[s+1]); segment k is phase seg_phase[k] of group
+// seg_group[k], its virtual blocks numbered from seg_start[k] (a running sum over all
+// segments). Staggering the groups' phases mixes FFT passes with maps and carries.
+struct BatchArgs {
+  const BatchGroup* groups;
+  int ngroups;
+  int nsteps;
+  const int* step_seg;
+  const long long* seg_start;
+  const int* seg_group;
+  const int* seg_phase;
+  unsigned* sync;                // grid barrier words (zeroed at creation)
+  DevStatus* status;
+  int leave_barrier;             // fault injection: the last CTA leaves at the first barrier
+};
+int batch_max_blocks(size_t smem);
+cudaError_t launch_batch_persistent(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);
 
 // Fraction bits of the fixed-point forward maps: coefficient products
 // (coef 2^(Q + r b)) x digit stay below 2^61.

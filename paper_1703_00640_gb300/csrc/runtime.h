@@ -1,6 +1,7 @@
 // Internal runtime of the library shared by api.cu and batch.cu: resident plan
 // tables, workspaces, the per-product launch sequence.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <memory>
 
@@ -38,6 +39,7 @@ struct Workspace {
   cudaEvent_t fork = nullptr, join = nullptr;
   unsigned long long* norms = nullptr;   // 4 words for the measured digit norms
   DevStatus* status_host = nullptr;      // page-locked copy of the status (tm_mul_host)
+  bool sync_ready = false;               // the single-launch barrier words are zeroed
 };
 
 size_t align_up(size_t x);
@@ -70,6 +72,19 @@ struct KeptOperand {
 // One whole product on stream s with workspace ws (see api.cu). u == v squares
 // (one forward map and one forward FFT); kept != nullptr takes v's transform from
 // it (v is then ignored).
+// Fault injection for tests of the single-launch paths: with TRUNCMUL_FAULT_BARRIER=1
+// (read once) the last CTA of each cooperative launch leaves at the first grid
+// barrier, so the others' bounded waits run out and the call reports TM_ETIMEOUT.
+bool fault_leave_barrier();
+// How products run (tm_set_fused): 0 automatic, 1 per-phase launches only, 2 one
+// cooperative launch wherever the layout allows.
+extern std::atomic<int> g_fused_mode;
+// The pass arguments of pass i of a plan's FFT (stride: elements between batch
+// entries), and the dynamic shared memory of that pass with C sequences per CTA.
+PassArgs pass_args(const PlanEntry& pe, int i, long long stride);
+size_t pass_smem(const FftPass& fp, int C);
+void ensure_kernel_attributes();
+
 int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n,
             cudaStream_t s, const PlanParams& p, const PlanEntry& pe, Workspace& ws,
             int64_t* coeff_out, void* const* events, const KeptOperand* kept = nullptr);

@@ -152,3 +152,53 @@ def test_without_injection_every_call_succeeds(pkg, scale):
     codes = _child(scale)["codes"]
     for key, c in codes.items():
         assert c == ([0, 0] if key == "server" else 0), (key, codes)
+
+
+BARRIER_CHILD = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1]); sys.path.insert(0, sys.argv[1] + "/tests")
+import numpy as np, torch
+import paper_1703_00640_gb300 as pkg
+import workloads
+pkg.load()
+n = 65536
+u, v = workloads.pattern_limbs("random", n, seed=8)
+du = torch.from_numpy(u.view(np.int64)).cuda()
+dv = torch.from_numpy(v.view(np.int64)).cuda()
+res = {}
+pkg.set_fused(pkg.FUSED_ALWAYS)
+_, rep = pkg.mul("lo", du, dv, n, check=False)
+res["single"] = rep["status"]
+items = [("hi", 40000 + 97 * i, torch.empty(pkg.out_limbs("hi", 40000 + 97 * i),
+          dtype=torch.int64, device="cuda"), du[:(40000 + 97 * i + 63) // 64],
+          dv[:(40000 + 97 * i + 63) // 64]) for i in range(8)]
+b = pkg.Batch(items)                     # created in mode 2: one persistent launch
+b.launch()
+res["batch"] = b.status()["rc"]
+b.close()
+pkg.set_fused(pkg.FUSED_NEVER)           # per-phase launches: no barrier, no injection
+out, rep = pkg.mul("lo", du, dv, n, check=False)
+res["after"] = rep["status"]
+res["after_out"] = out.cpu().numpy().view(np.uint64).tolist()
+print(json.dumps(res))
+'''
+
+
+def test_barrier_timeout_is_reported_and_the_device_stays_usable(pkg):
+    """TRUNCMUL_FAULT_BARRIER=1: the last CTA of a single-launch product and of a
+    persistent batch leaves at the first grid barrier; the others' bounded waits
+    run out (about a second) and the calls report TM_ETIMEOUT. A per-phase product
+    in the same process afterwards succeeds with the exact limbs."""
+    env = dict(os.environ)
+    env["TRUNCMUL_FAULT_BARRIER"] = "1"
+    env.pop("TRUNCMUL_FAULT_EMAX_SCALE", None)
+    r = subprocess.run([sys.executable, "-c", BARRIER_CHILD, ROOT], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert res["single"] == pkg.TM_ETIMEOUT, res
+    assert res["batch"] == pkg.TM_ETIMEOUT, res
+    assert res["after"] == 0
+    u, v = workloads.pattern_limbs("random", 65536, seed=8)
+    ref, _ = pkg.mul("lo", dev(u), dev(v), 65536)
+    assert np.array_equal(np.array(res["after_out"], dtype=np.uint64), host(ref))
