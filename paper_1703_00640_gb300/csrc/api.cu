@@ -982,7 +982,20 @@ int run_static(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, ui
   if (overlaps(out, ob, u, in_bytes) || overlaps(out, ob, v, in_bytes)) return TM_EALIAS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PlanEntry pe;
-  int rc = choose_params(kind, n, &pe.p);
+  int rc = TM_OK;
+  {
+    // the planner's choice for the last (kind, n), kept in a fixed record (no
+    // allocation): planning a high product costs milliseconds of host time
+    static std::mutex mu;
+    static struct { bool valid; int kind; uint64_t n; PlanParams p; } last = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (last.valid && last.kind == kind && last.n == n) {
+      pe.p = last.p;
+    } else {
+      rc = choose_params(kind, n, &pe.p);
+      if (rc == TM_OK) last = {true, kind, n, pe.p};
+    }
+  }
   if (rc) return rc;
   pe.M = pe.p.N / 2;
   rc = make_fft_plan(pe.M, &pe.fft);

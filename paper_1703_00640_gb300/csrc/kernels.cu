@@ -153,20 +153,55 @@ __device__ __forceinline__ DD dd_neg(DD x) { return DD{-x.hi, -x.lo}; }
 __device__ __constant__ const double kPi2Hi = 0x1.921fb54442d18p+0;
 __device__ __constant__ const double kPi2Lo = 0x1.1a62633145c07p-54;
 
-// sin x and cos x for 0 <= x <= pi/4 from their Taylor series, summed in
-// double-double up to the terms of degree 31 / 30 (below 2^-110 of the sums).
+__device__ __forceinline__ DD dd_mul_d(DD x, double y) {
+  const double p = __dmul_rn(x.hi, y);
+  const double e = __fma_rn(x.hi, y, -p);
+  return dd_fast_two_sum(p, __dadd_rn(e, __dmul_rn(x.lo, y)));
+}
+
+// cos and sin of j pi / 32, j = 0..8, as double-double (cos hi, lo, sin hi, lo), and
+// 1/k!, k = 0..15 (hi, lo): constants written out to 2^-106
+__device__ __constant__ const double kTrig32[9][4] = {
+    {0x1.0000000000000p+0, 0x0.0p+0, 0x0.0p+0, 0x0.0p+0},
+    {0x1.fd88da3d12526p-1, -0x1.87df6378811c7p-55, 0x1.917a6bc29b42cp-4, -0x1.e2718d26ed688p-60},
+    {0x1.f6297cff75cb0p-1, 0x1.562172a361fd3p-56, 0x1.8f8b83c69a60bp-3, -0x1.26d19b9ff8d82p-57},
+    {0x1.e9f4156c62ddap-1, 0x1.760b1e2e3f81ep-55, 0x1.294062ed59f06p-2, -0x1.5d28da2c4612dp-56},
+    {0x1.d906bcf328d46p-1, 0x1.457e610231ac2p-56, 0x1.87de2a6aea963p-2, -0x1.72cedd3d5a610p-57},
+    {0x1.c38b2f180bdb1p-1, -0x1.6e0b1757c8d07p-56, 0x1.e2b5d3806f63bp-2, 0x1.e0d891d3c6841p-58},
+    {0x1.a9b66290ea1a3p-1, 0x1.9f630e8b6dac8p-60, 0x1.1c73b39ae68c8p-1, 0x1.b25dd267f6600p-55},
+    {0x1.8bc806b151741p-1, -0x1.2c5e12ed1336dp-55, 0x1.44cf325091dd6p-1, 0x1.8076a2cfdc6b3p-57},
+    {0x1.6a09e667f3bcdp-1, -0x1.bdd3413b26456p-55, 0x1.6a09e667f3bcdp-1, -0x1.bdd3413b26456p-55}};
+__device__ __constant__ const double kInvFact[16][2] = {
+    {0x1.0000000000000p+0, 0x0.0p+0},          {0x1.0000000000000p+0, 0x0.0p+0},
+    {0x1.0000000000000p-1, 0x0.0p+0},          {0x1.5555555555555p-3, 0x1.5555555555555p-57},
+    {0x1.5555555555555p-5, 0x1.5555555555555p-59}, {0x1.1111111111111p-7, 0x1.1111111111111p-63},
+    {0x1.6c16c16c16c17p-10, -0x1.f49f49f49f49fp-65}, {0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-73},
+    {0x1.a01a01a01a01ap-16, 0x1.a01a01a01a01ap-76}, {0x1.71de3a556c734p-19, -0x1.c154f8ddc6c00p-73},
+    {0x1.27e4fb7789f5cp-22, 0x1.cbbc05b4fa99ap-76}, {0x1.ae64567f544e4p-26, -0x1.c062e06d1f209p-80},
+    {0x1.1eed8eff8d898p-29, -0x1.2aec959e14c06p-83}, {0x1.6124613a86d09p-33, 0x1.f28e0cc748ebep-87},
+    {0x1.93974a8c07c9dp-37, 0x1.05d6f8a2efd1fp-92}, {0x1.ae7f3e733b81fp-41, 0x1.1d8656b0ee8cbp-97}};
+
+// sin x and cos x for 0 <= x <= pi/4: x = j pi/32 + y with |y| <= pi/64, the Taylor
+// series of sin y and cos y to the terms of degree 15 / 14 by Horner's rule in y^2
+// (the next terms are below 2^-110 of the sums), then the angle-addition formulas
+// with the table's cos and sin of j pi/32.
 __device__ void dd_sincos_small(DD x, DD* sn, DD* cs) {
-  const DD x2 = dd_mul(x, x);
-  DD ts = x, tc = DD{1.0, 0.0};
-  DD ss = x, cc = DD{1.0, 0.0};
-  for (int j = 1; j <= 15; ++j) {
-    ts = dd_div_d(dd_mul(ts, x2), -double((2 * j) * (2 * j + 1)));
-    tc = dd_div_d(dd_mul(tc, x2), -double((2 * j - 1) * (2 * j)));
-    ss = dd_add(ss, ts);
-    cc = dd_add(cc, tc);
+  int j = int(rint(x.hi * (32.0 / 3.141592653589793)));
+  j = j < 0 ? 0 : (j > 8 ? 8 : j);
+  const DD pi32 = DD{kPi2Hi * 0.0625, kPi2Lo * 0.0625};          // exact: a power of two
+  const DD y = dd_add(x, dd_neg(dd_mul_d(pi32, double(j))));
+  const DD z = dd_mul(y, y);
+  DD S = DD{-kInvFact[15][0], -kInvFact[15][1]};                  // sum (-z)^i / (2i+1)!
+  DD C = DD{-kInvFact[14][0], -kInvFact[14][1]};                  // sum (-z)^i / (2i)!
+  for (int i = 6; i >= 0; --i) {
+    const double sg = (i & 1) ? -1.0 : 1.0;
+    S = dd_add(dd_mul(S, z), DD{sg * kInvFact[2 * i + 1][0], sg * kInvFact[2 * i + 1][1]});
+    C = dd_add(dd_mul(C, z), DD{sg * kInvFact[2 * i][0], sg * kInvFact[2 * i][1]});
   }
-  *sn = ss;
-  *cs = cc;
+  const DD sy = dd_mul(y, S), cy = C;
+  const DD cj = DD{kTrig32[j][0], kTrig32[j][1]}, sj = DD{kTrig32[j][2], kTrig32[j][3]};
+  *cs = dd_add(dd_mul(cj, cy), dd_neg(dd_mul(sj, sy)));
+  *sn = dd_add(dd_mul(sj, cy), dd_mul(cj, sy));
 }
 
 // cos and sin of 2 pi m / len in double-double. The angle is reduced with

@@ -263,3 +263,36 @@ def test_dft_constants_are_the_nearest_doubles():
     assert set(vals) == set(want), set(want) ^ set(vals)
     for name, text in vals.items():
         assert float.fromhex(text) == float(want[name]), name
+
+
+def test_double_double_constants():
+    """The double-double constants of the table kernels: cos and sin of j pi / 32
+    and 1/k! (hi + lo within 2^-104 of the exact value, hi the nearest double), and
+    pi / 2."""
+    from decimal import Decimal, localcontext
+    from math import factorial
+    import hp_trig
+    src = open(os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")).read()
+    hexnum = r"(-?0x[0-9a-fp.+-]+)"
+    trig = re.findall(r"\{" + r",\s*".join([hexnum] * 4) + r"\}", src.split("kTrig32")[1].split(";")[0])
+    fact = re.findall(r"\{" + hexnum + r",\s*" + hexnum + r"\}", src.split("kInvFact")[1].split(";")[0])
+    assert len(trig) == 9 and len(fact) == 16
+
+    def close(hi, lo, exact):
+        with localcontext() as ctx:
+            ctx.prec = 80
+            v = Decimal(float.fromhex(hi)) + Decimal(float.fromhex(lo))
+            assert float.fromhex(hi) == float(exact)
+            assert abs(v - exact) <= abs(exact) * Decimal(2) ** -104 + Decimal(10) ** -70
+
+    for j, (ch, cl, sh, sl) in enumerate(trig):
+        c, s = hp_trig.cossin_2pi(j, 64)                     # angle j pi / 32
+        close(ch, cl, c)
+        close(sh, sl, s)
+    with localcontext() as ctx:
+        ctx.prec = 80
+        for k, (h, l) in enumerate(fact):
+            close(h, l, Decimal(1) / Decimal(factorial(k)))
+        hi = re.search(r"kPi2Hi = " + hexnum, src).group(1)
+        lo = re.search(r"kPi2Lo = " + hexnum, src).group(1)
+        close(hi, lo, hp_trig.pi() / 2)
