@@ -91,6 +91,20 @@ for _R in (3, 5, 7):
     # and one final addition: per output sqrt(2) (3 + 2) U + (R - 1) U + U of ||x||_1
     LOCAL_L1[f"r{_R}tw"] = math.sqrt(2.0) * (TWIDDLE_PRODUCT + 2.0) + (_R - 1) + 1.0
     LOCAL_L2[f"r{_R}tw"] = math.sqrt(_R) * LOCAL_L1[f"r{_R}tw"]
+# Radix 3 in the 2-norm directly: with x12 = (x1, x2) the twiddle products add
+# sqrt3 3U ||x12|| (through the DFT, norm sqrt3), the rounding of t = x1 + x2
+# sqrt(3/2) U |t| <= sqrt3 U ||x12||, the difference d, the constant sqrt(3)/2 and
+# its product each sqrt2 (sqrt3/2) U |d| <= sqrt3 U ||x12||, the FMA m = x0 - t/2
+# sqrt2 U (|x0| + ||x12|| / sqrt2), the final additions U sqrt3 ||x||: in all
+# 13.12 U ||x12|| + 1.415 U |x0| + 1.733 U ||x||, at most 14.93 U ||x||, which is
+# 8.6213 U relative to sqrt3 ||x||, rounded up.
+LOCAL_L2["r3tw"] = 8.63
+# The first stage of every pass (Ns = 1) multiplies by no twiddle. Its constants are
+# at least FIRST_STAGE_L2 / FIRST_STAGE_L1 below the twiddled ones: plain radix 4
+# has 2 / 2 against 6.3 / 6, radix 2 1 / 1 against 4 / 4, radix 3 5.65 / 5.83
+# against 8.63 / 10.07, radix 5 and 7 lose sqrt(R) sqrt2 3 U / sqrt2 3 U.
+FIRST_STAGE_L2 = 2.9
+FIRST_STAGE_L1 = 3.0
 TWIST = 20.0          # roundings of the twist, relative to ||x||_2 ||y||_2 (1 + eF)^2
 Q_NORM = 2.0          # ||Q||_1 <= 2 ||x||_2 ||y||_2 for the inverse FFT's input
 SECOND_ORDER = 1.0 + 2.0 ** -20
@@ -98,10 +112,10 @@ SECOND_ORDER = 1.0 + 2.0 ** -20
 
 def stage_lists(M: int):
     """Every stage multiset a layout of the complex FFT of length M can have, priced
-    at the dearer variant (with twiddles): for 1, 2 and 3 passes, the odd primes of
-    M one stage each, the factor 2^a as radix-4 stages plus as many radix-2 stages as
-    passes allow (at most one per pass, same parity as a), and passes - 1 four-step
-    twiddle stages."""
+    at the dearer variant (with twiddles), with its pass count: for 1, 2 and 3
+    passes, the odd primes of M one stage each, the factor 2^a as radix-4 stages
+    plus as many radix-2 stages as passes allow (at most one per pass, same parity
+    as a), and passes - 1 four-step twiddle stages."""
     a, m = 0, M
     while m % 2 == 0:
         m //= 2
@@ -117,9 +131,20 @@ def stage_lists(M: int):
         r2 = min(passes, a)
         if (a - r2) % 2:
             r2 -= 1
-        lists.append(odd + ["r4tan"] * ((a - r2) // 2) + ["r2tw"] * r2
-                     + ["outer"] * (passes - 1))
+        lists.append((odd + ["r4tan"] * ((a - r2) // 2) + ["r2tw"] * r2
+                      + ["outer"] * (passes - 1), passes))
     return lists
+
+
+def _with_first_stages(consts, stages, passes, saving):
+    """Stage constants with the first stage of each pass untwiddled. Which stages
+    come first depends on the layout; taking the saving from the dearest radix
+    stages leaves the largest product, so the bound holds for every layout."""
+    radix = sorted((consts[k] for k in stages if k != "outer"), reverse=True)
+    outer = [consts[k] for k in stages if k == "outer"]
+    for i in range(min(passes, len(radix))):
+        radix[i] -= saving
+    return radix + outer
 
 
 def eta_conv(L: int) -> float:
@@ -127,11 +152,14 @@ def eta_conv(L: int) -> float:
     convolution of real length L (Section 2.1's Convolution step) as the FFT kernels
     compute it: the forward errors eF (2-norm) of both operands, the twist's
     roundings, and the inverse FFT's per-output error on an input of 1-norm
-    Q_NORM (1 + eF)^2 ||x|| ||y||; the worst of the possible layouts."""
+    Q_NORM (1 + eF)^2 ||x|| ||y||; the worst of the possible layouts, each pass's
+    first stage untwiddled."""
     worst = 0.0
-    for stages in stage_lists(L // 2):
-        eF = math.prod(1.0 + SECOND_ORDER * LOCAL_L2[k] * U for k in stages) - 1.0
-        eI = math.prod(1.0 + SECOND_ORDER * LOCAL_L1[k] * U for k in stages) - 1.0
+    for stages, passes in stage_lists(L // 2):
+        g = _with_first_stages(LOCAL_L2, stages, passes, FIRST_STAGE_L2)
+        d = _with_first_stages(LOCAL_L1, stages, passes, FIRST_STAGE_L1)
+        eF = math.prod(1.0 + SECOND_ORDER * c * U for c in g) - 1.0
+        eI = math.prod(1.0 + SECOND_ORDER * c * U for c in d) - 1.0
         grow = (1.0 + eF) ** 2
         twist = SECOND_ORDER * TWIST * U * grow
         worst = max(worst, 2.0 * eF + eF * eF + twist + (Q_NORM * grow + twist) * eI)

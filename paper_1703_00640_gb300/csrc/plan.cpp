@@ -69,18 +69,42 @@ int odd_factor_count(int64_t L) {
 //    parts of Q.
 // The layout (passes, placement of the odd primes) is the autotuner's, so the
 // bound takes the worst one: every stage priced with twiddles, as many radix-2
-// stages as the pass count allows, two four-step twiddle stages.
+// stages as the pass count allows, two four-step twiddle stages, except that the
+// first stage of each pass multiplies by no twiddle, which every radix turns into
+// a saving of at least kFirstG / kFirstD.
 namespace fftbound {
 constexpr double kMu = 3.0;             // product by a table twiddle: table u, cmul 2u
 constexpr double kR2 = kMu + 1.0;       // radix 2 with a twiddle (both norms)
 constexpr double kR4tG = 6.3;           // tangent-form radix 4: 2-norm, (sqrt(112) + 2) / 2
 constexpr double kR4tD = 6.0;           // tangent-form radix 4: per output
+constexpr double kR3G = 8.63;           // radix 3 in the 2-norm, derived on its own
 constexpr double kOuter = kMu;          // four-step twiddle product
 constexpr double kTwist = 20.0;         // twist + pointwise roundings, relative to ||x|| ||y||
 constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
+// The first stage of a pass multiplies by no twiddle; every radix saves at least
+// this much there (2-norm, per output).
+constexpr double kFirstG = 2.9;
+constexpr double kFirstD = 3.0;
 // radix R = 3, 5, 7 with twiddles, h = (R - 1) / 2 chained FMAs per output half:
-// per output sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt(R) times that
+// per output sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt(R) times that (radix 3:
+// kR3G, from its own 2-norm analysis)
 double odd_delta(int R) { return std::sqrt(2.0) * (kMu + 2.0) + 2.0 * ((R - 1) / 2) + 1.0; }
+double odd_gamma(int R) { return R == 3 ? kR3G : std::sqrt(double(R)) * odd_delta(R); }
+
+// prod (1 + c u) over the radix stages (count[i] stages of constant c[i], the
+// constants in decreasing order), the first `firsts` of them discounted by `save`:
+// which stages open a pass depends on the layout, and discounting the dearest
+// gives the largest product.
+double radix_product(const double* c, const int* count, int kinds, int firsts, double save) {
+  double p = 1.0;
+  for (int i = 0; i < kinds; ++i)
+    for (int j = 0; j < count[i]; ++j) {
+      const double ci = firsts > 0 ? c[i] - save : c[i];
+      if (firsts > 0) --firsts;
+      p *= 1.0 + kSlack * ci * kU;
+    }
+  return p;
+}
 }  // namespace fftbound
 
 double eta_conv(int64_t L) {
@@ -88,24 +112,20 @@ double eta_conv(int64_t L) {
   int64_t m = L / 2;
   int a = 0;
   while (m % 2 == 0) { m /= 2; ++a; }
-  double oddG = 1.0, oddD = 1.0;                    // products over the odd-radix stages
-  for (int R : {3, 5, 7})
-    while (m % R == 0) {
-      m /= R;
-      oddG *= 1.0 + kSlack * std::sqrt(double(R)) * odd_delta(R) * kU;
-      oddD *= 1.0 + kSlack * odd_delta(R) * kU;
-    }
+  int odd[3] = {0, 0, 0};                           // stages of radix 7, 5, 3
+  const int radix[3] = {7, 5, 3};
+  for (int i = 0; i < 3; ++i)
+    while (m % radix[i] == 0) { m /= radix[i]; ++odd[i]; }
+  const double cG[5] = {odd_gamma(7), odd_gamma(5), odd_gamma(3), kR4tG, kR2};
+  const double cD[5] = {odd_delta(7), odd_delta(5), odd_delta(3), kR4tD, kR2};
   double worst = 0.0;
   for (int P = 1; P <= 3; ++P) {
     int r2 = std::min(P, a);
     if ((a - r2) % 2) --r2;                         // radix-2 stages: one per pass at most
-    const int r4 = (a - r2) / 2;
-    const double g = oddG * std::pow(1.0 + kSlack * kR4tG * kU, r4) *
-                     std::pow(1.0 + kSlack * kR2 * kU, r2) *
-                     std::pow(1.0 + kSlack * kOuter * kU, P - 1);
-    const double d = oddD * std::pow(1.0 + kSlack * kR4tD * kU, r4) *
-                     std::pow(1.0 + kSlack * kR2 * kU, r2) *
-                     std::pow(1.0 + kSlack * kOuter * kU, P - 1);
+    const int count[5] = {odd[0], odd[1], odd[2], (a - r2) / 2, r2};
+    const double outer = std::pow(1.0 + kSlack * kOuter * kU, P - 1);
+    const double g = radix_product(cG, count, 5, P, kFirstG) * outer;
+    const double d = radix_product(cD, count, 5, P, kFirstD) * outer;
     const double eF = g - 1.0, eI = d - 1.0, grow = (1.0 + eF) * (1.0 + eF);
     const double e = 2.0 * eF + eF * eF + kSlack * kTwist * kU * grow +
                      (2.0 * grow + kSlack * kTwist * kU * grow) * eI;

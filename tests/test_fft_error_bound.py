@@ -116,9 +116,108 @@ def test_butterflies_within_local_constants(key, R):
                     r2 = math.sqrt(sum(e * e for e in err)) / (U * math.sqrt(R) * n2)
                     assert r1 <= P.LOCAL_L1[key], (key, Ns, kk, S, r1)
                     assert r2 <= P.LOCAL_L2[key], (key, Ns, kk, S, r2)
+                    if Ns == 1:          # a pass's first stage: no twiddle
+                        assert r1 <= P.LOCAL_L1[key] - P.FIRST_STAGE_L1, (key, S, r1)
+                        assert r2 <= P.LOCAL_L2[key] - P.FIRST_STAGE_L2, (key, S, r2)
                     worst1, worst2 = max(worst1, r1), max(worst2, r2)
     print(f"{key}: worst per-output {worst1:.2f} U (bound {P.LOCAL_L1[key]:.2f}), "
           f"worst 2-norm {worst2:.2f} U (bound {P.LOCAL_L2[key]:.2f})")
+
+
+def _dft3_first_order(x, S, twiddled):
+    """The output-error vectors of dft3's roundings to first order, one per real
+    rounding (a unit relative error there, every other operation exact), in the
+    kernel's order: t = x1 + x2, m = x0 - t/2 (FMA), d = x1 - x2, the constant
+    sqrt(3)/2 (one relative error for both components), d times it, the three
+    final additions. The twiddle products' error, at most 3 U |x_t| in any
+    direction, enters through the DFT (norm sqrt 3) and is returned apart."""
+    x0, x1, x2 = (complex(*v) for v in x)
+    c = math.sqrt(3) / 2
+    si = 1j * S
+
+    def outputs(eps):
+        def r(v, *keys):            # v with relative errors on its real / imaginary parts
+            return complex(v.real * (1 + eps.get(keys[0], 0)),
+                           v.imag * (1 + eps.get(keys[1], 0)))
+        t = r(x1 + x2, "tr", "ti")
+        m = r(x0 - t / 2, "mr", "mi")
+        d = r(x1 - x2, "dr", "di")
+        k = c * (1 + eps.get("k", 0))
+        sd = si * r(d * k, "pr", "pi")
+        return np.array([r(x0 + t, "y0r", "y0i"), r(m + sd, "y1r", "y1i"),
+                         r(m - sd, "y2r", "y2i")])
+
+    base = outputs({})
+    h = 2.0 ** -20
+    keys = ["tr", "ti", "mr", "mi", "dr", "di", "k", "pr", "pi",
+            "y0r", "y0i", "y1r", "y1i", "y2r", "y2i"]
+    vecs = []
+    for key in keys:
+        dv = (outputs({key: h}) - base) / h
+        vecs.append(np.concatenate([dv.real, dv.imag]))
+    tw = math.sqrt(3) * 3 * math.hypot(abs(x1), abs(x2)) if twiddled else 0.0
+    return np.array(vecs), tw
+
+
+def test_radix3_two_norm_constant_brute_force():
+    """The radix-3 2-norm constant (LOCAL_L2["r3tw"], and with the first-stage
+    saving for the untwiddled butterfly) against the worst first-order error of
+    dft3's operation sequence: every sign pattern of its 15 real roundings, on
+    random and hill-climbed unit inputs. A dropped or undercounted term in the
+    derivation shows as a pattern above the constant."""
+    signs = np.array([[1 - 2 * ((p >> i) & 1) for i in range(15)] for p in range(1 << 15)],
+                     dtype=np.float64)
+    rng = np.random.default_rng(3)
+
+    def worst(x, S, twiddled):
+        V, tw = _dft3_first_order(x, S, twiddled)
+        return (np.max(np.linalg.norm(signs @ V, axis=1)) + tw) / math.sqrt(3)
+
+    found = {}
+    for twiddled in (True, False):
+        limit = P.LOCAL_L2["r3tw"] - (0.0 if twiddled else P.FIRST_STAGE_L2)
+        best, bx = 0.0, None
+        for _ in range(60):
+            v = rng.normal(size=6)
+            v /= np.linalg.norm(v)
+            x = [(v[2 * i], v[2 * i + 1]) for i in range(3)]
+            w = worst(x, -1, twiddled)
+            if w > best:
+                best, bx = w, v
+        step = 0.3
+        for _ in range(120):            # hill-climb from the best random start
+            v = bx + step * rng.normal(size=6)
+            v /= np.linalg.norm(v)
+            w = worst([(v[2 * i], v[2 * i + 1]) for i in range(3)], -1, twiddled)
+            if w > best:
+                best, bx = w, v
+            else:
+                step *= 0.97
+        for S in (-1, 1):
+            w = worst([(bx[2 * i], bx[2 * i + 1]) for i in range(3)], S, twiddled)
+            assert w <= limit, (twiddled, S, w, limit)
+        assert best <= limit, (twiddled, best, limit)
+        found[twiddled] = (best, limit)
+    print("radix 3 first-order worst (twiddled, untwiddled):",
+          {k: (round(a, 3), round(b, 3)) for k, (a, b) in found.items()})
+
+
+def test_first_stage_discount_is_conservative():
+    """eta_conv with the discount taken from the dearest stages is at least eta_conv
+    with the discount on any other choice of P stages (the layout decides which
+    stages open a pass), checked for lengths with every mix of radices."""
+    import itertools
+    for M in (1260, 2520 * 7, 4608, 3 * 5 * 7 * 64):
+        for stages, passes in P.stage_lists(M):
+            radix = [P.LOCAL_L2[k] for k in stages if k != "outer"]
+            mine = math.prod(1 + c * U for c in
+                             P._with_first_stages(P.LOCAL_L2, stages, passes, P.FIRST_STAGE_L2)
+                             if True)
+            for pick in itertools.combinations(range(len(radix)), min(passes, len(radix))):
+                other = [c - (P.FIRST_STAGE_L2 if i in pick else 0.0)
+                         for i, c in enumerate(radix)]
+                other += [P.LOCAL_L2["outer"]] * stages.count("outer")
+                assert math.prod(1 + c * U for c in other) <= mine * (1 + 1e-15)
 
 
 def test_twiddle_product_within_constant():
