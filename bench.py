@@ -88,7 +88,10 @@ def parse():
                          "tm_autotune_plan / tm_autotune before timing)")
     ap.add_argument("--plan", action="append", default=[], metavar="KIND:B:N",
                     help="fix the plan of a product kind at the bench size with "
-                         "tm_plan_set (e.g. hi:7:2621440), instead of tuning it")
+                         "tm_plan_set (e.g. hi:8:2359296), instead of tuning it")
+    ap.add_argument("--layout", action="append", default=[], metavar="KIND:POINTS:SPLIT:PASSES",
+                    help="fix the FFT pass layout of a product kind at the bench size with "
+                         "tm_set_layout (as the line's plans report it), instead of tuning it")
     ap.add_argument("--large-bits", type=int, default=1 << 28,
                     help="operand size of the large single-product section")
     ap.add_argument("--no-large", action="store_true",
@@ -496,13 +499,24 @@ def run_cuda(args):
         k, b, N = spec.split(":")
         pkg.plan_set(k, n, int(b), int(N))
         fixed[k] = {"b": int(b), "N": int(N)}
+    fixed_layouts = {}
+    for spec in args.layout:
+        k, pts, split, passes = spec.split(":")
+        fixed_layouts[k] = {"points": int(pts), "split": int(split), "passes": int(passes)}
     if not args.no_autotune:
         tuned = {"plans": {k: pkg.autotune_plan(k, n, stream=stream)
                            for k in kinds if k not in fixed}}
-        tuned["layouts"] = {k: pkg.autotune(k, n, stream=stream) for k in kinds}
+        tuned["layouts"] = {k: pkg.autotune(k, n, stream=stream)
+                            for k in kinds if k not in fixed_layouts}
+    for k, lay in fixed_layouts.items():       # after the plans: the layout of their length
+        pkg.set_layout(k, n, lay["points"], lay["split"], lay["passes"])
     if fixed:
         tuned = dict(tuned or {}, fixed_plans=fixed)
     plans = {k: pkg.plan(k, n) for k in kinds}
+    layouts = {k: (fixed_layouts[k] if k in fixed_layouts else
+                   {x: tuned["layouts"][k][x] for x in ("points", "split", "passes")}
+                   if tuned and k in tuned.get("layouts", {}) else
+                   {"points": 1024, "split": 0, "passes": 0}) for k in kinds}
 
     # correctness gate on the bench workload (sampled against the oracle's low product)
     _, rep = pkg.mul("lo", u, v, n, out=outs["lo"])
@@ -757,7 +771,9 @@ def run_cuda(args):
         "wall_s_timed": wall,
         "ms": ms, "phases_ms_median": phases,
         "plans": {k: {x: plans[k][x] for x in ("b", "N", "lam_fwd", "lam_bwd", "fft_passes")}
-                  | {"e_max": sig(plans[k]["e_max"]), "margin": sig(margin[k])} for k in kinds},
+                  | {"e_max": sig(plans[k]["e_max"]), "margin": sig(margin[k]),
+                     "layout": ":".join(str(layouts[k][x]) for x in ("points", "split", "passes"))}
+                  for k in kinds},
         "status_after_timed_region": st["rc"],
         "square_and_kept_operand": variants, "division": division,
         "paper_parameters": paper_params,

@@ -553,7 +553,11 @@ int tm_convolution(double* out, const double* x, const double* y, int64_t N, voi
  *            = c2 (1 - i t2), or -i c2 (1 - i t2) with c2s = -c2 when its angle
  *            is pi/2 or more;
  *   which 2: the twist coefficients of real length N = len: out[2k], out[2k+1]
- *            = cos(2 pi k / N) (cos, -sin)(2 pi k / N) / N, k < count.
+ *            = cos(2 pi k / N) (cos, -sin)(2 pi k / N) / N, k < count;
+ *   which 3: the four-step twiddles of a pass with Mp = len and Qc = count
+ *            sequences (count must divide len), in the pass's output order:
+ *            out[2e], out[2e+1] = cos, -sin of 2 pi (qc k mod Mp) / Mp at
+ *            e = k Qc + qc, qc < Qc, k < len / count (len entries).
  * Each value is the double nearest to the exact one, up to 2^-40 of an ulp
  * (the tangent t is nearest to sin / c with the stored c). Returns TM_OK,
  * TM_EINVAL or TM_ECUDA.

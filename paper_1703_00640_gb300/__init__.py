@@ -311,11 +311,13 @@ def convolution(x, y, out=None, stream=None):
 
 def table_values(which: int, length: int, count: int):
     """tm_table_values: the FFT kernels' twiddle table `which` (0 twiddles, 1
-    tangent-form radix-4 records, 2 twist coefficients) as a float64 numpy array."""
+    tangent-form radix-4 records, 2 twist coefficients, 3 four-step twiddles of
+    Mp = length in the output order of count sequences) as a float64 numpy array."""
     import numpy as np
     import torch
     per = 4 if which == 1 else 2
-    out = torch.empty(per * count, dtype=torch.float64, device="cuda")
+    entries = length if which == 3 else count
+    out = torch.empty(per * max(entries, 0), dtype=torch.float64, device="cuda")
     rc = load().tm_table_values(int(which), int(length), int(count), _ptr(out), _stream_ptr(None))
     if rc:
         raise TruncMulError(rc, "tm_table_values")

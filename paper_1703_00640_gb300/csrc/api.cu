@@ -140,7 +140,8 @@ size_t workspace_bytes(const PlanParams& p) {
 }
 
 // Offsets of every twiddle table of a plan inside one double2 allocation:
-// per pass omega_L (when a stage needs it), omega_Mp, the radix-4 tangent
+// per pass omega_L (when a stage needs it), omega_Mp^(qc k) in output order (Mp
+// entries), the radix-4 tangent
 // tables; then the twist coefficients (1 + omega_N^(2k)) / (2N), k <= M/2.
 // Returns the count.
 size_t layout_twiddles(PlanEntry* e) {
@@ -177,7 +178,7 @@ void init_twiddles(const PlanEntry& e, cudaStream_t s) {
   for (int i = 0; i < e.fft.npass; ++i) {
     const FftPass& fp = e.fft.pass[i];
     launch_init_twiddles(e.tw + fp.tw_sub, fp.L, fp.L, s);
-    if (fp.Mp) launch_init_twiddles(e.tw + fp.tw_outer, fp.Mp, fp.Mp, s);
+    if (fp.Mp) launch_init_outer(e.tw + fp.tw_outer, fp.Mp, fp.Qc, s);
     int Ns = 1;
     for (int st = 0; st < fp.nstages; ++st) {
       if (fp.tw4_off[st] >= 0)
@@ -1738,6 +1739,10 @@ int tm_table_values(int which, int64_t len, int64_t count, double* out, void* st
       tmul::launch_init_tw4(reinterpret_cast<tmul::Tan4*>(out), int(len), s);
       break;
     case 2: tmul::launch_init_twist_coef(reinterpret_cast<double2*>(out), len, count, s); break;
+    case 3:
+      if (count < 1 || len % count) return TM_EINVAL;
+      tmul::launch_init_outer(reinterpret_cast<double2*>(out), len, count, s);
+      break;
     default: return TM_EINVAL;
   }
   return cudaGetLastError() == cudaSuccess ? TM_OK : TM_ECUDA;

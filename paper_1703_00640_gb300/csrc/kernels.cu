@@ -275,6 +275,32 @@ __global__ void __launch_bounds__(kTwThreads) k_init_twiddles(double2* tab, long
   }
 }
 
+// tab[k Qc + qc] = exp(-2 pi i (qc k mod Mp) / Mp), qc < Qc, k < Mp / Qc: the four-step
+// twiddles in the order a pass stores its outputs (output k of sequence qc), so
+// that the consecutive sequences of a warp read consecutive entries. Along a row
+// the exponent steps by k: a run rotates by exp(-2 pi i k / Mp) and starts over
+// where it enters the next row.
+__global__ void __launch_bounds__(kTwThreads) k_init_outer(double2* tab, long long Mp,
+                                                             long long Qc) {
+  const long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * kTwRun;
+  if (e0 >= Mp) return;
+  long long k = e0 / Qc, qc = e0 - k * Qc;
+  DD c, s, c1, s1;
+  for (int i = 0; i < kTwRun && e0 + i < Mp; ++i) {
+    const long long m = (qc * k) % Mp;
+    if (i == 0 || qc == 0) {
+      dd_cossin_2pi(m, Mp, &c, &s);
+      dd_cossin_2pi(k, Mp, &c1, &s1);
+    } else {
+      dd_rotate(c, s, c1, s1);
+    }
+    DD cc = c, ss = s;
+    dd_exact_axes(m, Mp, &cc, &ss);
+    tab[e0 + i] = make_double2(cc.hi, -ss.hi);
+    if (++qc == Qc) { qc = 0; ++k; }
+  }
+}
+
 // tab[k] = (1 + w^2) / (2N) = cos(2 pi k / N) w / N, w = exp(-2 pi i k / N), k < count:
 // the one twiddle of the fused real-FFT twist (see twist_pair), each component
 // rounded once.
@@ -1099,7 +1125,7 @@ __device__ __forceinline__ void fft_pass_body(const double2* __restrict__ in, do
     const long long qa = q / p.Qc, qc = q - qa * p.Qc;
     double2 val = buf[c * L + k];
     if (p.Mp) {
-      const double2 w = __ldg(p.tw_outer + qc * k);
+      const double2 w = __ldg(p.tw_outer + k * p.Qc + qc);
       val = S < 0 ? cmul(val, w) : cmulc(val, w);
     }
     out[qa * p.OA + qc * p.OC + (long long)k * p.OS] = val;
@@ -2442,6 +2468,11 @@ void launch_init_twist_coef(double2* tab, long long N, long long count, cudaStre
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s) {
   if (count <= 0) return;
   k_init_twiddles<<<tw_blocks(count), kTwThreads, 0, s>>>(tab, len, count);
+}
+
+void launch_init_outer(double2* tab, long long Mp, long long Qc, cudaStream_t s) {
+  if (Mp <= 0 || Qc <= 0) return;
+  k_init_outer<<<tw_blocks(Mp), kTwThreads, 0, s>>>(tab, Mp, Qc);
 }
 
 void launch_init_tw4(Tan4* tab, int Ns, cudaStream_t s) {

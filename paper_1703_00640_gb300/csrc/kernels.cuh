@@ -57,7 +57,7 @@ struct PassArgs {
   long long Q, Qc, IA, IC, IS, OA, OC, OS, Mp;
   long long batch_stride;        // complex elements between batch entries
   const double2* tw_sub;         // omega_L^k
-  const double2* tw_outer;       // omega_Mp^m (or nullptr)
+  const double2* tw_outer;       // omega_Mp^(qc k) at k Qc + qc (or nullptr)
   const Tan4* tw4;            // tangent-form radix-4 stage tables
   int tw4_len;
   int tw4_off[kMaxStages];
@@ -283,6 +283,9 @@ void launch_small(const SmallArgs& a, int grid, size_t smem, cudaStream_t s);
 // table initialisation
 // tab[m] = omega_len^m = exp(-2 pi i m / len), m < count
 void launch_init_twiddles(double2* tab, long long len, long long count, cudaStream_t s);
+// tab[k Qc + qc] = omega_Mp^(qc k mod Mp), qc < Qc, k < Mp / Qc (Qc divides Mp): the
+// four-step twiddles in a pass's output order
+void launch_init_outer(double2* tab, long long Mp, long long Qc, cudaStream_t s);
 // tab[k] = (1 + omega_N^(2k)) / (2N), k < count (coefficients of the fused twist)
 void launch_init_twist_coef(double2* tab, long long N, long long count, cudaStream_t s);
 // Tangent-form twiddles of one radix-4 Stockham stage with Ns > 1: entry k < Ns

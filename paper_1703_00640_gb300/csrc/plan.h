@@ -27,7 +27,7 @@ struct FftPass {
   int C = 1;         // sequences per CTA
   int threads = 32;  // CTA size
   size_t tw_sub = 0;     // offset (in double2) of omega_L^k, k < L, in the twiddle table
-  size_t tw_outer = 0;   // offset of omega_Mp^m, m < Mp
+  size_t tw_outer = 0;   // offset of omega_Mp^(qc k) at k Qc + qc (Mp = Qc L entries)
   // radix-4 stages with twiddles use tangent-form tables (t1, c1, t2, c2s) per
   // twiddle index: tw4 is their offset (double2 units, even), tw4_len the number
   // of double4 entries, tw4_off[s] the first entry of stage s (-1: none)

@@ -74,6 +74,32 @@ def test_twist_coefficients_are_correctly_rounded(pkg, N):
             assert _nearest_ok(tab[k, 1], -c * s / N), (N, k)
 
 
+OUTER = [(12, 3), (12, 4), (40, 8), (4096, 64), (6144, 48), (2 ** 20, 1024),
+         (9 * 2 ** 17, 1152), (5 * 2 ** 20, 5120), (45 * 2 ** 15, 1440), (7 * 2 ** 12, 7)]
+
+
+@pytest.mark.parametrize("Mp,Qc", OUTER, ids=[f"{m}x{q}" for m, q in OUTER])
+def test_outer_twiddles_in_output_order(pkg, Mp, Qc):
+    """The four-step table entry k Qc + qc is the double nearest to
+    exp(-2 pi i (qc k mod Mp) / Mp) (sampled against 200-bit values), and every
+    entry equals the plain table's entry at qc k mod Mp, bit for bit."""
+    tab = pkg.table_values(3, Mp, Qc).reshape(-1, 2)
+    plain = pkg.table_values(0, Mp, Mp).reshape(-1, 2)
+    e = np.arange(Mp, dtype=np.int64)
+    k, qc = e // Qc, e % Qc
+    m = (qc * k) % Mp
+    assert np.array_equal(tab.view(np.int64), plain[m].view(np.int64)), (Mp, Qc)
+    for i in _sample(Mp, k=600, seed=Mp + Qc):
+        c, s = hp_trig.cossin_2pi(int(m[i]), Mp)
+        assert _nearest_ok(tab[i, 0], c), (Mp, Qc, int(i), "cos")
+        assert _nearest_ok(tab[i, 1], -s), (Mp, Qc, int(i), "sin")
+
+
+def test_outer_twiddles_argument_checked(pkg):
+    with pytest.raises(pkg.TruncMulError):
+        pkg.table_values(3, 40, 7)
+
+
 @pytest.mark.parametrize("Ns", [1, 2, 4, 16, 64, 256, 1024])
 def test_tangent_records(pkg, Ns):
     """c is the nearest double to the cosine and t the nearest double to sin / c,
