@@ -361,10 +361,19 @@ void ensure_kernel_attributes() {
 }
 
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
-               long long stride, cudaStream_t s) {
+               long long stride, cudaStream_t s, const uint64_t* map_limbs,
+               const PlanParams* map_p) {
   for (int i = 0; i < pe.fft.npass; ++i) {
     const FftPass& fp = pe.fft.pass[i];
     PassArgs a{};
+    if (i == 0 && map_limbs && map_p) {
+      const PlanParams& p = *map_p;
+      a.map_limbs = reinterpret_cast<const unsigned long long*>(map_limbs);
+      a.map_n = p.n;
+      a.map_nlimbs = limbs_of(p.n);
+      a.map_limit = std::min<int64_t>(p.N, p.n_digits);
+      a.map_b = p.b;
+    }
     a.L = fp.L; a.nstages = fp.nstages; a.C = fp.C;
     std::copy(fp.radix, fp.radix + kMaxStages, a.radix);
     a.Q = fp.Q; a.Qc = fp.Qc; a.IA = fp.IA; a.IC = fp.IC; a.IS = fp.IS;
@@ -733,7 +742,30 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   const bool one = square || kept;
   double2* bufs[2] = {R0, R1};
   int cur;
-  if (!one && ws.side) {
+  // full product: the first forward pass computes the split of its operand as it
+  // loads it, so steps 1 and 2 are one launch per pass. (The low product's map on
+  // load measured slower: the first pass reads columns, so each thread walks a
+  // serial chain of digit and table loads per element; its own kernel reads tiles.)
+  const bool map_on_load = kind == TM_FULL && !ws.operands_mapped;
+  double2* bufs_v[2] = {R0 + M, R1 + M};
+  PlanParams mp = p;                 // this call's operand size and digit count
+  mp.n = n;
+  if (map_on_load) {
+    mark(1);
+    if (one) {
+      cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
+    } else if (ws.side) {          // u's transform on s, v's on the side stream
+      TM_CHECK(cudaEventRecord(ws.fork, s));
+      TM_CHECK(cudaStreamWaitEvent(ws.side, ws.fork, 0));
+      cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
+      launch_fft(pe, bufs_v, 0, -1, 1, M, ws.side, v, &mp);
+      TM_CHECK(cudaEventRecord(ws.join, ws.side));
+      TM_CHECK(cudaStreamWaitEvent(s, ws.join, 0));
+    } else {
+      cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
+      launch_fft(pe, bufs_v, 0, -1, 1, M, s, v, &mp);
+    }
+  } else if (!one && ws.side) {
     // 1. digits + forward maps of both operands in one launch (one pass over the map
     // table); 2. u's forward FFT on s, v's on the side stream, so that each
     // operand's passes fill the SMs the other's leave idle
@@ -744,7 +776,6 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
     mark(1);
     TM_CHECK(cudaEventRecord(ws.fork, s));
     TM_CHECK(cudaStreamWaitEvent(ws.side, ws.fork, 0));
-    double2* bufs_v[2] = {R0 + M, R1 + M};
     cur = launch_fft(pe, bufs, 0, -1, 1, M, s);
     launch_fft(pe, bufs_v, 0, -1, 1, M, ws.side);
     TM_CHECK(cudaEventRecord(ws.join, ws.side));
@@ -1117,7 +1148,9 @@ int tm_mul_host(int kind, uint64_t* out_host, const uint64_t* u_host, const uint
                       !tmul::overlaps(out_host, out_bytes, v_host, in_bytes);
   bool done = false;
   if (direct) {
+    ws->operands_mapped = true;
     rc = tmul::enqueue(kind, mo, mu, mv, n_bits, s, p, *pe, *ws, nullptr, nullptr);
+    ws->operands_mapped = false;
     if (rc) return rc;
     tmul::DevStatus* sh = nullptr;        // the status word, published by one kernel
     if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&sh), ws->status_host, 0) ==

@@ -1067,7 +1067,20 @@ __device__ __forceinline__ void stockham_stage4t(double2* buf, int L, int C, int
   }
 }
 
-template <int S>
+// The split of the full product (Algorithm 1, split step) at the positions 2m and
+// 2m + 1, for a first pass that computes its input as it loads it: the same
+// balanced digits as fwd_lo_full_body gives the full product (0 from the digit
+// count on), so the values are identical.
+__device__ __forceinline__ double2 split_pair(const unsigned long long* limbs,
+                                               unsigned long long n, long long nlimbs,
+                                               long long limit, int b, long long m) {
+  auto digit = [&](long long q) -> int {
+    return q < limit ? balanced_digit(limbs, nlimbs, n, 0, b, q, limit - 1, false) : 0;
+  };
+  return make_double2(i2d_exact(digit(2 * m)), i2d_exact(digit(2 * m + 1)));
+}
+
+template <int S, bool MAP = false>
 __device__ __forceinline__ void fft_pass_body(const double2* __restrict__ in, double2* __restrict__ out, PassArgs p, const uint3 bid, const uint3 gdim) {
   extern __shared__ double2 smem[];
   const int L = p.L, C = p.C;
@@ -1093,7 +1106,9 @@ __device__ __forceinline__ void fft_pass_body(const double2* __restrict__ in, do
     double2 val = make_double2(0.0, 0.0);
     if (q < p.Q) {
       const long long qa = q / p.Qc, qc = q - qa * p.Qc;
-      val = in[qa * p.IA + qc * p.IC + (long long)j * p.IS];
+      const long long m = qa * p.IA + qc * p.IC + (long long)j * p.IS;
+      val = MAP ? split_pair(p.map_limbs, p.map_n, p.map_nlimbs, p.map_limit, p.map_b, m)
+                : in[m];
     }
     buf[c * L + j] = val;
   }
@@ -1137,6 +1152,11 @@ __global__ void k_fft_pass(const double2* __restrict__ in, double2* __restrict__
   fft_pass_body<S>(in, out, p, blockIdx, gridDim);
 }
 
+// First forward pass with the full product's split computed on load (PassArgs::map_limbs).
+__global__ void k_fft_pass_map(double2* __restrict__ out, PassArgs p) {
+  fft_pass_body<-1, true>(nullptr, out, p, blockIdx, gridDim);
+}
+
 void set_small_smem_attribute(int bytes);
 
 // Shared memory above 48 KB per CTA needs the opt-in; set once before any launch
@@ -1147,6 +1167,7 @@ void set_fft_smem_attribute() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncSetAttribute(k_fft_pass<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_fft_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_fft_pass_map, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   set_small_smem_attribute(optin);
   set_fused_smem_attribute(optin);
 }
@@ -1157,7 +1178,9 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
   const size_t smem = (size_t((p.C * p.L + 1) & ~1) + 2 * size_t(p.tw4_len) +
                       (p.need_wL ? size_t(p.L) : 0)) * sizeof(double2);
   dim3 grid(blocks, batch);
-  if (dir < 0)
+  if (p.map_limbs)
+    launch_pdl(k_fft_pass_map, dim3(blocks), dim3(threads), smem, s, out, p);
+  else if (dir < 0)
     launch_pdl(k_fft_pass<-1>, grid, dim3(threads), smem, s, in, out, p);
   else
     launch_pdl(k_fft_pass<1>, grid, dim3(threads), smem, s, in, out, p);

@@ -62,6 +62,13 @@ struct PassArgs {
   int tw4_len;
   int tw4_off[kMaxStages];
   int need_wL;
+  // Full product's split computed as the first pass loads: element m is the pair of
+  // balanced digits (2m, 2m + 1) of the operand in map_limbs (0 from map_limit on),
+  // as the forward map kernel forms them. map_limbs == nullptr: read `in`.
+  const unsigned long long* map_limbs;
+  unsigned long long map_n;
+  long long map_nlimbs, map_limit;
+  int map_b;
 };
 
 // Per-product fields of the forward map, back map and carry kernels. A batch of

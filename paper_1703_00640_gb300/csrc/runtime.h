@@ -40,6 +40,9 @@ struct Workspace {
   unsigned long long* norms = nullptr;   // 4 words for the measured digit norms
   DevStatus* status_host = nullptr;      // page-locked copy of the status (tm_mul_host)
   bool sync_ready = false;               // the single-launch barrier words are zeroed
+  // set around enqueue when the operands are mapped host memory: the forward map then
+  // runs as its own kernel, which reads each limb once
+  bool operands_mapped = false;
 };
 
 size_t align_up(size_t x);
@@ -60,8 +63,13 @@ int get_tables(const PlanParams& p, bool single_pass, cudaStream_t s,
                std::shared_ptr<PlanEntry>* out);
 // FFT passes of a batch of `batch` sequences of length M (stride `stride`),
 // ping-ponging bufs[cur] <-> bufs[cur ^ 1]; returns the buffer index holding the result
+// With map_limbs, the first pass of a forward transform (batch 1) computes its input,
+// the full product's split (Algorithm 1) of the operand map_limbs under the call's
+// plan *map_p (its n and digit count, which tables shared across n do not carry),
+// as it loads it, instead of reading bufs[cur].
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
-               long long stride, cudaStream_t s);
+               long long stride, cudaStream_t s, const uint64_t* map_limbs = nullptr,
+               const PlanParams* map_p = nullptr);
 void ensure_kernel_attributes();
 // Forward transform of one operand kept on the device: the spectrum of V~ (complex
 // length M, the order the forward FFT leaves it in) and theta_V (high product).
