@@ -37,6 +37,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50/p99 ms"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of all FFT pass launches of one
+# product, from one ncu capture (each launch alone, cold caches) of the plans and layouts in
+# the keys, built from the kernel source with this SHA-256. roofline.traffic reports their
+# sum only while the timed plans, layouts and kernel source are these; otherwise null.
+FFT_DRAM_CAPTURE = {
+    "kernels_sha256": "ef680a74a2c8317034977753955f019b4f03bc5f93face6e1e56ca9bc8c0ce30",
+    "bytes": {("lo", 8, 2097152, "1024:0:0"): 151393280,
+              ("hi", 8, 2359296, "1024:2:0"): 170408448,
+              ("full", 12, 2949120, "1024:0:0"): 170081792},
+}
+
+
+def fft_traffic(plans, layouts, kinds):
+    """The captured DRAM bytes of one step's FFT passes, or None when the capture does
+    not describe this run (another plan, layout or kernel source)."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != FFT_DRAM_CAPTURE["kernels_sha256"]:
+            return None
+    keys = [(k, plans[k]["b"], plans[k]["N"],
+             ":".join(str(layouts[k][x]) for x in ("points", "split", "passes"))) for k in kinds]
+    if not all(key in FFT_DRAM_CAPTURE["bytes"] for key in keys):
+        return None
+    return sum(FFT_DRAM_CAPTURE["bytes"][key] for key in keys)
 UNIT = "Gbit/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 L2_FLUSH_BYTES = 256 << 20
@@ -616,10 +642,12 @@ def run_cuda(args):
         fft_ms += sum(phase[k][1]) + sum(phase[k][3])
         fft_launches += nphase_steps * 2 * plans[k]["fft_passes"]
     achieved = fft_flops / (fft_ms * 1e-3) / 1e12
-    # per two-operand product: 1 forward map (both operands), 2 x passes forward FFT
-    # launches (u and v on two streams), twist, passes inverse launches, back map,
-    # 3 carry kernels
-    launches = args.steps * sum(3 * plans[k]["fft_passes"] + 6 for k in kinds)
+    traffic = fft_traffic(plans, layouts, kinds)
+    # per two-operand product: 1 forward map (both operands; the full product's first
+    # forward pass forms its split itself), 2 x passes forward FFT launches (u and v on
+    # two streams), twist, passes inverse launches, back map, 3 carry kernels
+    launches = args.steps * sum(3 * plans[k]["fft_passes"] + (5 if k == "full" else 6)
+                                for k in kinds)
 
     # end to end through tm_mul_host with page-locked host buffers: every call moves
     # the operands host -> device and the product device -> host (the kernels read and
@@ -757,11 +785,13 @@ def run_cuda(args):
         "data": "synthetic", "config": workload_config(n, world),
         "roofline": {"bound": "alu", "kernel": "k_fft_pass", "achieved": sig(achieved),
                      "peak": sig(dfma_peak), "unit": "TFLOP/s", "frac": sig(achieved / dfma_peak),
-                     "traffic": None,
+                     "traffic": traffic,
                      "note": "FP64-bound FFT passes: 2.5 N log2 N flops per real transform, 3 "
                              "per product, over their device time (phase events); peak = FP64 "
                              "FMA rate measured in this run (tm_probe_dfma); nominal FP64 1.25; "
-                             "traffic not taken for the tuned plans"},
+                             "traffic = DRAM bytes of one step's FFT passes (one low, high and "
+                             "full product) from an ncu capture of these plans and layouts "
+                             "(cold caches), null when they differ"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 2 * nl * 8,
