@@ -452,8 +452,10 @@ int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
  * the paper's Section 5 picks N among its candidate lengths by their timings.
  * Candidates: every certified plan (worst-case bound within the target, so every
  * result stays exact) whose transform length is at most 1.15x the planner's, the
- * planner's first, at most 8. Each runs whole products on scratch operands on
- * `stream` (one warm-up, median of three, CUDA events); the fastest, if at least 1%
+ * planner's first, at most 8. Each candidate's FFT layout is tuned first
+ * (tm_autotune, which keeps the layout set for that transform length); then it runs
+ * whole products on scratch operands on `stream` (one warm-up, median of three, CUDA
+ * events); the fastest, if at least 1%
  * faster than the planner's (else the planner's), becomes the plan of (kind, n_bits)
  * for later calls in this process (tm_mul and the calls
  * built on it; tm_mul_static keeps the planner's). Low and full products do not

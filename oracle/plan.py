@@ -99,10 +99,32 @@ for _R in (3, 5, 7):
 # 13.12 U ||x12|| + 1.415 U |x0| + 1.733 U ||x||, at most 14.93 U ||x||, which is
 # 8.6213 U relative to sqrt3 ||x||, rounded up.
 LOCAL_L2["r3tw"] = 8.63
+# Radix 3 per output, directly. Output y1 = m + S i (sqrt3/2) d takes the twiddle
+# errors 3U (|x1| + |x2|), the rounding of t through the factor 1/2, of d, of the
+# constant and of its product each through sqrt3/2, the FMA m (|m| <= |x0| + |t|/2)
+# and the final addition (|y1| <= ||x||_1, an output of the DFT): on |x1|, |x2| at most
+# 3 + 1/2 + 3 sqrt3/2 + 1/2 + 1 = 7.598, on |x0| 2; y0 takes 3 + 1 + 1 on |x1|, |x2|.
+LOCAL_L1["r3tw"] = 7.6
+# Radix 5 (cos / sin of 2 pi / 5 and 4 pi / 5: c1, s1, c2, s2). Per output, y1 =
+# a1 + b1 with a1 = fma(c1, t1, fma(c2, t2, x0)), b1 = S i fma(s1, d1, s2 d2),
+# t_k, d_k the sums and differences of x_k and x_(5-k): on |x2|, |x3| the twiddles 3,
+# the roundings of t2 and d2 (|c2| + |s2|), the constants c2 and s2 (|c2| + |s2|),
+# the inner and outer FMAs (2 |c2|), the product s2 d2 and the FMA of b1 (2 |s2|), the
+# final addition 1: 9.588 in all, the largest coefficient of any output (y2: 9.04 on
+# |x2|, |x3|; y0: 6). In the 2-norm: the twiddles through the DFT, 3 sqrt5 ||x14||;
+# the roundings of t1, t2, d1, d2 enter the outputs along orthogonal columns of norm
+# sqrt(5/2), with ||(t, d)|| = sqrt2 ||x14||: sqrt5 ||x14||; the four constants
+# sqrt2 (|c1| + |c2|) ||t|| + sqrt2 (|s1| + |s2|) ||d|| <= 3.805 ||x14||; each FMA or
+# product rounding reaches two outputs (sqrt2) times the norm of the linear form it
+# rounds (Cauchy-Schwarz): 15.715 ||x|| for the eight; t1 + t2 for y0, 2 ||x14||; the
+# final roundings sqrt5 ||x||: at most 32.70 U ||x||, 14.62 U relative to sqrt5 ||x||.
+LOCAL_L1["r5tw"] = 9.59
+LOCAL_L2["r5tw"] = 14.63
 # The first stage of every pass (Ns = 1) multiplies by no twiddle. Its constants are
 # at least FIRST_STAGE_L2 / FIRST_STAGE_L1 below the twiddled ones: plain radix 4
-# has 2 / 2 against 6.3 / 6, radix 2 1 / 1 against 4 / 4, radix 3 5.65 / 5.83
-# against 8.63 / 10.07, radix 5 and 7 lose sqrt(R) sqrt2 3 U / sqrt2 3 U.
+# has 2 / 2 against 6.3 / 6, radix 2 1 / 1 against 4 / 4, radix 3 5.65 / 4.6 against
+# 8.63 / 7.6, radix 5 11.62 / 6.59 against 14.63 / 9.59 (the twiddle terms 3 sqrt5
+# ||x14|| and 3 drop), radix 7 loses sqrt7 sqrt2 3 U / sqrt2 3 U.
 FIRST_STAGE_L2 = 2.9
 FIRST_STAGE_L1 = 3.0
 TWIST = 20.0          # roundings of the twist, relative to ||x||_2 ||y||_2 (1 + eF)^2

@@ -1556,6 +1556,11 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
       std::lock_guard<std::mutex> lk(tmul::g_mu);
       tmul::g_params[key] = cands[c];
     }
+    // each candidate competes with its own best FFT layout: tune it first (the
+    // layouts stay set per transform length)
+    tm_tune lay;
+    rc = tm_autotune(kind, n_bits, stream, &lay);
+    if (rc) break;
     std::vector<float> t;
     for (int rep = 0; rep < 4 && rc == TM_OK; ++rep) {      // one warm-up, three timed
       cudaEventRecord(e0, s);

@@ -78,6 +78,9 @@ constexpr double kR2 = kMu + 1.0;       // radix 2 with a twiddle (both norms)
 constexpr double kR4tG = 6.3;           // tangent-form radix 4: 2-norm, (sqrt(112) + 2) / 2
 constexpr double kR4tD = 6.0;           // tangent-form radix 4: per output
 constexpr double kR3G = 8.63;           // radix 3 in the 2-norm, derived on its own
+constexpr double kR3D = 7.6;            // radix 3 per output: 3 + 1/2 + 3 sqrt3/2 + 1/2 + 1
+constexpr double kR5G = 14.63;          // radix 5 in the 2-norm, derived on its own
+constexpr double kR5D = 9.59;           // radix 5 per output (largest coefficient, on |x2|, |x3|)
 constexpr double kOuter = kMu;          // four-step twiddle product
 constexpr double kTwist = 20.0;         // twist + pointwise roundings, relative to ||x|| ||y||
 constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
@@ -85,11 +88,19 @@ constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
 // this much there (2-norm, per output).
 constexpr double kFirstG = 2.9;
 constexpr double kFirstD = 3.0;
-// radix R = 3, 5, 7 with twiddles, h = (R - 1) / 2 chained FMAs per output half:
-// per output sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt(R) times that (radix 3:
-// kR3G, from its own 2-norm analysis)
-double odd_delta(int R) { return std::sqrt(2.0) * (kMu + 2.0) + 2.0 * ((R - 1) / 2) + 1.0; }
-double odd_gamma(int R) { return R == 3 ? kR3G : std::sqrt(double(R)) * odd_delta(R); }
+// radix 7 with twiddles, h = 3 chained FMAs per output half: per output
+// sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt7 times that. Radix 3 and 5 take the
+// constants of their own analyses of the butterflies' operation sequences.
+double odd_delta(int R) {
+  if (R == 3) return kR3D;
+  if (R == 5) return kR5D;
+  return std::sqrt(2.0) * (kMu + 2.0) + 2.0 * ((R - 1) / 2) + 1.0;
+}
+double odd_gamma(int R) {
+  if (R == 3) return kR3G;
+  if (R == 5) return kR5G;
+  return std::sqrt(double(R)) * odd_delta(R);
+}
 
 // prod (1 + c u) over the radix stages (count[i] stages of constant c[i], the
 // constants in decreasing order), the first `firsts` of them discounted by `save`:

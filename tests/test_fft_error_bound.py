@@ -202,6 +202,149 @@ def test_radix3_two_norm_constant_brute_force():
           {k: (round(a, 3), round(b, 3)) for k, (a, b) in found.items()})
 
 
+def _round_model(eps):
+    """r(v, key): v with relative errors eps[key + "r"], eps[key + "i"] on its real and
+    imaginary parts (a componentwise rounding, to first order)."""
+    def r(v, key):
+        return complex(v.real * (1 + eps.get(key + "r", 0)), v.imag * (1 + eps.get(key + "i", 0)))
+    return r
+
+
+def _dft5_outputs(x, S, eps):
+    """dft5's operation sequence (sums and differences, two FMA chains per cosine
+    half, a product and an FMA per sine half, the final additions) with relative
+    errors eps on every rounding and on the four constants."""
+    r = _round_model(eps)
+    x0, x1, x2, x3, x4 = x
+    c1, c2 = math.cos(2 * math.pi / 5), math.cos(4 * math.pi / 5)
+    s1, s2 = math.sin(2 * math.pi / 5), math.sin(4 * math.pi / 5)
+    C1, C2 = c1 * (1 + eps.get("c1", 0)), c2 * (1 + eps.get("c2", 0))
+    S1, S2 = s1 * (1 + eps.get("s1", 0)), s2 * (1 + eps.get("s2", 0))
+    si = 1j * S
+    t1, t2 = r(x1 + x4, "t1"), r(x2 + x3, "t2")
+    d1, d2 = r(x1 - x4, "d1"), r(x2 - x3, "d2")
+    a1 = r(C1 * t1 + r(C2 * t2 + x0, "a1i"), "a1o")
+    a2 = r(C2 * t1 + r(C1 * t2 + x0, "a2i"), "a2o")
+    b1 = si * r(S1 * d1 + r(S2 * d2, "p1"), "b1")
+    b2 = si * r(S2 * d1 + r(-S1 * d2, "p2"), "b2")
+    y0 = r(x0 + r(t1 + t2, "s12"), "y0")
+    return np.array([y0, r(a1 + b1, "y1"), r(a2 + b2, "y2"), r(a2 - b2, "y3"), r(a1 - b1, "y4")])
+
+
+def _dft3_outputs(x, S, eps):
+    r = _round_model(eps)
+    x0, x1, x2 = x
+    k = math.sqrt(3) / 2 * (1 + eps.get("k", 0))
+    t = r(x1 + x2, "t")
+    m = r(x0 - t / 2, "m")
+    sd = 1j * S * r(r(x1 - x2, "d") * k, "p")
+    return np.array([r(x0 + t, "y0"), r(m + sd, "y1"), r(m - sd, "y2")])
+
+
+def _first_order_vectors(outputs, x, S, keys):
+    """Output-error vectors (complex, one per rounding) of a unit relative error at
+    each key, by a one-sided difference (the outputs are linear in each error)."""
+    base = outputs(x, S, {})
+    h = 2.0 ** -24
+    return np.array([(outputs(x, S, {key: h}) - base) / h for key in keys])
+
+
+def _keys(names, scalars=()):
+    return [n + c for n in names for c in ("r", "i")] + list(scalars)
+
+
+R5_KEYS = _keys(["t1", "t2", "d1", "d2", "a1i", "a1o", "a2i", "a2o", "p1", "b1", "p2", "b2",
+                 "s12", "y0", "y1", "y2", "y3", "y4"], ["c1", "c2", "s1", "s2"])
+R3_KEYS = _keys(["t", "m", "d", "p", "y0", "y1", "y2"], ["k"])
+
+
+def _worst_per_output(V, x, R, twiddled):
+    """max over outputs j of the largest first-order error of y_j over all rounding
+    errors in [-U, U] (max over directions phi of sum |Re(e^-i phi v_ij)|), plus the
+    twiddle products' 3 U |x_t| (t >= 1) aligned; relative to ||x||_1."""
+    phis = np.linspace(0, 2 * np.pi, 721)
+    rot = np.exp(-1j * phis)
+    tw = 3 * sum(abs(v) for v in x[1:]) if twiddled else 0.0
+    worst = max(float(np.max(np.abs(np.real(rot[:, None] * V[None, :, j])).sum(axis=1)))
+                for j in range(R))
+    return (worst + tw) / sum(abs(v) for v in x)
+
+
+def _worst_two_norm(V, x, R, twiddled, rng):
+    """A large ||sum theta_i v_i|| over signs theta (random starts, then single-sign
+    flips while they help), plus the twiddles' 3 sqrt(R) ||x_1..||; relative to
+    sqrt(R) ||x||. The exact maximum over 2^K patterns is out of reach for radix 5;
+    the derivation bounds every pattern."""
+    Vr = np.concatenate([V.real, V.imag], axis=1)
+    best = 0.0
+    for _ in range(12):
+        th = rng.choice([-1.0, 1.0], size=len(Vr))
+        val = np.linalg.norm(th @ Vr)
+        improved = True
+        while improved:
+            improved = False
+            for i in range(len(th)):
+                th[i] = -th[i]
+                nv = np.linalg.norm(th @ Vr)
+                if nv > val + 1e-15:
+                    val, improved = nv, True
+                else:
+                    th[i] = -th[i]
+        best = max(best, val)
+    tw = 3 * math.sqrt(R) * np.linalg.norm(x[1:]) if twiddled else 0.0
+    return (best + tw) / (math.sqrt(R) * np.linalg.norm(x))
+
+
+@pytest.mark.parametrize("R,outputs,keys,kind", [(5, _dft5_outputs, R5_KEYS, "r5tw"),
+                                                 (3, _dft3_outputs, R3_KEYS, "r3tw")],
+                         ids=["radix5", "radix3"])
+def test_odd_radix_constants_first_order(R, outputs, keys, kind):
+    """The radix-5 and radix-3 constants (per output LOCAL_L1, and for radix 5 the
+    2-norm LOCAL_L2), with and without twiddles, against the first-order error of the
+    butterfly's own operation sequence: per output the exact worst case over all
+    rounding errors, in the 2-norm a local search over sign patterns; inputs from
+    random starts improved by hill-climbing. A term dropped from the derivations
+    shows as an error above its constant."""
+    rng = np.random.default_rng(R)
+
+    def scores(v, tw):
+        x = v[:R] + 1j * v[R:]
+        V = _first_order_vectors(outputs, x, -1, keys)
+        return _worst_per_output(V, x, R, tw), (_worst_two_norm(V, x, R, tw, rng) if R == 5 else 0.0)
+
+    for tw in (True, False):
+        lim1 = P.LOCAL_L1[kind] - (0.0 if tw else P.FIRST_STAGE_L1)
+        lim2 = P.LOCAL_L2[kind] - (0.0 if tw else P.FIRST_STAGE_L2)
+        best1 = best2 = 0.0
+        x1 = x2 = None
+        for _ in range(40):
+            v = rng.normal(size=2 * R)
+            s1_, s2_ = scores(v, tw)
+            if s1_ > best1:
+                best1, x1 = s1_, v
+            if s2_ > best2:
+                best2, x2 = s2_, v
+        for target in (1, 2) if R == 5 else (1,):
+            xb = x1 if target == 1 else x2
+            step = 0.3
+            for _ in range(60):
+                v = xb + step * rng.normal(size=2 * R)
+                sc = scores(v, tw)[target - 1]
+                if sc > (best1 if target == 1 else best2):
+                    xb = v
+                    if target == 1:
+                        best1 = sc
+                    else:
+                        best2 = sc
+                else:
+                    step *= 0.95
+        assert best1 <= lim1, (kind, tw, best1, lim1)
+        assert best2 <= lim2, (kind, tw, best2, lim2)
+        two = f", 2-norm {best2:.3f} U (constant {lim2:.2f})" if R == 5 else ""
+        print(f"{kind} {'twiddled' if tw else 'first stage'}: per output {best1:.3f} U "
+              f"(constant {lim1:.2f}){two}")
+
+
 def test_first_stage_discount_is_conservative():
     """eta_conv with the discount taken from the dearest stages is at least eta_conv
     with the discount on any other choice of P stages (the layout decides which
