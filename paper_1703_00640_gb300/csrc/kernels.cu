@@ -28,7 +28,6 @@ constexpr double kS7_1 = 0x1.904c37505de4bp-1;    // sin(2 pi k/7)
 constexpr double kS7_2 = 0x1.f329c0558e969p-1;
 constexpr double kS7_3 = 0x1.bc4c04d71abc1p-2;
 constexpr double kSqrt3_2 = 0x1.bb67ae8584caap-1; // sqrt(3)/2
-constexpr double kSqrt1_2 = 0x1.6a09e667f3bcdp-1; // sqrt(1/2)
 
 // ------------------------------------------------------- complex helpers
 
@@ -869,26 +868,6 @@ template <>
 __device__ __forceinline__ void dft<4, -1>(double2* x) { dft4<-1>(x[0], x[1], x[2], x[3]); }
 template <>
 __device__ __forceinline__ void dft<4, 1>(double2* x) { dft4<1>(x[0], x[1], x[2], x[3]); }
-
-template <int S>
-__device__ __forceinline__ void dft8(double2* x) {
-  double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-  double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4<S>(e0, e1, e2, e3);
-  dft4<S>(o0, o1, o2, o3);
-  // omega^1 o1, omega^2 o2, omega^3 o3 with omega = exp(S 2 pi i / 8)
-  const double2 w1 = make_double2((o1.x - S * o1.y) * kSqrt1_2, (o1.y + S * o1.x) * kSqrt1_2);
-  const double2 w2 = mul_si<S>(o2);
-  const double2 w3 = make_double2((-o3.x - S * o3.y) * kSqrt1_2, (S * o3.x - o3.y) * kSqrt1_2);
-  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
-  x[1] = cadd(e1, w1); x[5] = csub(e1, w1);
-  x[2] = cadd(e2, w2); x[6] = csub(e2, w2);
-  x[3] = cadd(e3, w3); x[7] = csub(e3, w3);
-}
-template <>
-__device__ __forceinline__ void dft<8, -1>(double2* x) { dft8<-1>(x); }
-template <>
-__device__ __forceinline__ void dft<8, 1>(double2* x) { dft8<1>(x); }
 
 template <int S>
 __device__ __forceinline__ void dft3(double2* x) {

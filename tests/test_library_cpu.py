@@ -248,14 +248,14 @@ def test_plan_matches_oracle_plan_random_sizes(pkg):
 
 
 def test_dft_constants_are_the_nearest_doubles():
-    """The radix-3/5/7/8 DFT constants written in the kernels are the doubles
+    """The radix-3/5/7 DFT constants written in the kernels are the doubles
     nearest to cos / sin of 2 pi k / R (the FFT error bound takes each within
     2^-53 of its exact value)."""
     import hp_trig
     src = open(os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")).read()
-    vals = dict(re.findall(r"constexpr double (k[CS]\d_\d|kSqrt3_2|kSqrt1_2) = "
+    vals = dict(re.findall(r"constexpr double (k[CS]\d_\d|kSqrt3_2) = "
                            r"(-?0x[0-9a-fp.+-]+);", src))
-    want = {"kSqrt3_2": hp_trig.cossin_2pi(1, 3)[1], "kSqrt1_2": hp_trig.cossin_2pi(1, 8)[0]}
+    want = {"kSqrt3_2": hp_trig.cossin_2pi(1, 3)[1]}
     for R, count in ((5, 2), (7, 3)):
         for k in range(1, count + 1):
             c, s = hp_trig.cossin_2pi(k, R)
