@@ -77,9 +77,10 @@ extern "C" {
  * report TM_EPRECISION through every entry point while computing the same limbs.
  * Other values are ignored.
  * With TRUNCMUL_FAULT_BARRIER=1 (read once), the last CTA of every single-launch
- * product and persistent batch leaves at the first grid barrier without counting
- * itself in; the other CTAs' bounded waits (about a second) run out and the call
- * reports TM_ETIMEOUT, the device staying usable. */
+ * product leaves at the first grid barrier without counting itself in, and the first
+ * unit of every persistent batch is never reported as finished; the other
+ * CTAs' bounded waits (about a second) run out and the call reports TM_ETIMEOUT, the
+ * device staying usable. */
 
 /* ---- product kinds ---- */
 #define TM_FULL 0          /* Algorithm 1 */

@@ -18,10 +18,6 @@ namespace tmul {
 namespace {
 
 constexpr int kBranches = 12;  // concurrent graph branches
-// steps by which half of a persistent batch's work starts later (mixing one half's
-// FFT passes with the other half's maps and carries in each step); measured on the
-// 4096-product batch, a stagger of 5 steps gave the same time as none
-constexpr int kBatchStagger = 0;
 
 #define TB_CHECK(x)                                    \
   do {                                                 \
@@ -72,7 +68,7 @@ struct tm_batch {
   tmul::BatchArgs pargs{};
   int pgrid = 0;
   size_t psmem = 0;
-  bool sync_stale = false;       // a barrier wait timed out: zero the words first
+  size_t pcounter_bytes = 0;     // ticket and per-group counters, zeroed before each launch
 };
 
 namespace tmul {
@@ -365,9 +361,9 @@ SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
   return it;
 }
 
-// The persistent form: every group's phase arguments and the phase tables in device
-// memory, then one cooperative launch recorded as a one-node graph (a direct launch
-// per tm_batch_launch when the runtime cannot record it).
+// The persistent form: every group's phase arguments and the unit tables in device
+// memory, then one graph of two nodes, the counters' reset and one cooperative launch
+// (a reset and a direct launch per tm_batch_launch when the runtime cannot record it).
 int create_persistent(tm_batch* B, size_t groups_off, size_t start_off, size_t sync_off,
                       cudaStream_t s) {
   const int ng = int(B->groups.size());
@@ -381,77 +377,69 @@ int create_persistent(tm_batch* B, size_t groups_off, size_t start_off, size_t s
     const double N = double(B->groups[g].p.N);
     order[g] = {double(B->groups[g].members.size()) * N * (std::log2(N) + 8.0), g};
   }
-  // stagger: half of the estimated work starts kBatchStagger steps later, so that
-  // each step mixes one half's FFT passes with the other half's maps and carries
-  std::sort(order.rbegin(), order.rend());
-  std::vector<int> off(ng, 0);
-  double w0 = 0, w1 = 0;
-  for (const auto& o : order) {
-    if (w1 < w0) { off[o.second] = kBatchStagger; w1 += o.first; }
-    else w0 += o.first;
-  }
-  const int nsteps = kBatchPhases + kBatchStagger;
-  std::vector<int> step_seg(nsteps + 1, 0), seg_group, seg_phase;
-  std::vector<long long> seg_start(1, 0);
-  long long widest = 1;
-  for (int st = 0; st < nsteps; ++st) {
-    step_seg[st] = int(seg_group.size());
-    long long in_step = 0;
-    for (int g = 0; g < ng; ++g) {
-      const int ph = st - off[g];
-      if (ph < 0 || ph >= kBatchPhases || units[g][ph] == 0) continue;
+  std::sort(order.rbegin(), order.rend());             // largest estimated work first
+  // the unit list: phase by phase, each group's segment with the count of its units
+  // in earlier phases, which the segment's units wait for
+  std::vector<int> seg_group, seg_phase;
+  std::vector<long long> seg_start(1, 0), seg_wait, before(ng, 0);
+  for (int ph = 0; ph < kBatchPhases; ++ph)
+    for (const auto& o : order) {
+      const int g = o.second;
+      if (units[g][ph] == 0) continue;
       seg_group.push_back(g);
       seg_phase.push_back(ph);
+      seg_wait.push_back(before[g]);
       seg_start.push_back(seg_start.back() + units[g][ph]);
-      in_step += units[g][ph];
+      before[g] += units[g][ph];
     }
-    widest = std::max(widest, in_step);
-  }
-  step_seg[nsteps] = int(seg_group.size());
   const size_t nseg = seg_group.size();
-  // device copies: groups, then the step and segment tables
+  // device copies: groups, then the segment tables, then the counters
   BatchGroup* dg = reinterpret_cast<BatchGroup*>(B->mem + groups_off);
   char* tab = B->mem + start_off;
-  int* d_step = reinterpret_cast<int*>(tab);
-  long long* d_start = reinterpret_cast<long long*>(tab + align_up((nsteps + 1) * sizeof(int)));
-  int* d_group = reinterpret_cast<int*>(reinterpret_cast<char*>(d_start) +
-                                        align_up((nseg + 1) * sizeof(long long)));
+  long long* d_start = reinterpret_cast<long long*>(tab);
+  long long* d_wait = reinterpret_cast<long long*>(tab + align_up((nseg + 1) * sizeof(long long)));
+  int* d_group = reinterpret_cast<int*>(reinterpret_cast<char*>(d_wait) +
+                                        align_up(nseg * sizeof(long long) + 8));
   int* d_phase = reinterpret_cast<int*>(reinterpret_cast<char*>(d_group) +
                                         align_up(nseg * sizeof(int) + 4));
-  unsigned* sync = reinterpret_cast<unsigned*>(B->mem + sync_off);
+  unsigned* counters = reinterpret_cast<unsigned*>(B->mem + sync_off);   // ticket, done[ng]
   if (ng) TB_CHECK(cudaMemcpyAsync(dg, gs.data(), ng * sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
-  TB_CHECK(cudaMemcpyAsync(d_step, step_seg.data(), step_seg.size() * sizeof(int),
-                           cudaMemcpyHostToDevice, s));
   TB_CHECK(cudaMemcpyAsync(d_start, seg_start.data(), seg_start.size() * sizeof(long long),
                            cudaMemcpyHostToDevice, s));
   if (nseg) {
+    TB_CHECK(cudaMemcpyAsync(d_wait, seg_wait.data(), nseg * sizeof(long long),
+                             cudaMemcpyHostToDevice, s));
     TB_CHECK(cudaMemcpyAsync(d_group, seg_group.data(), nseg * sizeof(int),
                              cudaMemcpyHostToDevice, s));
     TB_CHECK(cudaMemcpyAsync(d_phase, seg_phase.data(), nseg * sizeof(int),
                              cudaMemcpyHostToDevice, s));
   }
-  TB_CHECK(cudaMemsetAsync(sync, 0, 8, s));
   TB_CHECK(cudaStreamSynchronize(s));
   const int resident = batch_max_blocks(smem);
   if (resident <= 0) return TM_ECUDA;
   B->pargs.groups = dg;
   B->pargs.ngroups = ng;
-  B->pargs.nsteps = nsteps;
-  B->pargs.step_seg = d_step;
+  B->pargs.nseg = int(nseg);
+  B->pargs.total = seg_start.back();
   B->pargs.seg_start = d_start;
   B->pargs.seg_group = d_group;
   B->pargs.seg_phase = d_phase;
-  B->pargs.sync = sync;
+  B->pargs.seg_wait = d_wait;
+  B->pargs.ticket = counters;
+  B->pargs.done = counters + 1;
   B->pargs.status = B->status;
-  B->pargs.leave_barrier = fault_leave_barrier() ? 1 : 0;
-  B->pgrid = int(std::min<long long>(widest, resident));
+  B->pargs.withhold = fault_leave_barrier() ? 1 : 0;
+  B->pcounter_bytes = size_t(ng + 1) * sizeof(unsigned);
+  B->pgrid = int(std::min<long long>(seg_start.back(), resident));
   B->psmem = smem;
   if (ng == 0) return TM_OK;
+  // one graph: zero the counters, then the launch
   cudaStream_t cs;
   TB_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (ce == cudaSuccess) {
-    const cudaError_t le = launch_batch_persistent(B->pargs, B->pgrid, B->psmem, cs);
+    cudaError_t le = cudaMemsetAsync(counters, 0, B->pcounter_bytes, cs);
+    if (le == cudaSuccess) le = launch_batch_persistent(B->pargs, B->pgrid, B->psmem, cs);
     ce = cudaStreamEndCapture(cs, &B->graph);
     if (le == cudaSuccess && ce == cudaSuccess) ce = cudaGraphInstantiate(&B->exec, B->graph, 0);
     else if (ce == cudaSuccess) ce = le;
@@ -543,10 +531,10 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
   const size_t pgroups_off = total;
   const size_t pstart_off = pgroups_off + align_up(ng * sizeof(BatchGroup));
   const size_t nseg_max = size_t(kBatchPhases) * ng;
-  const size_t psync_off = pstart_off + align_up((kBatchPhases + kBatchStagger + 1) * sizeof(int)) +
-                           align_up((nseg_max + 1) * sizeof(long long)) +
+  const size_t psync_off = pstart_off + align_up((nseg_max + 1) * sizeof(long long)) +
+                           align_up(nseg_max * sizeof(long long) + 8) +
                            2 * align_up(nseg_max * sizeof(int) + 4);
-  if (B->persistent) total = psync_off + 256;
+  if (B->persistent) total = psync_off + align_up((ng + 1) * sizeof(unsigned)) + 256;
   TB_CHECK(cudaMalloc(&B->mem, total));
   B->status = reinterpret_cast<DevStatus*>(B->mem);
   TB_CHECK(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), s));
@@ -654,16 +642,14 @@ int tm_batch_launch(tm_batch* batch, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (batch->persistent) {
     if (batch->pargs.ngroups == 0) return TM_OK;
-    if (batch->sync_stale) {
-      if (cudaMemsetAsync(batch->pargs.sync, 0, 8, s) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return TM_ECUDA;
-      }
-      batch->sync_stale = false;
+    cudaError_t e = cudaSuccess;
+    if (batch->exec) {
+      e = cudaGraphLaunch(batch->exec, s);
+    } else {                           // the recorded graph zeroes the counters itself
+      e = cudaMemsetAsync(batch->pargs.ticket, 0, batch->pcounter_bytes, s);
+      if (e == cudaSuccess)
+        e = tmul::launch_batch_persistent(batch->pargs, batch->pgrid, batch->psmem, s);
     }
-    const cudaError_t e = batch->exec ? cudaGraphLaunch(batch->exec, s)
-                                      : tmul::launch_batch_persistent(batch->pargs, batch->pgrid,
-                                                                      batch->psmem, s);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       return TM_ECUDA;
@@ -683,7 +669,6 @@ int tm_batch_status(tm_batch* batch, void* stream, tm_report* rep) {
   if (!batch) return TM_EINVAL;
   const int rc = tmul::read_status(static_cast<cudaStream_t>(stream), batch->status, rep);
   if (rep) rep->e_max = batch->e_max_min;
-  if (rc == TM_ETIMEOUT) batch->sync_stale = true;
   return rc;
 }
 

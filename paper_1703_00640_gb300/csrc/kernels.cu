@@ -2146,43 +2146,63 @@ __device__ void batch_unit(int ph, const BatchGroup& B, long long local, FwdShar
   }
 }
 
-// Every product of a batch in one cooperative launch: each step runs one phase (maps,
-// an FFT pass, twist, back map or a carry step) of each of its groups, block v of the
-// step on CTA v mod grid, then a grid barrier; a group's phases come in order in
-// consecutive steps. The block bodies are the per-phase kernels'.
+// Every product of a batch in one cooperative launch. The units (the virtual blocks of
+// each group's maps, FFT passes, twist, back map and carry steps) are taken in list
+// order by ticket; each waits, bounded by the global timer, until its group's
+// earlier phases have finished, so groups advance independently and no grid-wide
+// barrier is needed. The block bodies are the per-phase kernels'.
 __global__ void __launch_bounds__(kFusedThreads, 2) k_batch_persistent(BatchArgs A) {
   __shared__ FwdShared fsh;
   // the unit's group descriptor, staged in shared memory: the block bodies copy
   // their argument structs per thread, and shared-memory reads of one address
   // are broadcast to the warp
   __shared__ __align__(16) unsigned long long gsh[(sizeof(BatchGroup) + 7) / 8];
-  __shared__ int s_group;
-  const unsigned G = gridDim.x;
+  __shared__ int s_group, s_ok;
+  __shared__ long long s_v;
   if (threadIdx.x == 0) s_group = -1;
-  __syncthreads();
-  for (int step = 0; step < A.nsteps; ++step) {
-    const int a = A.step_seg[step], b = A.step_seg[step + 1];
-    if (a == b) continue;
-    const long long base = A.seg_start[a];
-    const long long total = A.seg_start[b] - base;
-    for (long long v = blockIdx.x; v < total; v += G) {
-      const int k = batch_segment_of(A.seg_start, a, b, base + v);
-      const int g = A.seg_group[k];
-      if (g != s_group) {                 // uniform: every thread reads the same s_group
-        __syncthreads();
-        const unsigned long long* src =
-            reinterpret_cast<const unsigned long long*>(A.groups + g);
-        for (int t = threadIdx.x; t < int((sizeof(BatchGroup) + 7) / 8); t += blockDim.x)
-          gsh[t] = src[t];
-        __syncthreads();
-        if (threadIdx.x == 0) s_group = g;
+  for (;;) {
+    if (threadIdx.x == 0) s_v = (long long)atomicAdd(A.ticket, 1u);
+    __syncthreads();
+    const long long v = s_v;
+    if (v >= A.total) break;                          // uniform
+    const int k = batch_segment_of(A.seg_start, 0, A.nseg, v);
+    const int g = A.seg_group[k];
+    if (threadIdx.x == 0) {
+      // the group's earlier phases: their units were taken before this one by CTAs
+      // that are resident, so the wait ends; it is bounded all the same
+      const long long need = A.seg_wait[k];
+      const volatile unsigned* d = A.done + g;
+      int ok = 1;
+      if ((long long)*d < need) {
+        const unsigned long long t0 = global_ns();
+        while ((long long)*d < need) {
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicOr(&A.status->flags, kFlagTimeout);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
       }
-      batch_unit(A.seg_phase[k], *reinterpret_cast<const BatchGroup*>(gsh),
-                 base + v - A.seg_start[k], fsh);
-      __syncthreads();
+      __threadfence();
+      s_ok = ok;
     }
-    const bool leave = A.leave_barrier && blockIdx.x == gridDim.x - 1;
-    if (step < A.nsteps - 1 && !grid_barrier(A.sync, A.status, leave)) return;
+    __syncthreads();
+    if (!s_ok) return;                                // uniform
+    if (g != s_group) {                               // uniform: every thread reads s_group
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.groups + g);
+      for (int t = threadIdx.x; t < int((sizeof(BatchGroup) + 7) / 8); t += blockDim.x)
+        gsh[t] = src[t];
+      __syncthreads();
+      if (threadIdx.x == 0) s_group = g;
+    }
+    batch_unit(A.seg_phase[k], *reinterpret_cast<const BatchGroup*>(gsh), v - A.seg_start[k],
+               fsh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();                                // the unit's writes, then its count
+      if (!(A.withhold && v == 0)) atomicAdd(A.done + g, 1u);
+    }
   }
 }
 

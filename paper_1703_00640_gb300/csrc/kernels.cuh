@@ -222,17 +222,24 @@ struct BatchGroup {
 // segments [step_seg[s], step_seg[s+1]); segment k is phase seg_phase[k] of group
 // seg_group[k], its virtual blocks numbered from seg_start[k] (a running sum over all
 // segments). Staggering the groups' phases mixes FFT passes with maps and carries.
+// The batch as one launch: the virtual blocks ("units") of every (group, phase)
+// segment in one list, phases in order and the largest groups first within a phase.
+// CTAs take units by ticket; a unit of phase p of group g starts once every unit of
+// g's earlier phases has finished (seg_wait of them), so groups move through their
+// phases independently.
 struct BatchArgs {
   const BatchGroup* groups;
   int ngroups;
-  int nsteps;
-  const int* step_seg;
-  const long long* seg_start;
+  int nseg;
+  long long total;               // units of all segments
+  const long long* seg_start;    // first unit of each segment (nseg + 1 entries)
   const int* seg_group;
   const int* seg_phase;
-  unsigned* sync;                // grid barrier words (zeroed at creation)
+  const long long* seg_wait;     // units of the segment's group in earlier phases
+  unsigned* ticket;              // next unit; zeroed before each launch
+  unsigned* done;                // finished units per group; zeroed before each launch
   DevStatus* status;
-  int leave_barrier;             // fault injection: the last CTA leaves at the first barrier
+  int withhold;                  // fault injection: unit 0 is never reported as finished
 };
 int batch_max_blocks(size_t smem);
 cudaError_t launch_batch_persistent(const BatchArgs& a, int grid, size_t smem, cudaStream_t s);

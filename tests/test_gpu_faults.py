@@ -185,9 +185,10 @@ print(json.dumps(res))
 
 
 def test_barrier_timeout_is_reported_and_the_device_stays_usable(pkg):
-    """TRUNCMUL_FAULT_BARRIER=1: the last CTA of a single-launch product and of a
-    persistent batch leaves at the first grid barrier; the others' bounded waits
-    run out (about a second) and the calls report TM_ETIMEOUT. A per-phase product
+    """TRUNCMUL_FAULT_BARRIER=1: the last CTA of a single-launch product leaves at
+    the first grid barrier, and the first unit of a persistent batch is never
+    reported as finished; the others' bounded waits run out (about a second) and the
+    calls report TM_ETIMEOUT. A per-phase product
     in the same process afterwards succeeds with the exact limbs."""
     env = dict(os.environ)
     env["TRUNCMUL_FAULT_BARRIER"] = "1"
