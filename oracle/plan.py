@@ -120,11 +120,24 @@ LOCAL_L1["r3tw"] = 7.6
 # final roundings sqrt5 ||x||: at most 32.70 U ||x||, 14.62 U relative to sqrt5 ||x||.
 LOCAL_L1["r5tw"] = 9.59
 LOCAL_L2["r5tw"] = 14.63
+# Radix 7 in the same way (a_m = x0 + sum_k C_mk t_k by three chained FMAs, innermost
+# k = 3; b_m = S i sum_k S_mk d_k by a product and two FMAs). Per output, over each pair
+# (x_k, x_(7-k)): the twiddles 3, the rounding of t_k and d_k and the errors of the two
+# constants 2 (|C_mk| + |S_mk|), every FMA or product whose form contains t_k or d_k
+# |C_mk| or |S_mk| each, the final addition 1: at most 11.027 (on x0: 4; y0: 7). In the
+# 2-norm: twiddles 3 sqrt7 ||x16||; t, d roundings along six orthogonal columns of
+# norm sqrt(7/2), sqrt7 ||x16||; the six constants, each meeting every t_k (or d_k)
+# once, sqrt2 (sum |c| ||t|| + sum |s| ||d||) <= 4.98 ||x16||; the eighteen FMA and
+# product roundings, sqrt2 times the norms of their forms, 39.55 ||x||; y0's two
+# partial sums 2 + sqrt6; the final roundings sqrt7 ||x||: 62.50 U ||x||, 23.622 U
+# relative to sqrt7 ||x||.
+LOCAL_L1["r7tw"] = 11.03
+LOCAL_L2["r7tw"] = 23.63
 # The first stage of every pass (Ns = 1) multiplies by no twiddle. Its constants are
 # at least FIRST_STAGE_L2 / FIRST_STAGE_L1 below the twiddled ones: plain radix 4
 # has 2 / 2 against 6.3 / 6, radix 2 1 / 1 against 4 / 4, radix 3 5.65 / 4.6 against
-# 8.63 / 7.6, radix 5 11.62 / 6.59 against 14.63 / 9.59 (the twiddle terms 3 sqrt5
-# ||x14|| and 3 drop), radix 7 loses sqrt7 sqrt2 3 U / sqrt2 3 U.
+# 8.63 / 7.6, radix 5 11.62 / 6.59 against 14.63 / 9.59, radix 7 20.62 / 8.03 against
+# 23.63 / 11.03 (the twiddle terms, 3 sqrt(R) ||x_1..|| and 3, drop).
 FIRST_STAGE_L2 = 2.9
 FIRST_STAGE_L1 = 3.0
 TWIST = 20.0          # roundings of the twist, relative to ||x||_2 ||y||_2 (1 + eF)^2

@@ -81,6 +81,8 @@ constexpr double kR3G = 8.63;           // radix 3 in the 2-norm, derived on its
 constexpr double kR3D = 7.6;            // radix 3 per output: 3 + 1/2 + 3 sqrt3/2 + 1/2 + 1
 constexpr double kR5G = 14.63;          // radix 5 in the 2-norm, derived on its own
 constexpr double kR5D = 9.59;           // radix 5 per output (largest coefficient, on |x2|, |x3|)
+constexpr double kR7G = 23.63;          // radix 7 in the 2-norm, derived on its own
+constexpr double kR7D = 11.03;          // radix 7 per output
 constexpr double kOuter = kMu;          // four-step twiddle product
 constexpr double kTwist = 20.0;         // twist + pointwise roundings, relative to ||x|| ||y||
 constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
@@ -88,19 +90,10 @@ constexpr double kSlack = 1.0 + 1.0 / (1 << 20);   // second-order terms
 // this much there (2-norm, per output).
 constexpr double kFirstG = 2.9;
 constexpr double kFirstD = 3.0;
-// radix 7 with twiddles, h = 3 chained FMAs per output half: per output
-// sqrt2 (mu + 2) + 2h + 1, in the 2-norm sqrt7 times that. Radix 3 and 5 take the
-// constants of their own analyses of the butterflies' operation sequences.
-double odd_delta(int R) {
-  if (R == 3) return kR3D;
-  if (R == 5) return kR5D;
-  return std::sqrt(2.0) * (kMu + 2.0) + 2.0 * ((R - 1) / 2) + 1.0;
-}
-double odd_gamma(int R) {
-  if (R == 3) return kR3G;
-  if (R == 5) return kR5G;
-  return std::sqrt(double(R)) * odd_delta(R);
-}
+// radix 3, 5 and 7 with twiddles: the constants of the analyses of the butterflies'
+// own operation sequences
+double odd_delta(int R) { return R == 3 ? kR3D : (R == 5 ? kR5D : kR7D); }
+double odd_gamma(int R) { return R == 3 ? kR3G : (R == 5 ? kR5G : kR7G); }
 
 // prod (1 + c u) over the radix stages (count[i] stages of constant c[i], the
 // constants in decreasing order), the first `firsts` of them discounted by `save`:

@@ -231,6 +231,29 @@ def _dft5_outputs(x, S, eps):
     return np.array([y0, r(a1 + b1, "y1"), r(a2 + b2, "y2"), r(a2 - b2, "y3"), r(a1 - b1, "y4")])
 
 
+def _dft7_outputs(x, S, eps):
+    """dft7's operation sequence: sums and differences, a_m by three chained FMAs
+    (innermost k = 3), b_m by a product (k = 3) and two FMAs, y0 = x0 + (t1 + (t2 + t3)),
+    the final additions; relative errors eps on every rounding and constant."""
+    r = _round_model(eps)
+    x0 = x[0]
+    c = [math.cos(2 * math.pi * k / 7) * (1 + eps.get(f"c{k}", 0)) for k in (1, 2, 3)]
+    s_ = [math.sin(2 * math.pi * k / 7) * (1 + eps.get(f"s{k}", 0)) for k in (1, 2, 3)]
+    cm = {1: (c[0], c[1], c[2]), 2: (c[1], c[2], c[0]), 3: (c[2], c[0], c[1])}
+    sm = {1: (s_[0], s_[1], s_[2]), 2: (s_[1], -s_[2], -s_[0]), 3: (s_[2], -s_[0], s_[1])}
+    t = [r(x[k] + x[7 - k], f"t{k}") for k in (1, 2, 3)]
+    d = [r(x[k] - x[7 - k], f"d{k}") for k in (1, 2, 3)]
+    si = 1j * S
+    y = [None] * 7
+    for m in (1, 2, 3):
+        C, Sn = cm[m], sm[m]
+        a = r(C[0] * t[0] + r(C[1] * t[1] + r(C[2] * t[2] + x0, f"a{m}i"), f"a{m}m"), f"a{m}o")
+        b = si * r(Sn[0] * d[0] + r(Sn[1] * d[1] + r(Sn[2] * d[2], f"p{m}"), f"b{m}i"), f"b{m}o")
+        y[m], y[7 - m] = r(a + b, f"y{m}"), r(a - b, f"y{7 - m}")
+    y[0] = r(x0 + r(t[0] + r(t[1] + t[2], "s23"), "s123"), "y0")
+    return np.array(y)
+
+
 def _dft3_outputs(x, S, eps):
     r = _round_model(eps)
     x0, x1, x2 = x
@@ -256,6 +279,11 @@ def _keys(names, scalars=()):
 R5_KEYS = _keys(["t1", "t2", "d1", "d2", "a1i", "a1o", "a2i", "a2o", "p1", "b1", "p2", "b2",
                  "s12", "y0", "y1", "y2", "y3", "y4"], ["c1", "c2", "s1", "s2"])
 R3_KEYS = _keys(["t", "m", "d", "p", "y0", "y1", "y2"], ["k"])
+R7_KEYS = _keys([f"{v}{k}" for v in "td" for k in (1, 2, 3)]
+                + [f"a{m}{w}" for m in (1, 2, 3) for w in "imo"]
+                + [f"{v}{m}{w}" for m in (1, 2, 3) for v, w in (("p", ""), ("b", "i"), ("b", "o"))]
+                + ["s23", "s123"] + [f"y{j}" for j in range(7)],
+                [f"{v}{k}" for v in "cs" for k in (1, 2, 3)])
 
 
 def _worst_per_output(V, x, R, twiddled):
@@ -296,10 +324,11 @@ def _worst_two_norm(V, x, R, twiddled, rng):
 
 
 @pytest.mark.parametrize("R,outputs,keys,kind", [(5, _dft5_outputs, R5_KEYS, "r5tw"),
+                                                 (7, _dft7_outputs, R7_KEYS, "r7tw"),
                                                  (3, _dft3_outputs, R3_KEYS, "r3tw")],
-                         ids=["radix5", "radix3"])
+                         ids=["radix5", "radix7", "radix3"])
 def test_odd_radix_constants_first_order(R, outputs, keys, kind):
-    """The radix-5 and radix-3 constants (per output LOCAL_L1, and for radix 5 the
+    """The radix-3, 5 and 7 constants (per output LOCAL_L1, and for radix 5 and 7 the
     2-norm LOCAL_L2), with and without twiddles, against the first-order error of the
     butterfly's own operation sequence: per output the exact worst case over all
     rounding errors, in the 2-norm a local search over sign patterns; inputs from
@@ -310,7 +339,7 @@ def test_odd_radix_constants_first_order(R, outputs, keys, kind):
     def scores(v, tw):
         x = v[:R] + 1j * v[R:]
         V = _first_order_vectors(outputs, x, -1, keys)
-        return _worst_per_output(V, x, R, tw), (_worst_two_norm(V, x, R, tw, rng) if R == 5 else 0.0)
+        return _worst_per_output(V, x, R, tw), (_worst_two_norm(V, x, R, tw, rng) if R > 3 else 0.0)
 
     for tw in (True, False):
         lim1 = P.LOCAL_L1[kind] - (0.0 if tw else P.FIRST_STAGE_L1)
@@ -324,7 +353,7 @@ def test_odd_radix_constants_first_order(R, outputs, keys, kind):
                 best1, x1 = s1_, v
             if s2_ > best2:
                 best2, x2 = s2_, v
-        for target in (1, 2) if R == 5 else (1,):
+        for target in (1, 2) if R > 3 else (1,):
             xb = x1 if target == 1 else x2
             step = 0.3
             for _ in range(60):
@@ -340,7 +369,7 @@ def test_odd_radix_constants_first_order(R, outputs, keys, kind):
                     step *= 0.95
         assert best1 <= lim1, (kind, tw, best1, lim1)
         assert best2 <= lim2, (kind, tw, best2, lim2)
-        two = f", 2-norm {best2:.3f} U (constant {lim2:.2f})" if R == 5 else ""
+        two = f", 2-norm {best2:.3f} U (constant {lim2:.2f})" if R > 3 else ""
         print(f"{kind} {'twiddled' if tw else 'first stage'}: per output {best1:.3f} U "
               f"(constant {lim1:.2f}){two}")
 
