@@ -43,10 +43,10 @@ METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50
 # the keys, built from the kernel source with this SHA-256. roofline.traffic reports their
 # sum only while the timed plans, layouts and kernel source are these; otherwise null.
 FFT_DRAM_CAPTURE = {
-    "kernels_sha256": "ef680a74a2c8317034977753955f019b4f03bc5f93face6e1e56ca9bc8c0ce30",
-    "bytes": {("lo", 8, 2097152, "1024:0:0"): 151393280,
-              ("hi", 8, 2359296, "1024:2:0"): 170408448,
-              ("full", 12, 2949120, "1024:0:0"): 170081792},
+    "kernels_sha256": "108dd3bd0270c5ff214c27c29f1fed82cb197c7ac49ed5aed65fd19caf3bcec2",
+    "bytes": {("lo", 8, 2097152, "1024:0:0"): 151422720,
+              ("hi", 8, 2293760, "1024:0:0"): 165637888,
+              ("full", 12, 2949120, "1024:0:0"): 170102784},
 }
 
 
