@@ -414,7 +414,8 @@ def test_twiddle_product_within_constant():
 
 CONV_CASES = [(8, None), (12, None), (20, None), (28, None), (40, None), (56, None),
               (96, (4, 12)), (120, (12, 5)), (168, (12, 7)), (256, (8, 16)),
-              (420, (14, 15))]
+              (420, (14, 15)), (250, None), (486, (27, 9)), (686, (7, 49)),
+              (1250, (25, 25))]
 
 
 @pytest.mark.parametrize("N,split", CONV_CASES, ids=[f"N{n}" for n, _ in CONV_CASES])
