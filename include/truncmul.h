@@ -123,6 +123,10 @@ typedef struct tm_report {
  * Algorithm 2, Theorem 2.2, Proposition 3.1; high product - Algorithm 3,
  * Theorem 2.3, Proposition 4.1 (the result is the returned round(t), rounding
  * half up, which is one of the at most two admissible values).
+ * Execution: products whose complex transform length N/2 is at most 640 run whole
+ * in one CTA (one launch); larger ones as the per-phase launch sequence (maps, FFT
+ * passes, twist, back map, carry scan). tm_set_fused selects other forms. The
+ * results are the same limbs either way.
  */
 int tm_mul_full(uint64_t* out, const uint64_t* u, const uint64_t* v, uint64_t n_bits,
                 void* stream, tm_report* rep);

@@ -309,6 +309,28 @@ BatchGroup batch_group(tm_batch* B, const Group& g, size_t* smem) {
 
 }  // namespace
 
+SmallItem small_item_for(const void* out, const void* u, const void* v, uint64_t n,
+                         const PlanParams& q, int plan) {
+  SmallItem it{};
+  it.u = static_cast<const unsigned long long*>(u);
+  it.v = static_cast<const unsigned long long*>(v);
+  it.out = static_cast<unsigned long long*>(const_cast<void*>(out));
+  it.n = n;
+  it.nlimbs = limbs_of(n);
+  it.nd = q.n_digits;
+  it.s0 = int64_t(q.N + 1) * q.b - int64_t(n);
+  int64_t nS, shift, rbit;
+  carry_shape(q, &nS, &shift, &rbit);
+  it.nS = nS;
+  it.round_bit = rbit;
+  it.shift_bits = shift;
+  it.nout = out_limbs(q.kind, n);
+  it.top_mask = (q.kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
+  it.emax_fx = emax_fixed(q.limit > 0.0 ? q.limit : q.e_max);
+  it.plan = plan;
+  return it;
+}
+
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
   SmallPlan sp{};
   const FftPass& fp = pe.fft.pass[0];
@@ -338,28 +360,6 @@ SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe) {
 }
 
 namespace {
-
-SmallItem small_item_of(const tm_desc& d, const PlanParams& q, int plan) {
-  SmallItem it{};
-  const uint64_t n = d.n_bits;
-  it.u = reinterpret_cast<const unsigned long long*>(d.u);
-  it.v = reinterpret_cast<const unsigned long long*>(d.v);
-  it.out = reinterpret_cast<unsigned long long*>(d.out);
-  it.n = n;
-  it.nlimbs = limbs_of(n);
-  it.nd = q.n_digits;
-  it.s0 = int64_t(q.N + 1) * q.b - int64_t(n);
-  int64_t nS, shift, rbit;
-  carry_shape(q, &nS, &shift, &rbit);
-  it.nS = nS;
-  it.round_bit = rbit;
-  it.shift_bits = shift;
-  it.nout = out_limbs(q.kind, n);
-  it.top_mask = (q.kind == TM_LO && n % 64) ? ((1ull << (n % 64)) - 1ull) : ~0ull;
-  it.emax_fx = emax_fixed(q.e_max);
-  it.plan = plan;
-  return it;
-}
 
 // The persistent form: every group's phase arguments and the unit tables in device
 // memory, then one graph of two nodes, the counters' reset and one cooperative launch
@@ -515,7 +515,8 @@ int create(tm_batch** out, const tm_desc* descs, uint32_t count, cudaStream_t s)
                                small_smem_bytes(q.N, pe->M, fp.tw4_len, fp.need_wL));
       it = small_index.find(key);
     }
-    small_items.push_back(small_item_of(B->descs[i], q, it->second));
+    small_items.push_back(small_item_for(B->descs[i].out, B->descs[i].u, B->descs[i].v,
+                                          B->descs[i].n_bits, q, it->second));
   }
   // device memory: status word, CTA-resident items and plans, one region per group
   size_t total = 256;

@@ -2285,18 +2285,26 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_products(SmallArgs A
   __shared__ double s_theta[2], s_top[2];
   __shared__ double Pw[kMaxLam];
   __shared__ double Hh[kMaxLam + 64 + 1];
+  // the current product's descriptor and plan, staged in shared memory (from the
+  // arrays of a batch, or from the arguments for one product)
+  __shared__ SmallItem s_it;
+  __shared__ SmallPlan s_plan;
   const int tid = threadIdx.x;
-  for (;;) {
+  for (int round = 0;; ++round) {
     if (tid == 0) {
-      s_item = atomicAdd(A.counter, 1);
+      s_item = A.items ? atomicAdd(A.counter, 1) : (round == 0 ? 0 : A.count);
       s_bmax = 0;
       s_flags = 0;
+      if (s_item < A.count) {
+        s_it = A.items ? A.items[s_item] : A.item0;
+        s_plan = A.items ? A.plans[s_it.plan] : A.plan0;
+      }
     }
     __syncthreads();
     const int idx = s_item;
     if (idx >= A.count) return;                       // uniform
-    const SmallItem& it = A.items[idx];
-    const SmallPlan& P = A.plans[it.plan];
+    const SmallItem& it = s_it;
+    const SmallPlan& P = s_plan;
     const int kind = P.kind, b = P.b;
     const int N = int(P.N), M = int(P.M);
     double2* Z = sm;

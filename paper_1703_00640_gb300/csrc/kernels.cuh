@@ -283,11 +283,13 @@ struct SmallItem {
 };
 
 struct SmallArgs {
-  const SmallItem* items;
+  const SmallItem* items;        // nullptr: the one product item0 of plan plan0
   int count;
   const SmallPlan* plans;
-  int* counter;                  // next item to take (zeroed before the launch)
+  int* counter;                  // next item to take (zeroed before the launch; unused for one)
   DevStatus* status;
+  SmallItem item0;
+  SmallPlan plan0;
 };
 
 // shared memory a CTA-resident product of this plan needs

@@ -103,6 +103,9 @@ int enqueue_transform(int kind, const uint64_t* v, uint64_t n, cudaStream_t s,
                       double* theta);
 // Single-pass plan tables of a CTA-resident product, and its per-product item.
 SmallPlan small_plan_of(const PlanParams& p, const PlanEntry& pe);
+// The CTA-resident kernel's descriptor of one product (plan index `plan`).
+SmallItem small_item_for(const void* out, const void* u, const void* v, uint64_t n,
+                         const PlanParams& q, int plan);
 // Waits for s, reads the status word into *rep and resets it. may_allocate = false
 // keeps to calls that allocate nothing (no page-locked status buffer).
 int read_status(cudaStream_t s, DevStatus* status, tm_report* rep, bool may_allocate = true);

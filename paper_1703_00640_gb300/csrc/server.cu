@@ -100,28 +100,6 @@ int init_slot(Slot& sl) {
   return TM_OK;
 }
 
-SmallItem small_item(const Request& r, int plan) {
-  SmallItem it{};
-  const PlanParams& q = r.p;
-  it.u = reinterpret_cast<const unsigned long long*>(r.u);
-  it.v = reinterpret_cast<const unsigned long long*>(r.v);
-  it.out = reinterpret_cast<unsigned long long*>(r.out);
-  it.n = r.n;
-  it.nlimbs = limbs_of(r.n);
-  it.nd = q.n_digits;
-  it.s0 = int64_t(q.N + 1) * q.b - int64_t(r.n);
-  int64_t nS, shift, rbit;
-  carry_shape(q, &nS, &shift, &rbit);
-  it.nS = nS;
-  it.round_bit = rbit;
-  it.shift_bits = shift;
-  it.nout = out_limbs(q.kind, r.n);
-  it.top_mask = (q.kind == TM_LO && r.n % 64) ? ((1ull << (r.n % 64)) - 1ull) : ~0ull;
-  it.emax_fx = emax_fixed(q.e_max);
-  it.plan = plan;
-  return it;
-}
-
 // Retires finished slots into S->done.
 void retire(tm_server* S) {
   for (Slot& sl : S->slots) {
@@ -162,7 +140,7 @@ int admit_small(tm_server* S, Slot& sl) {
       smem = std::max(smem, small_smem_bytes(r.p.N, pe->M, fp.tw4_len, fp.need_wL));
       it = index.emplace(key, nplans++).first;
     }
-    sl.h_items[count++] = small_item(r, it->second);
+    sl.h_items[count++] = small_item_for(r.out, r.u, r.v, r.n, r.p, it->second);
     sl.tickets.push_back(r.ticket);
     S->queue.pop_front();
   }
