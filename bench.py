@@ -43,10 +43,10 @@ METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50
 # the keys, built from the kernel source with this SHA-256. roofline.traffic reports their
 # sum only while the timed plans, layouts and kernel source are these; otherwise null.
 FFT_DRAM_CAPTURE = {
-    "kernels_sha256": "108dd3bd0270c5ff214c27c29f1fed82cb197c7ac49ed5aed65fd19caf3bcec2",
+    "kernels_sha256": "feb0816c39608521f3f2c8d2814fc4fec0a4c0c799a55ae171f0d2a825bf5122",
     "bytes": {("lo", 8, 2097152, "1024:0:0"): 151422720,
-              ("hi", 8, 2293760, "1024:0:0"): 165637888,
-              ("full", 12, 2949120, "1024:0:0"): 170102784},
+              ("hi", 8, 2293760, "1024:0:0"): 165646848,
+              ("full", 12, 2949120, "1024:0:0"): 170108928},
 }
 
 
