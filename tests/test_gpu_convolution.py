@@ -39,11 +39,11 @@ def _exact_cyclic(x, y):
     return out
 
 
-# every radix, one to three passes; several stages of one odd radix (2^8 x 3^5,
-# 2^12 x 5^3, 2^10 x 7^3), and the high product's certified lengths at n = 2^24
-# (2^16 x 35, 2^14 x 135)
+# every radix, one to three passes; the longest odd parts the library takes (2^8 x 189 =
+# 3^3 x 7, 2^12 x 5^3, 2^10 x 147 = 3 x 7^2), and the high product's certified lengths
+# at n = 2^24 (2^16 x 35, 2^14 x 135)
 LENGTHS = [4, 6, 12, 40, 56, 210, 6144, 6720, 8192, 2 ** 15 * 3, 2 ** 14 * 35,
-           2 ** 8 * 243, 2 ** 12 * 125, 2 ** 10 * 343,
+           2 ** 8 * 189, 2 ** 12 * 125, 2 ** 10 * 147,
            2 ** 17 * 5, 2 ** 20, 2 ** 14 * 135, 2 ** 16 * 35, 2 ** 21 * 3]
 
 
