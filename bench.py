@@ -43,10 +43,10 @@ METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50
 # the keys, built from the kernel source with this SHA-256. roofline.traffic reports their
 # sum only while the timed plans, layouts and kernel source are these; otherwise null.
 FFT_DRAM_CAPTURE = {
-    "kernels_sha256": "feb0816c39608521f3f2c8d2814fc4fec0a4c0c799a55ae171f0d2a825bf5122",
-    "bytes": {("lo", 8, 2097152, "1024:0:0"): 151422720,
-              ("hi", 8, 2293760, "1024:0:0"): 165646848,
-              ("full", 12, 2949120, "1024:0:0"): 170108928},
+    "kernels_sha256": "fb65a9bed1ccde92ab6eff2f543481af6ee85aff9c9c4fed7be5b533b8d2044e",
+    "bytes": {("lo", 8, 2097152, "1024:0:0"): 151417600,
+              ("hi", 8, 2293760, "1024:0:0"): 165634048,
+              ("full", 12, 2949120, "1024:0:0"): 170144256},
 }
 
 
@@ -644,10 +644,11 @@ def run_cuda(args):
     achieved = fft_flops / (fft_ms * 1e-3) / 1e12
     traffic = fft_traffic(plans, layouts, kinds)
     # per two-operand product: 1 forward map (both operands; the full product's first
-    # forward pass forms its split itself), 2 x passes forward FFT launches (u and v on
-    # two streams), twist, passes inverse launches, back map, 3 carry kernels
-    launches = args.steps * sum(3 * plans[k]["fft_passes"] + (5 if k == "full" else 6)
-                                for k in kinds)
+    # forward pass forms its split itself), fwd_streams x passes forward FFT launches
+    # (u and v on two streams, or both in one launch per pass), twist, passes inverse
+    # launches, back map, 3 carry kernels
+    launches = args.steps * sum((plans[k]["fwd_streams"] + 1) * plans[k]["fft_passes"] +
+                                (5 if k == "full" else 6) for k in kinds)
 
     # end to end through tm_mul_host with page-locked host buffers: every call moves
     # the operands host -> device and the product device -> host (the kernels read and

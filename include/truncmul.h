@@ -103,6 +103,10 @@ typedef struct tm_report {
   uint32_t lam_fwd;   /* terms of alpha* (low) or gamma* (high); 0 for full       */
   uint32_t lam_bwd;   /* terms of beta* (low) or delta* (high); 0 for full        */
   uint32_t fft_passes;/* HBM passes of each complex FFT of length N/2             */
+  uint32_t fwd_streams;/* forward FFT launches per pass of a two-operand product
+                         in the per-phase sequence: 2 when u's and v's transforms
+                         run on two streams (each pass fills the GPU alone), 1 when
+                         one launch per pass carries both                         */
   double   margin;    /* largest |2^b Wbar_i - c_i| (low/high) or |W_i - w_i|
                          (full) over the call; filled when rep != NULL           */
   double   e_max;     /* a-priori bound on that distance (< 1/2)                  */
@@ -490,8 +494,9 @@ int tm_plan_set(int kind, uint64_t n_bits, uint32_t b, uint32_t N);
 
 /*
  * tm_plan_query: the plan the library uses for (kind, n_bits), without any
- * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, e_max and
- * workspace_bytes of *rep. Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.
+ * device work: fills b, N, n_digits, lam_fwd, lam_bwd, fft_passes, fwd_streams,
+ * e_max and workspace_bytes of *rep (fwd_streams from the current device's SM
+ * count, 152 without a device). Host only. Returns TM_OK, TM_EINVAL or TM_ERANGE.
  */
 int tm_plan_query(int kind, uint64_t n_bits, tm_report* rep);
 

@@ -24,7 +24,8 @@ class Report(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("status", ctypes.c_int32), ("b", ctypes.c_uint32),
                 ("N", ctypes.c_uint32), ("n_digits", ctypes.c_uint32),
                 ("lam_fwd", ctypes.c_uint32), ("lam_bwd", ctypes.c_uint32),
-                ("fft_passes", ctypes.c_uint32), ("margin", ctypes.c_double),
+                ("fft_passes", ctypes.c_uint32), ("fwd_streams", ctypes.c_uint32),
+                ("margin", ctypes.c_double),
                 ("e_max", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
                 ("table_bytes", ctypes.c_uint64)]
 

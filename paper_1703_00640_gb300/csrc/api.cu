@@ -362,13 +362,14 @@ void ensure_kernel_attributes() {
 
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
                long long stride, cudaStream_t s, const uint64_t* map_limbs,
-               const PlanParams* map_p) {
+               const PlanParams* map_p, const uint64_t* map_limbs2) {
   for (int i = 0; i < pe.fft.npass; ++i) {
     const FftPass& fp = pe.fft.pass[i];
     PassArgs a{};
     if (i == 0 && map_limbs && map_p) {
       const PlanParams& p = *map_p;
       a.map_limbs = reinterpret_cast<const unsigned long long*>(map_limbs);
+      a.map_limbs2 = reinterpret_cast<const unsigned long long*>(map_limbs2);
       a.map_n = p.n;
       a.map_nlimbs = limbs_of(p.n);
       a.map_limit = std::min<int64_t>(p.N, p.n_digits);
@@ -389,6 +390,23 @@ int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int 
     cur ^= 1;
   }
   return cur;
+}
+
+bool fft_fills_gpu(const FftPlan& fft) {
+  static const long long sm_threads = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      sms = 152;
+    }
+    return 1024LL * sms;
+  }();
+  for (int i = 0; i < fft.npass; ++i) {
+    const FftPass& fp = fft.pass[i];
+    if ((fp.Q + fp.C - 1) / fp.C * fp.threads < sm_threads) return false;
+  }
+  return true;
 }
 
 namespace {
@@ -466,6 +484,7 @@ void fill_plan_report(const PlanParams& p, const FftPlan& f, tm_report* rep) {
   rep->lam_fwd = uint32_t(p.lam_fwd);
   rep->lam_bwd = uint32_t(p.lam_bwd);
   rep->fft_passes = uint32_t(f.npass);
+  rep->fwd_streams = fft_fills_gpu(f) ? 2u : 1u;
   rep->margin = 0.0;
   rep->e_max = p.e_max;
   rep->workspace_bytes = workspace_bytes(p);
@@ -747,14 +766,18 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
   // load measured slower: the first pass reads columns, so each thread walks a
   // serial chain of digit and table loads per element; its own kernel reads tiles.)
   const bool map_on_load = kind == TM_FULL && !ws.operands_mapped;
+  // u's and v's forward FFTs on two streams when one transform's passes fill the GPU
+  // (each fills the SMs the other's last partial wave leaves idle); otherwise both
+  // in one launch per pass on s, which keeps the chain of programmatic dependent
+  // launches unbroken (on GB300: 87 against 118 us for the low product at n = 2^20,
+  // 477 against 488 us the other way at 2^24)
+  const bool two_streams = !one && ws.side && fft_fills_gpu(pe.fft);
   double2* bufs_v[2] = {R0 + M, R1 + M};
   PlanParams mp = p;                 // this call's operand size and digit count
   mp.n = n;
   if (map_on_load) {
     mark(1);
-    if (one) {
-      cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
-    } else if (ws.side) {          // u's transform on s, v's on the side stream
+    if (two_streams) {             // u's transform on s, v's on the side stream
       TM_CHECK(cudaEventRecord(ws.fork, s));
       TM_CHECK(cudaStreamWaitEvent(ws.side, ws.fork, 0));
       cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
@@ -762,10 +785,9 @@ int enqueue(int kind, uint64_t* out, const uint64_t* u, const uint64_t* v, uint6
       TM_CHECK(cudaEventRecord(ws.join, ws.side));
       TM_CHECK(cudaStreamWaitEvent(s, ws.join, 0));
     } else {
-      cur = launch_fft(pe, bufs, 0, -1, 1, M, s, u, &mp);
-      launch_fft(pe, bufs_v, 0, -1, 1, M, s, v, &mp);
+      cur = launch_fft(pe, bufs, 0, -1, one ? 1 : 2, M, s, u, &mp, v);
     }
-  } else if (!one && ws.side) {
+  } else if (two_streams) {
     // 1. digits + forward maps of both operands in one launch (one pass over the map
     // table); 2. u's forward FFT on s, v's on the side stream, so that each
     // operand's passes fill the SMs the other's leave idle

@@ -643,13 +643,14 @@ __device__ __forceinline__ void fwd_lo_full_body(FwdArgs a0, int kind, const uin
   unsigned long long* stu = sh.stu;
   unsigned long long* stv = sh.stv;
   const bool two = !a.one_operand;
-  const long long j0 = (long long)bid.x * kFwdTile;
+  const int tile = a.tile ? a.tile : kFwdTile;
+  const long long j0 = (long long)bid.x * tile;
   const int halo = a.lam > 0 ? a.lam - 1 : 0;
-  const int span = kFwdTile + halo;
+  const int span = tile + halo;
   const long long limit = a.N < a.nd ? a.N : a.nd;
   {
     const long long p_lo = j0 - halo > 0 ? j0 - halo : 0;
-    const long long p_hi = j0 + kFwdTile < limit ? j0 + kFwdTile : limit;
+    const long long p_hi = j0 + tile < limit ? j0 + tile : limit;
     const DigitStage gu = stage_digits(stu, a.u, a.nlimbs, a.n, 0, a.b, p_lo, p_hi);
     DigitStage gv{0, true};
     if (two) gv = stage_digits(stv, a.v, a.nlimbs, a.n, 0, a.b, p_lo, p_hi);
@@ -662,7 +663,7 @@ __device__ __forceinline__ void fwd_lo_full_body(FwdArgs a0, int kind, const uin
   }
   __syncthreads();
   const int Q = fx_q(a.b);
-  for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
+  for (int t = threadIdx.x; t < tile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= a.N) break;
     if (a.lam == 0) {
@@ -737,9 +738,10 @@ __device__ __forceinline__ void fwd_hi_body(FwdArgs a0, const uint3 bid, const u
   double& topu = sh.topu;
   double& topv = sh.topv;
   const bool two = !a.one_operand;
-  const long long j0 = (long long)bid.x * kFwdTile;
+  const int tile = a.tile ? a.tile : kFwdTile;
+  const long long j0 = (long long)bid.x * tile;
   const int halo = a.lam - 1;
-  const int span = kFwdTile + halo;
+  const int span = tile + halo;
   const long long N = a.N;
   const bool head = bid.x == 0;
   const int Q = fx_q(a.b);
@@ -749,7 +751,7 @@ __device__ __forceinline__ void fwd_hi_body(FwdArgs a0, const uint3 bid, const u
   }
   {
     const long long p_lo = j0 - halo > 0 ? j0 - halo : 0;
-    const long long p_hi = j0 + kFwdTile < N ? j0 + kFwdTile : N;
+    const long long p_hi = j0 + tile < N ? j0 + tile : N;
     const DigitStage gu = stage_digits(stu, a.u, a.nlimbs, a.n, a.s0, a.b, p_lo, p_hi);
     DigitStage gv{0, true};
     if (two) gv = stage_digits(stv, a.v, a.nlimbs, a.n, a.s0, a.b, p_lo, p_hi);
@@ -776,7 +778,7 @@ __device__ __forceinline__ void fwd_hi_body(FwdArgs a0, const uint3 bid, const u
     __syncthreads();
   }
   const long long head_end = head ? (long long)a.nkappa + a.lam - 1 : 0;
-  for (int t = threadIdx.x; t < kFwdTile; t += blockDim.x) {
+  for (int t = threadIdx.x; t < tile; t += blockDim.x) {
     const long long j = j0 + t;
     if (j >= N) break;
     if (j < head_end) {             // reads a kappa-corrected F'_i or wraps: FP64
@@ -834,8 +836,35 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_hi(FwdArgs a0) {
   fwd_hi_body<ROWS>(a0, blockIdx, gridDim, sh);
 }
 
-void launch_fwd(int kind, const FwdArgs& a, int batch, cudaStream_t s) {
-  const dim3 grid(unsigned((a.N + kFwdTile - 1) / kFwdTile), unsigned(batch));
+// SMs of the current device (read once). A map launch takes 256-position tiles (one
+// position per thread instead of four) when their grid fits in two CTAs per SM: at
+// n = 2^16 and 2^18 bits that cuts 4-30 us from a single product; at 2^20 the 480
+// small CTAs take a second wave and cost 6-9 us, so the 1024-position tiles stay.
+int map_sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    return v;
+  }();
+  return n;
+}
+constexpr int kSmallTile = 256;
+bool small_tile_fits(long long N) {
+  return (N + kSmallTile - 1) / kSmallTile <= 2LL * map_sm_count();
+}
+// the high product's head positions (fewer than nkappa + lam, nkappa <= 3 + 128 / b
+// for N < 2^64) stay in block 0, as the map bodies require
+static_assert(kSmallTile >= 131 + kMaxLam, "head positions outside block 0");
+
+void launch_fwd(int kind, const FwdArgs& a0, int batch, cudaStream_t s) {
+  FwdArgs a = a0;
+  if (!a.items && a.tile == 0 && small_tile_fits(a.N)) a.tile = kSmallTile;
+  const int tile = a.tile ? a.tile : kFwdTile;
+  const dim3 grid(unsigned((a.N + tile - 1) / tile), unsigned(batch));
   const int rows = a.lam - 1;                    // map rows r = 1..lam-1
   if (kind == TM_HI) {
     TM_ROWS_DISPATCH(rows, k_fwd_hi, (grid, kFwdThreads, 0, s), (a));
@@ -1086,7 +1115,8 @@ __device__ __forceinline__ void fft_pass_body(const double2* __restrict__ in, do
     if (q < p.Q) {
       const long long qa = q / p.Qc, qc = q - qa * p.Qc;
       const long long m = qa * p.IA + qc * p.IC + (long long)j * p.IS;
-      val = MAP ? split_pair(p.map_limbs, p.map_n, p.map_nlimbs, p.map_limit, p.map_b, m)
+      val = MAP ? split_pair(bid.y ? p.map_limbs2 : p.map_limbs, p.map_n, p.map_nlimbs,
+                             p.map_limit, p.map_b, m)
                 : in[m];
     }
     buf[c * L + j] = val;
@@ -1158,7 +1188,7 @@ void launch_fft_pass(int dir, const double2* in, double2* out, const PassArgs& p
                       (p.need_wL ? size_t(p.L) : 0)) * sizeof(double2);
   dim3 grid(blocks, batch);
   if (p.map_limbs)
-    launch_pdl(k_fft_pass_map, dim3(blocks), dim3(threads), smem, s, out, p);
+    launch_pdl(k_fft_pass_map, grid, dim3(threads), smem, s, out, p);
   else if (dir < 0)
     launch_pdl(k_fft_pass<-1>, grid, dim3(threads), smem, s, in, out, p);
   else
@@ -1361,11 +1391,12 @@ __device__ __forceinline__ void back_lo_body(BackArgs a0, const uint3 bid, const
   __shared__ unsigned long long bmax;
   __shared__ unsigned bflags;
   const long long N = a.N;
-  const long long i0 = (long long)bid.x * kBackTile;
+  const int tile = a.tile ? a.tile : kBackTile;
+  const long long i0 = (long long)bid.x * tile;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
   unsigned long long dmax = 0;
-  for (int t = threadIdx.x; t < kBackTile; t += blockDim.x) {
+  for (int t = threadIdx.x; t < tile; t += blockDim.x) {
     const long long i = i0 + t;
     if (i >= N) break;
     if (i < a.lam) {
@@ -1491,12 +1522,13 @@ __device__ __forceinline__ void back_hi_body(BackArgs a0, const uint3 bid, const
   __shared__ double P[kMaxLam];
   __shared__ double Hh[kMaxLam + 64 + 1];
   const long long N = a.N;
-  const long long i0 = (long long)bid.x * kBackTile;
+  const int tile = a.tile ? a.tile : kBackTile;
+  const long long i0 = (long long)bid.x * tile;
   const long long head = a.lam + a.nkappa;
   if (threadIdx.x == 0) { bmax = 0; bflags = 0; }
   __syncthreads();
   unsigned long long dmax = 0;
-  for (int t = threadIdx.x; t < kBackTile; t += blockDim.x) {
+  for (int t = threadIdx.x; t < tile; t += blockDim.x) {
     const long long i = i0 + t;
     if (i >= N) break;
     if (i < head) continue;
@@ -1610,7 +1642,9 @@ __global__ void k_back_small(BackArgs a0, int kind) {
   back_small_body_k(a0, kind, blockIdx, gridDim);
 }
 
-void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
+void launch_back(int kind, const BackArgs& a0, int batch, cudaStream_t s) {
+  BackArgs a = a0;
+  if (!a.items && a.tile == 0 && small_tile_fits(a.N)) a.tile = kSmallTile;
   const long long n = a.count;
   unsigned blocks = unsigned((n + kBackThreads - 1) / kBackThreads);
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -1622,7 +1656,8 @@ void launch_back(int kind, const BackArgs& a, int batch, cudaStream_t s) {
     launch_pdl(k_back_small, dim3(1, unsigned(batch)), dim3(32), 0, s, a, kind);
   } else {
     const int rows = kind == TM_LO ? a.lam - 1 : a.lam;
-    const dim3 tgrid(unsigned((a.N + kBackTile - 1) / kBackTile), unsigned(batch));
+    const int tile = a.tile ? a.tile : kBackTile;
+    const dim3 tgrid(unsigned((a.N + tile - 1) / tile), unsigned(batch));
     if (kind == TM_LO) {
       TM_ROWS_DISPATCH(rows, k_back_lo, (tgrid, kBackThreads, 0, s), (a));
     } else {

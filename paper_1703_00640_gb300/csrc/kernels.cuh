@@ -64,8 +64,10 @@ struct PassArgs {
   int need_wL;
   // Full product's split computed as the first pass loads: element m is the pair of
   // balanced digits (2m, 2m + 1) of the operand in map_limbs (0 from map_limit on),
-  // as the forward map kernel forms them. map_limbs == nullptr: read `in`.
+  // as the forward map kernel forms them. map_limbs == nullptr: read `in`. Batch
+  // entry 1 (blockIdx.y = 1) reads the second operand, map_limbs2.
   const unsigned long long* map_limbs;
+  const unsigned long long* map_limbs2;
   unsigned long long map_n;
   long long map_nlimbs, map_limit;
   int map_b;
@@ -106,6 +108,7 @@ struct FwdArgs {
   int one_operand;               // 1: map u only (a square, a kept v, or v on another stream)
   const double* theta_v;         // one_operand: theta_V to copy into theta[1]
   int square_theta;              // one_operand: theta[1] = theta_U (a square)
+  int tile;                      // positions per block, <= kFwdTile (0: kFwdTile)
 };
 
 struct BackItem {
@@ -131,6 +134,7 @@ struct BackArgs {
   long long count;               // number of c values (N, N+1 or L)
   unsigned long long emax_fx;    // bound, units of 2^-63
   DevStatus* status;
+  int tile;                      // coefficients per block, <= kBackTile (0: kBackTile)
 };
 
 struct CarryItem {

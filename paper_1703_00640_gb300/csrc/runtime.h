@@ -63,13 +63,17 @@ int get_tables(const PlanParams& p, bool single_pass, cudaStream_t s,
                std::shared_ptr<PlanEntry>* out);
 // FFT passes of a batch of `batch` sequences of length M (stride `stride`),
 // ping-ponging bufs[cur] <-> bufs[cur ^ 1]; returns the buffer index holding the result
-// With map_limbs, the first pass of a forward transform (batch 1) computes its input,
-// the full product's split (Algorithm 1) of the operand map_limbs under the call's
-// plan *map_p (its n and digit count, which tables shared across n do not carry),
-// as it loads it, instead of reading bufs[cur].
+// With map_limbs, the first pass of a forward transform computes its input, the full
+// product's split (Algorithm 1) of the operand map_limbs under the call's plan *map_p
+// (its n and digit count, which tables shared across n do not carry), as it loads
+// it, instead of reading bufs[cur]; with batch 2, sequence 1 is the split of
+// map_limbs2.
 int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int batch,
                long long stride, cudaStream_t s, const uint64_t* map_limbs = nullptr,
-               const PlanParams* map_p = nullptr);
+               const PlanParams* map_p = nullptr, const uint64_t* map_limbs2 = nullptr);
+// True when every pass of the plan's FFT fills the GPU with one sequence (at least
+// 1024 threads per SM): only then do two sequences gain from running on two streams.
+bool fft_fills_gpu(const FftPlan& fft);
 void ensure_kernel_attributes();
 // Forward transform of one operand kept on the device: the spectrum of V~ (complex
 // length M, the order the forward FFT leaves it in) and theta_V (high product).

@@ -82,6 +82,15 @@ def test_plan_matches_oracle_plan(pkg, n, kind):
     assert mine["e_max"] < 0.5
 
 
+@pytest.mark.parametrize("kind", ["lo", "hi", "full"])
+def test_forward_stream_choice(pkg, kind):
+    # u's and v's forward transforms go to two streams only where one transform's
+    # passes fill the GPU (152 SMs, 1024 threads each): the headline size, not below
+    for n in (1000, 65536, 2**20, 2**22):
+        assert pkg.plan(kind, n)["fwd_streams"] == 1, n
+    assert pkg.plan(kind, 2**24)["fwd_streams"] == 2
+
+
 def test_host_side_errors(pkg):
     lib = pkg.load()
     rep = pkg.Report()
