@@ -40,29 +40,57 @@ METRIC = "truncated-product Gbit/s (lo/hi), t_trunc/t_full on GB300, batched p50
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of all FFT pass launches of one
 # product, from one ncu capture (each launch alone, cold caches) of the plans and layouts in
-# the keys, built from the kernel source with this SHA-256. roofline.traffic reports their
-# sum only while the timed plans, layouts and kernel source are these; otherwise null.
+# the keys, built from FFT pass source with this digest (fft_source_digest). roofline.traffic
+# reports their sum only while the timed plans, layouts and that source are these;
+# otherwise null.
 FFT_DRAM_CAPTURE = {
-    "kernels_sha256": "fb65a9bed1ccde92ab6eff2f543481af6ee85aff9c9c4fed7be5b533b8d2044e",
+    "fft_source_sha256": "4aa18ddfe1420121ba775214995c707e644f7caa4326c284cf93ec7436388be1",
     "bytes": {("lo", 8, 2097152, "1024:0:0"): 151417600,
               ("hi", 8, 2293760, "1024:0:0"): 165634048,
               ("full", 12, 2949120, "1024:0:0"): 170144256},
 }
 
+# Sections of csrc/kernels.cu that the FFT pass kernels compile from (shared constants and
+# helpers, the digit extraction of the split on load, the passes themselves), each from
+# its header line to the next section's header line.
+FFT_SECTIONS = (("// ------------------------------------------------------------ constants",
+                 "// -------------------------------------------------------- table kernels"),
+                ("// ------------------------------------------------------------ digits",
+                 "// ----------------------------------------------------- digit norms"),
+                ("// ------------------------------------------------------------ FFT pass",
+                 "// ------------------------------------------------ twist + pointwise product"))
+
+
+def fft_source_digest():
+    """SHA-256 of the FFT pass kernels' source: csrc/kernels.cuh and the FFT_SECTIONS
+    of csrc/kernels.cu (None if a section header is missing)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1703_00640_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels.cu")) as f:
+        cu = f.read()
+    with open(os.path.join(csrc, "kernels.cuh")) as f:
+        h = hashlib.sha256(f.read().encode())
+    for start, end in FFT_SECTIONS:
+        i = cu.find(start)
+        j = cu.find(end, i + 1)
+        if i < 0 or j < 0:
+            return None
+        h.update(cu[i:j].encode())
+    return h.hexdigest()
+
 
 def fft_traffic(plans, layouts, kinds):
     """The captured DRAM bytes of one step's FFT passes, or None when the capture does
-    not describe this run (another plan, layout or kernel source)."""
-    import hashlib
-    path = os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")
-    with open(path, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != FFT_DRAM_CAPTURE["kernels_sha256"]:
-            return None
+    not describe this run (another plan, layout or FFT pass source)."""
+    if fft_source_digest() != FFT_DRAM_CAPTURE["fft_source_sha256"]:
+        return None
     keys = [(k, plans[k]["b"], plans[k]["N"],
              ":".join(str(layouts[k][x]) for x in ("points", "split", "passes"))) for k in kinds]
     if not all(key in FFT_DRAM_CAPTURE["bytes"] for key in keys):
         return None
     return sum(FFT_DRAM_CAPTURE["bytes"][key] for key in keys)
+
+
 UNIT = "Gbit/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 L2_FLUSH_BYTES = 256 << 20

@@ -1518,17 +1518,23 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
     }
     tmul::init_twiddles(e, s);
     double2* bufs[2] = {buf, reinterpret_cast<double2*>(reinterpret_cast<char*>(buf) + region)};
+    // one warm-up, then three timings of kRun transform pairs back to back (the host
+    // launches ahead of the device); values start near 0.5 and grow by at most M per
+    // forward and inverse pair, far from overflow after kRun pairs
+    constexpr int kRun = 4;
     std::vector<float> t;
-    for (int rep = 0; rep < 4; ++rep) {          // one warm-up, three timed
-      cudaMemsetAsync(buf, 0x3f, 2 * region, s);  // bounded values in every repetition
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaMemsetAsync(buf, 0x3f, 2 * region, s);
       cudaEventRecord(e0, s);
-      const int cur = tmul::launch_fft(e, bufs, 0, -1, 2, M, s);
-      tmul::launch_fft(e, bufs, cur, 1, 1, M, s);
+      for (int i = 0; i < (rep ? kRun : 1); ++i) {
+        const int cur = tmul::launch_fft(e, bufs, 0, -1, 2, M, s);
+        tmul::launch_fft(e, bufs, cur, 1, 1, M, s);
+      }
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = TM_ECUDA; break; }
       float x = 0;
       cudaEventElapsedTime(&x, e0, e1);
-      if (rep) t.push_back(x);
+      if (rep) t.push_back(x / kRun);
     }
     cudaFree(e.tw);
     if (rc) break;
@@ -1617,15 +1623,22 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
     tm_tune lay;
     rc = tm_autotune(kind, n_bits, stream, &lay);
     if (rc) break;
+    // one warm-up product (it builds the tables), then three timings of kRun products
+    // back to back: the host enqueues the next product while the device runs this one,
+    // so the time is the device's, not the host's planning and launch work
+    constexpr int kRun = 8;
+    rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
+    if (rc == TM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = TM_ECUDA;
     std::vector<float> t;
-    for (int rep = 0; rep < 4 && rc == TM_OK; ++rep) {      // one warm-up, three timed
+    for (int rep = 0; rep < 3 && rc == TM_OK; ++rep) {
       cudaEventRecord(e0, s);
-      rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
+      for (int i = 0; i < kRun && rc == TM_OK; ++i)
+        rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
       cudaEventRecord(e1, s);
       if (rc == TM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TM_ECUDA;
       float x = 0;
       cudaEventElapsedTime(&x, e0, e1);
-      if (rep) t.push_back(x);
+      t.push_back(x / kRun);
     }
     if (rc) break;
     std::sort(t.begin(), t.end());
