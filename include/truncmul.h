@@ -423,8 +423,8 @@ int tm_coeffs(int kind, int64_t* c_out, const uint64_t* u, const uint64_t* v, ui
  * n_bits) by measurement. Candidates vary the points per CTA, how the odd prime
  * factors of the length are spread over the passes, and the number of passes; each
  * is timed on `stream` (two forward transforms and one inverse, CUDA events, median
- * of three timings of four such sets back to back, after a warm-up) on scratch
- * buffers of 4 x 16 (N/2) bytes allocated for
+ * of five after a warm-up, each behind a short device-side delay so that the host's
+ * launches are not timed) on scratch buffers of 4 x 16 (N/2) bytes allocated for
  * the call. The fastest, if at least 1% faster than the default layout (else the
  * default), becomes the layout of every later plan with that length on
  * this device (plans built before keep theirs for their current users, e.g. a
@@ -465,8 +465,8 @@ int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
  * planner's first, at most 8. Each candidate's FFT layout is tuned first
  * (tm_autotune, which keeps the layout set for that transform length); then it runs
  * whole products on scratch operands on `stream` (one warm-up, then the median of
- * three CUDA-event timings of 8 products back to back, so that the host's work per
- * call overlaps the device's); the fastest, if at least 1%
+ * five CUDA-event timings of one product each, behind a short device-side delay so
+ * that the host's planning and launch work is not timed); the fastest, if at least 1%
  * faster than the planner's (else the planner's), becomes the plan of (kind, n_bits)
  * for later calls in this process (tm_mul and the calls
  * built on it; tm_mul_static keeps the planner's). Low and full products do not

@@ -1462,6 +1462,9 @@ int tm_operand_destroy(tm_operand* op) {
 
 // An autotuner replaces the default only for a candidate at least 1% faster.
 constexpr double kTuneGain = 0.99;
+// the delay before each timed run of the autotuners: longer than the host's planning
+// and launch work for one product (about 30 us)
+constexpr unsigned long long kTuneDelayNs = 200000ull;
 
 int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
   if (!out) return TM_EINVAL;
@@ -1518,23 +1521,21 @@ int tm_autotune(int kind, uint64_t n_bits, void* stream, tm_tune* out) {
     }
     tmul::init_twiddles(e, s);
     double2* bufs[2] = {buf, reinterpret_cast<double2*>(reinterpret_cast<char*>(buf) + region)};
-    // one warm-up, then three timings of kRun transform pairs back to back (the host
-    // launches ahead of the device); values start near 0.5 and grow by at most M per
-    // forward and inverse pair, far from overflow after kRun pairs
-    constexpr int kRun = 4;
+    // one warm-up, then the median of five isolated timings: a delay kernel holds the
+    // stream while the host enqueues the transforms, so the time is the device's
+    // latency for one forward pair and one inverse, as a single product sees it
     std::vector<float> t;
-    for (int rep = 0; rep < 4; ++rep) {
-      cudaMemsetAsync(buf, 0x3f, 2 * region, s);
+    for (int rep = 0; rep < 6; ++rep) {
+      cudaMemsetAsync(buf, 0x3f, 2 * region, s);  // bounded values in every repetition
+      tmul::launch_delay(kTuneDelayNs, s);
       cudaEventRecord(e0, s);
-      for (int i = 0; i < (rep ? kRun : 1); ++i) {
-        const int cur = tmul::launch_fft(e, bufs, 0, -1, 2, M, s);
-        tmul::launch_fft(e, bufs, cur, 1, 1, M, s);
-      }
+      const int cur = tmul::launch_fft(e, bufs, 0, -1, 2, M, s);
+      tmul::launch_fft(e, bufs, cur, 1, 1, M, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = TM_ECUDA; break; }
       float x = 0;
       cudaEventElapsedTime(&x, e0, e1);
-      if (rep) t.push_back(x / kRun);
+      if (rep) t.push_back(x);
     }
     cudaFree(e.tw);
     if (rc) break;
@@ -1623,22 +1624,22 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
     tm_tune lay;
     rc = tm_autotune(kind, n_bits, stream, &lay);
     if (rc) break;
-    // one warm-up product (it builds the tables), then three timings of kRun products
-    // back to back: the host enqueues the next product while the device runs this one,
-    // so the time is the device's, not the host's planning and launch work
-    constexpr int kRun = 8;
+    // one warm-up product (it builds the tables), then the median of five isolated
+    // products: a delay kernel holds the stream while the host plans and enqueues the
+    // product, so the time is the device's latency for one product, without the
+    // host's work and without overlap with a neighbouring product
     rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
     if (rc == TM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = TM_ECUDA;
     std::vector<float> t;
-    for (int rep = 0; rep < 3 && rc == TM_OK; ++rep) {
+    for (int rep = 0; rep < 5 && rc == TM_OK; ++rep) {
+      tmul::launch_delay(kTuneDelayNs, s);
       cudaEventRecord(e0, s);
-      for (int i = 0; i < kRun && rc == TM_OK; ++i)
-        rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
+      rc = tmul::run(kind, dout, du, dv, n_bits, s, nullptr, nullptr);
       cudaEventRecord(e1, s);
       if (rc == TM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TM_ECUDA;
       float x = 0;
       cudaEventElapsedTime(&x, e0, e1);
-      t.push_back(x / kRun);
+      t.push_back(x);
     }
     if (rc) break;
     std::sort(t.begin(), t.end());

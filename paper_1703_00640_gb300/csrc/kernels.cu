@@ -2612,6 +2612,20 @@ double launch_probe_dfma(int iters, cudaStream_t s) {
   return 2.0 * 8.0 * double(iters) * 256.0 * double(blocks);
 }
 
+// Holds the stream for about `ns` nanoseconds (one thread reads the global timer;
+// at most 2^24 polls, so the kernel ends even if the timer stands still). The
+// autotuners launch it before a timed run so that the host has enqueued the run
+// before the device reaches it.
+__global__ void k_delay(unsigned long long ns) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 24); ++i)
+    if (global_ns() - t0 >= ns) break;
+}
+
+void launch_delay(unsigned long long ns, cudaStream_t s) {
+  k_delay<<<1, 1, 0, s>>>(ns);
+}
+
 void launch_init_rho_powers(double* tab, int nkappa, int ntheta, int b, double lr,
                             cudaStream_t s) {
   if (nkappa + ntheta <= 0) return;

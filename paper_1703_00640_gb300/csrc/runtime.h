@@ -74,6 +74,9 @@ int launch_fft(const PlanEntry& pe, double2* const* bufs, int cur, int dir, int 
 // True when every pass of the plan's FFT fills the GPU with one sequence (at least
 // 1024 threads per SM): only then do two sequences gain from running on two streams.
 bool fft_fills_gpu(const FftPlan& fft);
+// a one-thread kernel (csrc/kernels.cu) that holds the stream for about ns
+// nanoseconds (bounded): the autotuners' timed runs start behind it
+void launch_delay(unsigned long long ns, cudaStream_t s);
 void ensure_kernel_attributes();
 // Forward transform of one operand kept on the device: the spectrum of V~ (complex
 // length M, the order the forward FFT leaves it in) and theta_V (high product).

@@ -67,3 +67,36 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_fft_capture_keyed_to_the_pass_source():
+    # the section headers that bound the FFT pass kernels' source exist in kernels.cu,
+    # so the digest is defined; a change inside a section changes it, a change outside
+    # (another kernel) does not
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.fft_source_digest()
+    assert d is not None and len(d) == 64
+    path = os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cu")
+    with open(path) as f:
+        cu = f.read()
+    start = cu.index(bench.FFT_SECTIONS[2][0])
+    end = cu.index(bench.FFT_SECTIONS[2][1])
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1703_00640_gb300", "csrc", "kernels.cuh")) as f:
+        cuh = f.read()
+
+    def digest(text):
+        h = hashlib.sha256(cuh.encode())
+        for a, b in bench.FFT_SECTIONS:
+            i = text.find(a)
+            h.update(text[i:text.find(b, i + 1)].encode())
+        return h.hexdigest()
+
+    assert digest(cu) == d
+    body = start + len(bench.FFT_SECTIONS[2][0]) + 1
+    inside = cu[:body] + "x" + cu[body:]
+    assert digest(inside) != d
+    after = end + len(bench.FFT_SECTIONS[2][1]) + 1
+    outside = cu[:after] + "x" + cu[after:]
+    assert digest(outside) == d
