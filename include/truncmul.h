@@ -462,8 +462,8 @@ int tm_set_layout(int kind, uint64_t n_bits, const tm_tune* layout);
  * the paper's Section 5 picks N among its candidate lengths by their timings.
  * Candidates: every certified plan (worst-case bound within the target, so every
  * result stays exact) whose transform length is at most 1.15x the planner's, the
- * planner's first, at most 8. Each candidate's FFT layout is tuned first
- * (tm_autotune, which keeps the layout set for that transform length); then it runs
+ * planner's first, at most 8. Each candidate runs with the FFT layout set for its
+ * transform length (the default unless tm_autotune or tm_set_layout set one); it runs
  * whole products on scratch operands on `stream` (one warm-up, then the median of
  * five CUDA-event timings of one product each, behind a short device-side delay so
  * that the host's planning and launch work is not timed); the fastest, if at least 1%

@@ -1619,11 +1619,10 @@ int tm_autotune_plan(int kind, uint64_t n_bits, void* stream, tm_plan_tune* out)
       std::lock_guard<std::mutex> lk(tmul::g_mu);
       tmul::g_params[key] = cands[c];
     }
-    // each candidate competes with its own best FFT layout: tune it first (the
-    // layouts stay set per transform length)
-    tm_tune lay;
-    rc = tm_autotune(kind, n_bits, stream, &lay);
-    if (rc) break;
+    // each candidate runs with the layout already set for its length (the default
+    // unless tm_autotune or tm_set_layout chose one): tm_autotune's choice comes from
+    // timing the transforms alone, and at n = 2^20 a layout it ranked 3% faster there
+    // made whole products 35% slower, so the plan tuner does not re-tune layouts
     // one warm-up product (it builds the tables), then the median of five isolated
     // products: a delay kernel holds the stream while the host plans and enqueues the
     // product, so the time is the device's latency for one product, without the
