@@ -38,7 +38,10 @@
  *
  * Streams and status. `stream` is a cudaStream_t (NULL = the legacy default
  * stream); the device is the current device of the calling thread. Work is
- * enqueued on `stream`. If `rep` is NULL the call returns as soon as the work
+ * enqueued on `stream`; where one operand's FFT passes fill the GPU on their own
+ * (tm_report.fwd_streams = 2), v's forward transform runs on a second stream of
+ * the workspace, forked from and joined back into `stream` by events, so the call
+ * stays ordered on `stream`. If `rep` is NULL the call returns as soon as the work
  * is enqueued and the device-side status (margin check) is collected later
  * by tm_stream_status(). If `rep` is non-NULL the call waits for the stream,
  * fills *rep and returns the device-side status as well.
